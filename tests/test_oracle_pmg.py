@@ -1,0 +1,121 @@
+"""Pins of the oracle's p-multilevel solver (Secs. 3 and 4.2): explicit
+projection matrices, Galerkin coarse operators, the GMRES smoother's residual
+minimisation, closed forms of the two-level correction, and FGMRES versus a
+direct solve."""
+import numpy as np
+import pytest
+
+from oracle.basis import dim_P, element_basis, face_basis
+from oracle.hho import HHO
+from oracle.pmg import PMG, fgmres, gmres_steps, restriction
+from synthetic import quad_mesh, tri_mesh, fields
+
+
+def _explicit_restriction(h, k_f, k_c):
+    """I^{l+1}_l from the integrals int psi_i^{l+1} psi_j^l over every face and element."""
+    m, d = h.mesh, h.d
+    nFf, nFc = dim_P(d - 1, k_f), dim_P(d - 1, k_c)
+    nPf = 1 if h.cond == "vp" else dim_P(d, k_f)
+    nPc = 1 if h.cond == "vp" else dim_P(d, k_c)
+    nf, ne = m.n_face, m.n_elem
+    R = np.zeros((nf * d * nFc + ne * nPc, nf * d * nFf + ne * nPf))
+    for F in h.faces:
+        # independent bases of degree k_f and k_c built on this face
+        Bf, Bc = face_basis(F, k_f), face_basis(F, k_c)
+        X, W = F.rule(2 * k_f + 2)
+        I = Bc.eval(X).T @ (W[:, None] * Bf.eval(X))
+        for c in range(d):
+            R[np.ix_(F.id * d * nFc + c * nFc + np.arange(nFc), F.id * d * nFf + c * nFf + np.arange(nFf))] = I
+    for e in h.elems:
+        Bf, Bc = element_basis(e, k_f), element_basis(e, k_c)
+        X, W = e.rule(2 * k_f + 2)
+        I = Bc.eval(X).T @ (W[:, None] * Bf.eval(X))
+        R[np.ix_(nf * d * nFc + e.id * nPc + np.arange(nPc), nf * d * nFf + e.id * nPf + np.arange(nPf))] = I[:nPc, :nPf]
+    return R
+
+
+@pytest.mark.parametrize("cond", ["vp", "v"])
+def test_restriction_is_unit_diagonal_and_galerkin_is_extraction(cond):
+    h = HHO(tri_mesh(2, jitter=0.2, seed=3), 3, cond)
+    S = h.S.toarray()
+    for k_f, k_c in ((3, 2), (3, 1), (2, 0)):
+        R = restriction(h.mesh, 2, k_f, k_c, cond).toarray()
+        Rx = _explicit_restriction(h, k_f, k_c)
+        assert np.abs(R - Rx).max() < 1e-13
+    pmg = PMG(h, [3, 2, 1, 0], coarse="lu")
+    Sl = S
+    for l in range(1, 4):
+        Rx = _explicit_restriction(h, pmg.degrees[l - 1], pmg.degrees[l])
+        Sl = Rx @ Sl @ Rx.T
+        got = pmg.levels[l].S.toarray()
+        assert np.abs(got - Sl).max() < 1e-13 * np.abs(S).max()
+
+
+def test_gmres_smoother_minimises_over_krylov_space():
+    h = HHO(tri_mesh(3, jitter=0.2, seed=3, neumann_sides=(1,)), 2, "v")
+    pmg = PMG(h, [2, 1, 0])
+    lev = pmg.levels[0]
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal(lev.n)
+    x0 = rng.standard_normal(lev.n)
+    x = gmres_steps(lev.S, lev.precond, b, x0, 2)
+    # brute force: min over y of ||b - S (x0 + Z y)||, Z = [M^-1 r0, M^-1 S M^-1 r0]
+    S = lev.S.toarray()
+    r0 = b - S @ x0
+    z1 = lev.precond(r0)
+    z2 = lev.precond(S @ z1)
+    Z = np.stack([z1, z2], axis=1)
+    y = np.linalg.lstsq(S @ Z, r0, rcond=None)[0]
+    ref = x0 + Z @ y
+    assert np.linalg.norm(x - ref) < 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("cond", ["vp", "v"])
+def test_two_level_correction_closed_forms(cond):
+    """With no smoothing the V-cycle is I^T S_L^{-1} I b; on S I^T c it returns I^T c."""
+    h = HHO(tri_mesh(3, jitter=0.2, seed=3, neumann_sides=(1,)), 2, cond)
+    pmg = PMG(h, [2, 0], smooth_its=0, coarse="lu")
+    R = pmg.R[0].toarray()
+    SL = pmg.levels[1].S.toarray()
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal(h.ndof)
+    z = pmg.apply(b)
+    ref = R.T @ np.linalg.solve(SL, R @ b)
+    assert np.linalg.norm(z - ref) < 1e-10 * np.linalg.norm(ref)
+    c = rng.standard_normal(SL.shape[0])
+    z = pmg.apply(h.S @ (R.T @ c))
+    assert np.linalg.norm(z - R.T @ c) < 1e-9 * np.linalg.norm(c)
+
+
+def test_smoother_with_full_krylov_space_is_exact():
+    h = HHO(quad_mesh(2), 1, "v")
+    pmg = PMG(h, [1, 0])
+    lev = pmg.levels[0]
+    rng = np.random.default_rng(3)
+    b = lev.S @ rng.standard_normal(lev.n)
+    x = gmres_steps(lev.S, lev.precond, b, np.zeros(lev.n), lev.n, x0_zero=True)
+    assert np.linalg.norm(lev.S @ x - b) < 1e-8 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("mk,cond", [(lambda: quad_mesh(4), "vp"),
+                                     (lambda: tri_mesh(4, jitter=0.2, seed=1, neumann_sides=(1,)), "v")])
+def test_fgmres_matches_direct_solve(mk, cond):
+    h = HHO(mk(), 3, cond)
+    rhs = h.assemble_rhs(*h.data_values(fields.TrigStokes2D()))
+    pmg = PMG(h, [3, 2, 1, 0])
+    x, it, rr = fgmres(h.S, pmg.apply, rhs, rtol=1e-12, null=h.null_vector())
+    xd = h.direct_solve(rhs)
+    assert rr <= 1e-12
+    assert np.linalg.norm(x - xd) < 1e-8 * np.linalg.norm(xd)
+
+
+def test_iteration_counts_mesh_independent_vcond():
+    """Near h-independence of the FGMRES count on uniform meshes (Sec. 5.5)."""
+    its = []
+    for n in (4, 8, 16):
+        h = HHO(quad_mesh(n), 2, "v")
+        rhs = h.assemble_rhs(*h.data_values(fields.TrigStokes2D()))
+        pmg = PMG(h, [2, 1, 0])
+        _, it, _ = fgmres(h.S, pmg.apply, rhs, rtol=1e-8, null=h.null_vector())
+        its.append(it)
+    assert its[-1] <= its[0] + 6, its

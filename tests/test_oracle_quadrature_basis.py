@@ -1,0 +1,94 @@
+"""Pins of the oracle's quadrature and hierarchical orthonormal bases (Sec. 2.1, Sec. 4.2)."""
+from math import factorial
+
+import numpy as np
+import pytest
+
+from oracle.basis import dim_P, legendre, multi_indices, element_basis, face_basis
+from oracle.geometry import mesh_geometry
+from oracle.quadrature import segment_rule, triangle_rule, tet_rule
+from synthetic import quad_mesh, tri_mesh, hex_mesh
+
+
+@pytest.mark.parametrize("p", range(0, 13))
+def test_simplex_rules_exact_on_monomials(p):
+    # closed forms on reference simplices: int x^a y^b = a! b! / (a+b+2)!, etc.
+    X, W = segment_rule([0.0], [1.0], p)
+    assert abs(W @ X[:, 0] ** p - 1.0 / (p + 1)) < 1e-14
+    X, W = triangle_rule([0.0, 0.0], [1.0, 0.0], [0.0, 1.0], p)
+    for a in range(p + 1):
+        b = p - a
+        exact = factorial(a) * factorial(b) / factorial(a + b + 2)
+        assert abs(W @ (X[:, 0] ** a * X[:, 1] ** b) - exact) < 1e-14
+    if p <= 8:
+        X, W = tet_rule([0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], p)
+        for a in range(p + 1):
+            for b in range(p + 1 - a):
+                c = p - a - b
+                exact = factorial(a) * factorial(b) * factorial(c) / factorial(a + b + c + 3)
+                assert abs(W @ (X[:, 0] ** a * X[:, 1] ** b * X[:, 2] ** c) - exact) < 1e-14
+
+
+def test_element_measures_match_shoelace():
+    m = quad_mesh(4, jitter=0.25, seed=11)
+    elems, _ = mesh_geometry(m)
+    for e in elems:
+        P = np.array([m.xyz[v] for v in _ccw_vertices(m, e.id)])
+        shoelace = 0.5 * abs(np.dot(P[:, 0], np.roll(P[:, 1], -1)) - np.dot(P[:, 1], np.roll(P[:, 0], -1)))
+        assert abs(e.meas - shoelace) < 1e-14
+
+
+def _ccw_vertices(m, t):
+    # quad faces are (bottom, right, top, left) with vertices (v00,v10),(v10,v11),(v01,v11),(v00,v01)
+    b, r, tp, l = m.faces_of(t)
+    v00, v10 = m.verts_of_face(b)
+    v11 = m.verts_of_face(r)[1]
+    v01 = m.verts_of_face(tp)[0]
+    return [v00, v10, v11, v01]
+
+
+def test_legendre_matches_library():
+    x = np.linspace(-1, 1, 37)
+    P, D = legendre(8, x)
+    for n in range(9):
+        c = np.zeros(n + 1)
+        c[n] = 1.0
+        assert np.allclose(P[n], np.polynomial.legendre.legval(x, c), atol=1e-14)
+        assert np.allclose(D[n], np.polynomial.legendre.legval(x, np.polynomial.legendre.legder(c)), atol=1e-12)
+
+
+def test_multi_index_counts():
+    for nv in (1, 2, 3):
+        for K in range(7):
+            idx = multi_indices(nv, K)
+            assert len(idx) == dim_P(nv, K)
+            assert len(set(idx)) == len(idx)
+            degs = [sum(a) for a in idx]
+            assert degs == sorted(degs)
+
+
+@pytest.mark.parametrize("mesh", [quad_mesh(3, jitter=0.3, seed=2), tri_mesh(3, jitter=0.3, seed=2),
+                                  hex_mesh(2, jitter=0.3, seed=2)], ids=["quad", "tri", "hex"])
+def test_bases_orthonormal_and_hierarchical(mesh):
+    elems, faces = mesh_geometry(mesh)
+    K = 4 if mesh.dim == 2 else 3
+    rng = np.random.default_rng(0)
+    for e in elems[:4]:
+        B = element_basis(e, K)
+        X, W = e.rule(2 * K + 2)
+        V = B.eval(X)
+        assert np.abs(V.T @ (W[:, None] * V) - np.eye(B.n)).max() < 1e-13
+        # first basis function is the constant 1/sqrt|T|
+        assert np.allclose(V[:, 0], 1.0 / np.sqrt(e.meas), rtol=1e-13)
+        # hierarchy: the first dim P^l functions reproduce any polynomial of degree l
+        for l in range(K + 1):
+            n = dim_P(mesh.dim, l)
+            coef = rng.standard_normal(len(multi_indices(mesh.dim, l)))
+            vals = sum(c * np.prod(X ** np.array(a), axis=1) for c, a in zip(coef, multi_indices(mesh.dim, l)))
+            proj = V[:, :n] @ (V[:, :n].T @ (W * vals))
+            assert np.abs(proj - vals).max() < 1e-9 * max(1.0, np.abs(vals).max())
+    for F in faces[:6]:
+        B = face_basis(F, K)
+        X, W = F.rule(2 * K + 2)
+        V = B.eval(X)
+        assert np.abs(V.T @ (W[:, None] * V) - np.eye(B.n)).max() < 1e-13
