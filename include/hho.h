@@ -1,0 +1,179 @@
+/*
+ * hho.h -- C ABI of the GB300 (sm_103a) library for the statically condensed
+ * HHO Stokes system and its p-multilevel V-cycle / FGMRES solve
+ * (Botti & Di Pietro, arXiv 2009.13840).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns an hho_status; no call aborts the process.  On error
+ *    hho_last_error() returns a one-line message.
+ *  - Host pointers ("host") are read during the call only and stay owned by the
+ *    caller.  Device pointers ("device") are caller-owned CUDA allocations on
+ *    the context's device; the library never frees them.
+ *  - All device work is enqueued on the stream given to hho_setup.  Calls that
+ *    return host data synchronise that stream.
+ *  - The context owns every internal device buffer and frees them in
+ *    hho_destroy.
+ *  - Vector layout of a condensed vector at level l (degree k_l): one block of
+ *    b_l = d * dim P^{k_l}_{d-1} values per face (component-major, each
+ *    component's coefficients in the hierarchical orthonormal face basis), then
+ *    one block of n_P values per element (n_P = 1 for v&p-cond, the mean
+ *    pressure coefficient; n_P = dim P^{k_l}_d for v-cond).
+ */
+#ifndef HHO_H
+#define HHO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HHO_OK = 0,
+    HHO_ERR_ARG = 1,           /* invalid argument (null pointer, size, option) */
+    HHO_ERR_MESH = 2,          /* inconsistent mesh arrays */
+    HHO_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    HHO_ERR_NOMEM = 4,         /* device allocation failed */
+    HHO_ERR_SINGULAR = 5,      /* a local or coarse factorisation met a zero pivot */
+    HHO_ERR_NOT_CONVERGED = 6, /* FGMRES stopped at maxit above the tolerance */
+    HHO_ERR_TIMEOUT = 7,       /* a bounded device wait expired */
+    HHO_ERR_STATE = 8,         /* call out of order (e.g. solve before pmg_setup) */
+    HHO_ERR_UNSUPPORTED = 9    /* element shape, degree or dimension not built */
+} hho_status;
+
+typedef enum { HHO_VCOND = 0, HHO_VPCOND = 1 } hho_cond;
+typedef enum { HHO_FP64 = 0, HHO_FP32 = 1 } hho_prec;
+typedef enum { HHO_SMOOTH_BJACOBI = 0 } hho_smoother;
+typedef enum { HHO_NODES_ELEM = 0, HHO_NODES_FACE = 1 } hho_node_set;
+
+typedef struct hho_ctx hho_ctx;
+
+/* Mesh of Sec. 2.1 (host arrays, copied by hho_setup).
+ *   dim            2 or 3
+ *   xyz            n_vert*dim vertex coordinates
+ *   elem_face_ptr  n_elem+1 CSR offsets into elem_face; elem_face lists the
+ *                  faces of each element (any order; it fixes the local order)
+ *   face_vert_ptr  n_face+1 CSR offsets into face_vert; a face is a segment
+ *                  (2 vertices) in 2D, a planar polygon with vertices in cyclic
+ *                  order in 3D
+ *   face_elem      2*n_face: the one or two elements of each face (T1 < T2),
+ *                  -1 in the second slot for a boundary face
+ *   face_bc        n_face tags: 0 interior, 1 Dirichlet, 2 Neumann
+ * Supported: 2D triangles and convex polygons with up to 8 faces, 3D convex
+ * polyhedra with up to 6 faces of up to 4 vertices (hexahedra). */
+typedef struct {
+    int32_t dim;
+    int64_t n_vert;
+    const double* xyz;
+    int64_t n_elem;
+    const int64_t* elem_face_ptr;
+    const int64_t* elem_face;
+    int64_t n_face;
+    const int64_t* face_vert_ptr;
+    const int64_t* face_vert;
+    const int64_t* face_elem;
+    const int8_t* face_bc;
+} hho_mesh;
+
+typedef struct {
+    int32_t iterations;        /* FGMRES iterations (one V-cycle each) */
+    int32_t coarse_iterations; /* total coarse-solver iterations (1 per V-cycle for LU) */
+    double rel_residual;       /* true ||b - S x|| / ||b|| in FP64 */
+    double solve_ms;           /* device time of the solve (CUDA events) */
+    int32_t status;            /* hho_status of the solve */
+} hho_solve_info;
+
+/* Build the context: copy and check the mesh, compute on the GPU the element
+ * and face geometry, hierarchical orthonormal bases (Secs. 2.1, 4.2), the
+ * local operators of Scheme 1 with k' = k (Sec. 2.2, Eq. HHOdiscr:residuals,
+ * Eq. def:HHOAB), the element static condensation (v-cond Eq. ST.1 or
+ * v&p-cond Eq. ST.2) and the assembled level-0 condensed operator in the
+ * face-block layout.  k in 0..5 (2D) or 0..3 (3D).  stream: a cudaStream_t
+ * (NULL = legacy default stream).  *out receives the new context. */
+hho_status hho_setup(const hho_mesh* mesh, int k, int cond, void* stream, hho_ctx** out);
+
+/* Number of condensed unknowns at level `level` (0 = fine) after pmg_setup, or
+ * at level 0 before it. */
+hho_status hho_ndof(const hho_ctx* ctx, int level, int64_t* ndof);
+
+/* Quadrature nodes where the data of hho_assemble are sampled (degree 2k+6
+ * rules on the element and face simplex fans).  which = HHO_NODES_ELEM or
+ * HHO_NODES_FACE.  *n_nodes receives the count.  If d_xyz (device,
+ * n_nodes*dim) is not NULL the coordinates are written there; for the face
+ * set, d_normals (device, n_nodes*dim, may be NULL) receives the unit normal
+ * pointing out of the face's first element. */
+hho_status hho_quad_nodes(hho_ctx* ctx, int which, int64_t* n_nodes, double* d_xyz, double* d_normals);
+
+/* Condensed right-hand side (Eq. ST.1 / Eq. ST.2 right-hand sides) from the
+ * body force and boundary data sampled at the nodes of hho_quad_nodes:
+ *   d_f   device, n_elem_nodes*dim   f at the element nodes
+ *   d_gD  device, n_face_nodes*dim   g_D (read on Dirichlet faces only)
+ *   d_gN  device, n_face_nodes*dim   traction (grad u - p I) n_TF1 (read on
+ *                                    Neumann faces only)
+ *   d_rhs device, ndof(0) or NULL    receives a copy of the condensed RHS. */
+hho_status hho_assemble(hho_ctx* ctx, const double* d_f, const double* d_gD, const double* d_gN, double* d_rhs);
+
+/* Build the p-hierarchy: levels of degrees degrees[0] = k > degrees[1] > ...
+ * > degrees[n_levels-1] >= 0, coarse operators by Galerkin block extraction
+ * from the fine condensed operator (Sec. 4.2), smoother data (face-block
+ * Jacobi with element pressure pivot blocks), and the coarse solver (dense LU
+ * if the coarse level has at most 10^4 unknowns, else block-Jacobi GMRES to a
+ * 1e-3 relative residual).  prec: HHO_FP64.  smooth_its: GMRES iterations per
+ * pre/post smoothing (the paper uses 2). */
+hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, int smooth_its);
+
+/* One V-cycle MG_V(0, r, 0) of the Algorithm of Sec. 3.3: d_z = MG(d_r).
+ * d_r, d_z: device, ndof(0) doubles, may not alias. */
+hho_status pmg_vcycle(hho_ctx* ctx, const double* d_r, double* d_z);
+
+/* y = S^l x with the level-l condensed operator (device vectors of ndof(l)). */
+hho_status hho_spmv(hho_ctx* ctx, int level, const double* d_x, double* d_y);
+
+/* FGMRES (Sec. 3.3) on S x = rhs (the RHS of the last hho_assemble) with one
+ * V-cycle per iteration, CGS2 orthogonalisation, x0 = 0, restart `restart`,
+ * stopping at ||rhs - S x|| <= rtol ||rhs||.  d_x: device, ndof(0).  info may
+ * be NULL.  Returns HHO_ERR_NOT_CONVERGED if maxit is reached. */
+hho_status hho_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double* d_x, hho_solve_info* info);
+
+/* Back-substitution of the eliminated unknowns (Eq. ST.1 / ST.2): for every
+ * element the full local vector [U_T | U_F1 .. U_FN | P_T] (velocity
+ * component-major, orthonormal element/face bases) from the condensed
+ * solution d_x (device, ndof(0)).  d_local: device, sum over elements of
+ * (d*n_E + N*d*n_F + n_E) doubles, elements in order. */
+hho_status hho_recover(hho_ctx* ctx, const double* d_x, double* d_local);
+
+/* L2 errors of Sec. 5.2.2 from recovered local vectors and exact values at the
+ * element nodes of hho_quad_nodes: d_u (n*dim), d_gradu (n*dim*dim, row i =
+ * d u_i / d x_j), d_p (n).  out[4] (host) = ||P u_h - u||, ||grad(P u_h - u)||,
+ * ||p_h - p|| (both means removed when no Neumann face exists), ||div u_T||. */
+hho_status hho_errors(hho_ctx* ctx, const double* d_local, const double* d_u, const double* d_gradu,
+                      const double* d_p, double out[4]);
+
+/* Test hooks (exact-input parity checks).  Copy to host the element Schur
+ * complements S_T (elements in order, each n_k*n_k row-major over the kept
+ * local unknowns [U_F1 .. U_FN | pressure block]); *count receives the total
+ * number of doubles (host_out may be NULL to query). */
+hho_status hho_get_element_schur(hho_ctx* ctx, double* host_out, int64_t* count);
+
+/* Copy the level-l operator to host as COO triplets of its stored blocks
+ * (explicit zeros included).  Query with null arrays to get *nnz. */
+hho_status hho_get_level_coo(hho_ctx* ctx, int level, int64_t* rows, int64_t* cols, double* vals, int64_t* nnz);
+
+/* Replace the element Schur complements by host values (same layout as
+ * hho_get_element_schur) and re-assemble the level-0 operator; the RHS and
+ * hierarchy must be rebuilt afterwards (hho_assemble is unaffected). */
+hho_status hho_set_element_schur(hho_ctx* ctx, const double* host_in);
+
+/* Number of kernels the library has launched on this context since setup
+ * (counts every launch of the solver, V-cycle and SpMV entry points). */
+hho_status hho_launch_count(const hho_ctx* ctx, int64_t* launches);
+
+hho_status hho_destroy(hho_ctx* ctx);
+const char* hho_last_error(const hho_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HHO_H */

@@ -1,0 +1,270 @@
+// C ABI entry points of libhho (declared in include/hho.h).
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace hho {
+
+hho_status device_alloc(hho_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 8;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e);
+        *p = nullptr;
+        return HHO_ERR_NOMEM;
+    }
+    return HHO_OK;
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+static hho_status check_mesh(hho_ctx* ctx, const hho_mesh* m, int k) {
+    auto bad = [&](const char* why) {
+        ctx->err = std::string("hho_setup: ") + why;
+        return HHO_ERR_MESH;
+    };
+    if (m->dim != 2 && m->dim != 3) return bad("dim must be 2 or 3");
+    if ((m->dim == 2 && (k < 0 || k > MAX_K2)) || (m->dim == 3 && (k < 0 || k > MAX_K3))) {
+        ctx->err = "hho_setup: degree k not built for this dimension";
+        return HHO_ERR_UNSUPPORTED;
+    }
+    if (m->n_vert <= 0 || m->n_elem <= 0 || m->n_face <= 0) return bad("empty mesh");
+    if (!m->xyz || !m->elem_face_ptr || !m->elem_face || !m->face_vert_ptr || !m->face_vert || !m->face_elem || !m->face_bc)
+        return bad("null mesh array");
+    if (m->n_elem > INT32_MAX || m->n_face > INT32_MAX || m->n_vert > INT32_MAX) return bad("mesh too large");
+    if (m->elem_face_ptr[0] != 0 || m->face_vert_ptr[0] != 0) return bad("CSR offsets must start at 0");
+    for (int64_t t = 0; t < m->n_elem; ++t) {
+        int64_t N = m->elem_face_ptr[t + 1] - m->elem_face_ptr[t];
+        if (N < m->dim + 1 || N > MAX_NFACE || (m->dim == 3 && N > 6)) return bad("unsupported number of element faces");
+        for (int64_t i = m->elem_face_ptr[t]; i < m->elem_face_ptr[t + 1]; ++i)
+            if (m->elem_face[i] < 0 || m->elem_face[i] >= m->n_face) return bad("element face index out of range");
+    }
+    std::vector<int> seen(m->n_face, 0);
+    for (int64_t t = 0; t < m->n_elem; ++t)
+        for (int64_t i = m->elem_face_ptr[t]; i < m->elem_face_ptr[t + 1]; ++i) {
+            int64_t F = m->elem_face[i];
+            if (m->face_elem[2 * F] != t && m->face_elem[2 * F + 1] != t) return bad("face_elem does not list an element of the face");
+            ++seen[F];
+        }
+    for (int64_t F = 0; F < m->n_face; ++F) {
+        int64_t nv = m->face_vert_ptr[F + 1] - m->face_vert_ptr[F];
+        if ((m->dim == 2 && nv != 2) || (m->dim == 3 && (nv < 3 || nv > MAX_FVERT))) return bad("unsupported face vertex count");
+        for (int64_t i = m->face_vert_ptr[F]; i < m->face_vert_ptr[F + 1]; ++i)
+            if (m->face_vert[i] < 0 || m->face_vert[i] >= m->n_vert) return bad("face vertex index out of range");
+        int64_t T1 = m->face_elem[2 * F], T2 = m->face_elem[2 * F + 1];
+        if (T1 < 0 || T1 >= m->n_elem || T2 >= m->n_elem || T2 == T1) return bad("invalid face_elem entry");
+        int expect = (T2 >= 0) ? 2 : 1;
+        if (seen[F] != expect) return bad("face_elem inconsistent with elem_face");
+        int8_t bc = m->face_bc[F];
+        if (bc < 0 || bc > 2) return bad("face_bc must be 0, 1 or 2");
+        if ((T2 >= 0) != (bc == 0)) return bad("boundary tag on an interior face or interior tag on a boundary face");
+    }
+    return HHO_OK;
+}
+
+}  // namespace hho
+
+using namespace hho;
+
+extern "C" {
+
+hho_status hho_setup(const hho_mesh* mesh, int k, int cond, void* stream, hho_ctx** out) {
+    if (!out) return HHO_ERR_ARG;
+    *out = nullptr;
+    hho_ctx* ctx = new (std::nothrow) hho_ctx();
+    if (!ctx) return HHO_ERR_NOMEM;
+    *out = ctx;
+    if (!mesh) {
+        ctx->err = "hho_setup: null mesh";
+        return HHO_ERR_ARG;
+    }
+    if (cond != HHO_VCOND && cond != HHO_VPCOND) {
+        ctx->err = "hho_setup: cond must be HHO_VCOND or HHO_VPCOND";
+        return HHO_ERR_ARG;
+    }
+    HHO_TRY(check_mesh(ctx, mesh, k));
+    HHO_CUDA(cudaGetDevice(&ctx->device));
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    HHO_TRY(dalloc(ctx, &ctx->d_flag, 4));
+    HHO_TRY(build_discretisation(ctx, mesh, k, cond));
+    HHO_TRY(build_topology(ctx));
+    HHO_TRY(assemble_level0(ctx));
+    HHO_TRY(dalloc(ctx, &ctx->rhs, (size_t)ctx->levels[0].n));
+    return HHO_OK;
+}
+
+hho_status hho_ndof(const hho_ctx* ctx, int level, int64_t* ndof) {
+    if (!ctx || !ndof) return HHO_ERR_ARG;
+    if (level < 0 || level >= (int)ctx->levels.size()) return HHO_ERR_ARG;
+    *ndof = ctx->levels[level].n;
+    return HHO_OK;
+}
+
+hho_status hho_quad_nodes(hho_ctx* ctx, int which, int64_t* n_nodes, double* d_xyz, double* d_normals) {
+    if (!ctx || !n_nodes) return HHO_ERR_ARG;
+    return quad_nodes(ctx, which, n_nodes, d_xyz, d_normals);
+}
+
+hho_status hho_assemble(hho_ctx* ctx, const double* d_f, const double* d_gD, const double* d_gN, double* d_rhs) {
+    if (!ctx) return HHO_ERR_ARG;
+    if (!d_f || !d_gD || !d_gN) {
+        ctx->err = "hho_assemble: null data array";
+        return HHO_ERR_ARG;
+    }
+    HHO_TRY(build_rhs(ctx, d_f, d_gD, d_gN));
+    HHO_TRY(assemble_rhs_vector(ctx, ctx->rhs));
+    if (d_rhs)
+        HHO_CUDA(cudaMemcpyAsync(d_rhs, ctx->rhs, ctx->levels[0].n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+    HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->have_rhs = true;
+    return HHO_OK;
+}
+
+hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, int smooth_its) {
+    if (!ctx) return HHO_ERR_ARG;
+    if (!degrees || n_levels < 1 || n_levels > 8 || degrees[0] != ctx->disc.k) {
+        ctx->err = "pmg_setup: degrees must start at k and have 1..8 entries";
+        return HHO_ERR_ARG;
+    }
+    for (int l = 1; l < n_levels; ++l)
+        if (!(degrees[l] < degrees[l - 1] && degrees[l] >= 0)) {
+            ctx->err = "pmg_setup: degrees must decrease strictly to >= 0";
+            return HHO_ERR_ARG;
+        }
+    if (prec != HHO_FP64) {
+        ctx->err = "pmg_setup: only HHO_FP64 is built";
+        return HHO_ERR_UNSUPPORTED;
+    }
+    if (smooth_its < 0 || smooth_its > 16) {
+        ctx->err = "pmg_setup: smooth_its must be in 0..16";
+        return HHO_ERR_ARG;
+    }
+    ctx->have_pmg = false;
+    while ((int)ctx->levels.size() > 1) {
+        free_level(ctx->levels.back());
+        ctx->levels.pop_back();
+    }
+    ctx->degrees.assign(degrees, degrees + n_levels);
+    ctx->prec = prec;
+    ctx->smooth_its = smooth_its;
+    for (int l = 1; l < n_levels; ++l) HHO_TRY(build_level(ctx, l, degrees[l]));
+    for (int l = 0; l < n_levels; ++l) HHO_TRY(build_smoother(ctx, l));
+    HHO_TRY(pmg_build(ctx));
+    HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->have_pmg = true;
+    return HHO_OK;
+}
+
+hho_status pmg_vcycle(hho_ctx* ctx, const double* d_r, double* d_z) {
+    if (!ctx) return HHO_ERR_ARG;
+    if (!ctx->have_pmg) {
+        ctx->err = "pmg_vcycle: call pmg_setup first";
+        return HHO_ERR_STATE;
+    }
+    if (!d_r || !d_z || d_r == d_z) {
+        ctx->err = "pmg_vcycle: null or aliased vectors";
+        return HHO_ERR_ARG;
+    }
+    HHO_TRY(vcycle(ctx, d_r, d_z));
+    HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
+}
+
+hho_status hho_spmv(hho_ctx* ctx, int level, const double* d_x, double* d_y) {
+    if (!ctx || !d_x || !d_y || d_x == d_y) return HHO_ERR_ARG;
+    if (level < 0 || level >= (int)ctx->levels.size()) {
+        ctx->err = "hho_spmv: no such level";
+        return HHO_ERR_ARG;
+    }
+    return spmv(ctx, level, d_x, d_y);
+}
+
+hho_status hho_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double* d_x, hho_solve_info* info) {
+    if (!ctx || !d_x) return HHO_ERR_ARG;
+    if (!ctx->have_pmg || !ctx->have_rhs) {
+        ctx->err = "hho_solve: call hho_assemble and pmg_setup first";
+        return HHO_ERR_STATE;
+    }
+    return fgmres(ctx, rtol, maxit, restart, d_x, info);
+}
+
+hho_status hho_recover(hho_ctx* ctx, const double* d_x, double* d_local) {
+    if (!ctx || !d_x || !d_local) return HHO_ERR_ARG;
+    if (!ctx->have_rhs) {
+        ctx->err = "hho_recover: call hho_assemble first";
+        return HHO_ERR_STATE;
+    }
+    HHO_TRY(recover_local(ctx, d_x, d_local));
+    HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    return HHO_OK;
+}
+
+hho_status hho_errors(hho_ctx* ctx, const double* d_local, const double* d_u, const double* d_gradu, const double* d_p,
+                      double out[4]) {
+    if (!ctx || !d_local || !d_u || !d_gradu || !d_p || !out) return HHO_ERR_ARG;
+    return compute_errors(ctx, d_local, d_u, d_gradu, d_p, out);
+}
+
+hho_status hho_get_element_schur(hho_ctx* ctx, double* host_out, int64_t* count) {
+    if (!ctx || !count) return HHO_ERR_ARG;
+    *count = ctx->disc.tot_S;
+    if (!host_out) return HHO_OK;
+    HHO_CUDA(cudaMemcpyAsync(host_out, ctx->disc.S, ctx->disc.tot_S * sizeof(double), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    return HHO_OK;
+}
+
+hho_status hho_set_element_schur(hho_ctx* ctx, const double* host_in) {
+    if (!ctx || !host_in) return HHO_ERR_ARG;
+    HHO_CUDA(cudaMemcpyAsync(ctx->disc.S, host_in, ctx->disc.tot_S * sizeof(double), cudaMemcpyHostToDevice,
+                             ctx->stream));
+    HHO_TRY(assemble_level0(ctx));
+    ctx->have_pmg = false;
+    return HHO_OK;
+}
+
+hho_status hho_get_level_coo(hho_ctx* ctx, int level, int64_t* rows, int64_t* cols, double* vals, int64_t* nnz) {
+    if (!ctx || !nnz) return HHO_ERR_ARG;
+    return level_coo(ctx, level, rows, cols, vals, nnz);
+}
+
+hho_status hho_launch_count(const hho_ctx* ctx, int64_t* launches) {
+    if (!ctx || !launches) return HHO_ERR_ARG;
+    *launches = ctx->launches;
+    return HHO_OK;
+}
+
+hho_status hho_destroy(hho_ctx* ctx) {
+    if (!ctx) return HHO_OK;
+    free_workspace(ctx);
+    for (auto& L : ctx->levels) free_level(L);
+    Disc& D = ctx->disc;
+    void* ps[] = {D.xyz, D.ef_ptr, D.ef, D.fv_ptr, D.fv, D.fe, D.flf, D.fbc, D.fgeo, D.fC, D.eC, D.emeas,
+                  D.off_S, D.off_X, D.off_Kei, D.off_P, D.off_loc, D.S, D.X, D.Kei, D.P, D.gT, D.yT, D.off_gT,
+                  D.off_yT, D.enode_off, D.fnode_off, D.gl};
+    for (void* p : ps) dfree(p);
+    Topo& T = ctx->topo;
+    void* pt[] = {T.ff_col, T.ff_nsl, T.fp_col, T.pf_col, T.pf_nsl, T.asm_T, T.asm_lf, T.asm_lg};
+    for (void* p : pt) dfree(p);
+    dfree(ctx->rhs);
+    dfree(ctx->null_vec0);
+    dfree(ctx->null_vec);
+    dfree(ctx->d_flag);
+    delete ctx;
+    return HHO_OK;
+}
+
+const char* hho_last_error(const hho_ctx* ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+// Internal declarations shared by the translation units of libhho.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hho.h"
+
+namespace hho {
+
+constexpr int MAX_K2 = 5;       // highest face degree built in 2D
+constexpr int MAX_K3 = 3;       // highest face degree built in 3D
+constexpr int MAX_NFACE = 8;    // faces per element
+constexpr int MAX_FVERT = 4;    // vertices per 3D face
+constexpr int MAX_GL = 16;      // Gauss-Legendre tables 1..MAX_GL points
+
+__host__ __device__ inline int dimP(int nvar, int deg) {
+    if (deg < 0) return 0;
+    if (nvar == 0) return 1;
+    if (nvar == 1) return deg + 1;
+    if (nvar == 2) return (deg + 1) * (deg + 2) / 2;
+    return (deg + 1) * (deg + 2) * (deg + 3) / 6;
+}
+
+// Geometry of a face (written by the face kernel, read by the element kernels).
+struct FaceGeo {
+    double xF[3];   // vertex average
+    double n[3];    // fixed unit normal
+    double t1[3];   // tangent frame
+    double t2[3];
+    double bc[2];   // bounding-box centre in the frame
+    double br[2];   // bounding-box half widths in the frame
+    double hF;      // diameter
+    double meas;    // measure
+};
+
+// Device-resident mesh and per-element/per-face data of the fine discretisation.
+struct Disc {
+    int d = 0, k = 0, cond = 0;
+    int64_t nv = 0, ne = 0, nf = 0;
+    int nR = 0, nE = 0, nF = 0, b = 0, nP = 0;
+    int maxN = 0;                 // most faces of one element
+    // mesh (device)
+    double* xyz = nullptr;
+    int32_t* ef_ptr = nullptr;    // element -> faces CSR
+    int32_t* ef = nullptr;
+    int32_t* fv_ptr = nullptr;    // face -> vertices CSR
+    int32_t* fv = nullptr;
+    int32_t* fe = nullptr;        // 2 per face
+    int32_t* flf = nullptr;       // local index of the face in each of its elements, 2 per face
+    int8_t* fbc = nullptr;
+    // geometry and bases (device)
+    FaceGeo* fgeo = nullptr;
+    double* fC = nullptr;         // face basis coefficients, nF*nF per face
+    double* eC = nullptr;         // element basis coefficients, nR*nR per element
+    double* emeas = nullptr;      // |T|
+    // local operators (device), per element offsets in the arrays below
+    int64_t* off_S = nullptr;     // S_T (nk*nk)
+    int64_t* off_X = nullptr;     // X = Kee^{-1} Kek (ne_el*nk)
+    int64_t* off_Kei = nullptr;   // Kee^{-1} (ne_el*ne_el)
+    int64_t* off_P = nullptr;     // reconstruction (nR*ns)
+    int64_t* off_loc = nullptr;   // full local vector offsets (recovery output)
+    double* S = nullptr;
+    double* X = nullptr;
+    double* Kei = nullptr;
+    double* P = nullptr;
+    double* gT = nullptr;         // condensed local RHS, nk per element (off_gT)
+    double* yT = nullptr;         // Kee^{-1} rhs_e (recovery), per element (off_yT)
+    int64_t* off_gT = nullptr;
+    int64_t* off_yT = nullptr;
+    std::vector<int64_t> h_off_S, h_off_loc, h_off_gT;
+    int64_t tot_S = 0, tot_X = 0, tot_Kei = 0, tot_P = 0, tot_loc = 0, tot_gT = 0, tot_yT = 0;
+    // data nodes
+    int64_t n_enodes = 0, n_fnodes = 0;
+    int64_t* enode_off = nullptr; // per element
+    int64_t* fnode_off = nullptr; // per face
+    std::vector<int64_t> h_enode_off, h_fnode_off;
+    // Gauss-Legendre tables on [0,1]
+    double* gl = nullptr;         // [MAX_GL+1][MAX_GL] nodes then weights
+    // host copies of topology
+    std::vector<int32_t> h_ef_ptr, h_ef, h_fe, h_flf;
+    std::vector<int8_t> h_fbc;
+};
+
+// Block layout of one level operator (face-block ELL, values innermost over rows).
+struct LevelMat {
+    int k = 0, nF = 0, b = 0, nP = 0;
+    int64_t nf = 0, ne = 0, n = 0;
+    int S_max = 0;    // face slots per face row
+    int N_max = 0;    // face slots per element row
+    // topology (device, shared layout across levels)
+    const int32_t* ff_col = nullptr;  // [S_max][nf]
+    const int32_t* ff_nsl = nullptr;  // [nf]
+    const int32_t* fp_col = nullptr;  // [2][nf]  (-1 = none)
+    const int32_t* pf_col = nullptr;  // [N_max][ne]
+    const int32_t* pf_nsl = nullptr;  // [ne]
+    // values (device, FP64)
+    double* ff = nullptr;   // [S_max][b c][b r][nf]
+    double* fp = nullptr;   // [2][nP c][b r][nf]
+    double* pf = nullptr;   // [N_max][b c][nP r][ne]
+    double* pp = nullptr;   // [nP c][nP r][ne]
+    // smoother data
+    double* dinv = nullptr; // [b c][b r][nf]
+    double* minv = nullptr; // [nP c][nP r][ne]
+};
+
+struct Topo {
+    int S_max = 0, N_max = 0;
+    int32_t *ff_col = nullptr, *ff_nsl = nullptr, *fp_col = nullptr, *pf_col = nullptr, *pf_nsl = nullptr;
+    // assembly sources for level 0
+    int32_t* asm_T = nullptr;   // [S_max][nf] element of the off-diagonal / first diag source
+    int32_t* asm_lf = nullptr;  // [S_max][nf] local index of the row face in that element
+    int32_t* asm_lg = nullptr;  // [S_max][nf] local index of the column face in that element
+    std::vector<int32_t> h_ff_col, h_ff_nsl, h_fp_col, h_pf_col, h_pf_nsl;
+};
+
+struct Workspace;  // solver work vectors (solve.cu)
+
+}  // namespace hho
+
+struct hho_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    hho::Disc disc;
+    hho::Topo topo;
+    std::vector<hho::LevelMat> levels;   // levels[0] always present after setup
+    bool have_rhs = false, have_pmg = false;
+    double* rhs = nullptr;               // condensed RHS (level 0)
+    int smooth_its = 2;
+    int prec = 0;
+    std::vector<int> degrees;
+    // coarse solver
+    int coarse_kind = 0;                 // 0 = dense LU, 1 = block-Jacobi GMRES
+    double coarse_rtol = 1e-3;
+    int coarse_restart = 50, coarse_maxit = 1000;
+    double* lu = nullptr;                // dense LU factors (column-major n*n)
+    int32_t* piv = nullptr;
+    double* null_vec = nullptr;          // unit constant-pressure vector at the coarse level (or null)
+    double* null_vec0 = nullptr;         // same at level 0
+    bool has_null = false;
+    hho::Workspace* ws = nullptr;
+    int64_t coarse_its_total = 0;
+    int* d_flag = nullptr;               // device status word for bounded waits / breakdowns
+    int64_t launches = 0;                // kernels launched by the solver entry points
+};
+
+// ---- helpers shared across units ----
+#define HHO_CUDA(call)                                                          \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+            return HHO_ERR_CUDA;                                                 \
+        }                                                                        \
+    } while (0)
+
+#define HHO_TRY(call)                   \
+    do {                                \
+        hho_status s_ = (call);         \
+        if (s_ != HHO_OK) return s_;    \
+    } while (0)
+
+namespace hho {
+hho_status device_alloc(hho_ctx* ctx, void** p, size_t bytes);
+template <class T>
+inline hho_status dalloc(hho_ctx* ctx, T** p, size_t count) {
+    return device_alloc(ctx, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+void dfree(void* p);
+
+// setup.cu
+hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond);
+hho_status build_rhs(hho_ctx* ctx, const double* f, const double* gD, const double* gN);
+hho_status quad_nodes(hho_ctx* ctx, int which, int64_t* n, double* xyz, double* normals);
+hho_status recover_local(hho_ctx* ctx, const double* x, double* local);
+hho_status compute_errors(hho_ctx* ctx, const double* local, const double* u, const double* gu,
+                          const double* p, double out[4]);
+// assemble.cu
+hho_status build_topology(hho_ctx* ctx);
+hho_status assemble_level0(hho_ctx* ctx);
+hho_status assemble_rhs_vector(hho_ctx* ctx, double* rhs);
+hho_status build_level(hho_ctx* ctx, int l, int k_l);
+hho_status build_smoother(hho_ctx* ctx, int l);
+hho_status level_coo(hho_ctx* ctx, int l, int64_t* rows, int64_t* cols, double* vals, int64_t* nnz);
+void free_level(hho::LevelMat& L);
+// solve.cu
+hho_status pmg_build(hho_ctx* ctx);
+hho_status spmv(hho_ctx* ctx, int l, const double* x, double* y);
+hho_status vcycle(hho_ctx* ctx, const double* r, double* z);
+hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, hho_solve_info* info);
+void free_workspace(hho_ctx* ctx);
+}  // namespace hho

@@ -1,0 +1,261 @@
+"""Thin Python binding of libhho (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts meshes and
+torch CUDA tensors into the plain pointers and sizes of the C ABI declared in
+``include/hho.h``.  Importing it loads ``libhho.so`` from the package
+directory and raises if the library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhho.so")
+
+HHO_OK = 0
+STATUS = {0: "HHO_OK", 1: "HHO_ERR_ARG", 2: "HHO_ERR_MESH", 3: "HHO_ERR_CUDA", 4: "HHO_ERR_NOMEM",
+          5: "HHO_ERR_SINGULAR", 6: "HHO_ERR_NOT_CONVERGED", 7: "HHO_ERR_TIMEOUT", 8: "HHO_ERR_STATE",
+          9: "HHO_ERR_UNSUPPORTED"}
+COND = {"v": 0, "vp": 1}
+NODES = {"elem": 0, "face": 1}
+
+# every entry point declared in include/hho.h
+SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "pmg_setup", "pmg_vcycle", "hho_spmv",
+           "hho_solve", "hho_recover", "hho_errors", "hho_get_element_schur", "hho_get_level_coo",
+           "hho_set_element_schur", "hho_launch_count", "hho_destroy", "hho_last_error"]
+
+
+class HHOError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_vert", C.c_int64), ("xyz", C.POINTER(C.c_double)),
+                ("n_elem", C.c_int64), ("elem_face_ptr", C.POINTER(C.c_int64)), ("elem_face", C.POINTER(C.c_int64)),
+                ("n_face", C.c_int64), ("face_vert_ptr", C.POINTER(C.c_int64)), ("face_vert", C.POINTER(C.c_int64)),
+                ("face_elem", C.POINTER(C.c_int64)), ("face_bc", C.POINTER(C.c_int8))]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("coarse_iterations", C.c_int32), ("rel_residual", C.c_double),
+                ("solve_ms", C.c_double), ("status", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhho.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libhho.so not found at {path}; build it with paper_2009_13840_gb300.build.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "hho_setup": (C.c_int, [C.POINTER(_Mesh), C.c_int, C.c_int, P, C.POINTER(P)]),
+        "hho_ndof": (C.c_int, [P, C.c_int, C.POINTER(C.c_int64)]),
+        "hho_quad_nodes": (C.c_int, [P, C.c_int, C.POINTER(C.c_int64), P, P]),
+        "hho_assemble": (C.c_int, [P, P, P, P, P]),
+        "pmg_setup": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int]),
+        "pmg_vcycle": (C.c_int, [P, P, P]),
+        "hho_spmv": (C.c_int, [P, C.c_int, P, P]),
+        "hho_solve": (C.c_int, [P, C.c_double, C.c_int, C.c_int, P, C.POINTER(SolveInfo)]),
+        "hho_recover": (C.c_int, [P, P, P]),
+        "hho_errors": (C.c_int, [P, P, P, P, P, C.POINTER(C.c_double)]),
+        "hho_get_element_schur": (C.c_int, [P, P, C.POINTER(C.c_int64)]),
+        "hho_get_level_coo": (C.c_int, [P, C.c_int, P, P, P, C.POINTER(C.c_int64)]),
+        "hho_set_element_schur": (C.c_int, [P, P]),
+        "hho_launch_count": (C.c_int, [P, C.POINTER(C.c_int64)]),
+        "hho_destroy": (C.c_int, [P]),
+        "hho_last_error": (C.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    """Device pointer of a contiguous torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class MeshArrays:
+    """Host arrays of a mesh in the layout of the C ABI."""
+    dim: int
+    xyz: np.ndarray
+    elem_face_ptr: np.ndarray
+    elem_face: np.ndarray
+    face_vert_ptr: np.ndarray
+    face_vert: np.ndarray
+    face_elem: np.ndarray
+    face_bc: np.ndarray
+
+    @classmethod
+    def from_mesh(cls, m):
+        return cls(m.dim, np.ascontiguousarray(m.xyz, np.float64), np.ascontiguousarray(m.elem_face_ptr, np.int64),
+                   np.ascontiguousarray(m.elem_face, np.int64), np.ascontiguousarray(m.face_vert_ptr, np.int64),
+                   np.ascontiguousarray(m.face_vert, np.int64), np.ascontiguousarray(m.face_elem, np.int64).ravel(),
+                   np.ascontiguousarray(m.face_bc, np.int8))
+
+
+class Context:
+    """One discretisation (mesh, degree, condensation) on the current CUDA device."""
+
+    def __init__(self, mesh, k: int, cond: str = "vp", stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.mesh = mesh
+        self.k = k
+        self.cond = cond
+        a = MeshArrays.from_mesh(mesh)
+        self._keep = a
+        cm = _Mesh(a.dim, a.xyz.shape[0], a.xyz.ctypes.data_as(C.POINTER(C.c_double)),
+                   a.elem_face_ptr.shape[0] - 1, a.elem_face_ptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                   a.elem_face.ctypes.data_as(C.POINTER(C.c_int64)), a.face_vert_ptr.shape[0] - 1,
+                   a.face_vert_ptr.ctypes.data_as(C.POINTER(C.c_int64)), a.face_vert.ctypes.data_as(C.POINTER(C.c_int64)),
+                   a.face_elem.ctypes.data_as(C.POINTER(C.c_int64)), a.face_bc.ctypes.data_as(C.POINTER(C.c_int8)))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = C.c_void_p()
+        st = self.lib.hho_setup(C.byref(cm), k, COND[cond], C.c_void_p(self.stream.cuda_stream), C.byref(self.h))
+        self._check(st)
+        self.dim = mesh.dim
+
+    # --- plumbing ---
+    def _check(self, st):
+        if st != HHO_OK:
+            msg = self.lib.hho_last_error(self.h).decode() if self.h else ""
+            raise HHOError(st, msg)
+
+    def close(self):
+        if self.h:
+            self.lib.hho_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, *shape):
+        return self._torch.empty(*shape, dtype=self._torch.float64, device="cuda")
+
+    # --- API ---
+    def ndof(self, level: int = 0) -> int:
+        n = C.c_int64()
+        self._check(self.lib.hho_ndof(self.h, level, C.byref(n)))
+        return n.value
+
+    def quad_nodes(self, which: str):
+        n = C.c_int64()
+        self._check(self.lib.hho_quad_nodes(self.h, NODES[which], C.byref(n), None, None))
+        xyz = self._empty(n.value, self.dim)
+        nrm = self._empty(n.value, self.dim) if which == "face" else None
+        self._check(self.lib.hho_quad_nodes(self.h, NODES[which], C.byref(n), _ptr(xyz), _ptr(nrm)))
+        return (xyz, nrm) if which == "face" else xyz
+
+    def assemble(self, f, gD, gN, rhs_out=None):
+        self._check(self.lib.hho_assemble(self.h, _ptr(f), _ptr(gD), _ptr(gN), _ptr(rhs_out)))
+
+    def pmg_setup(self, degrees, smooth_its: int = 2, prec: int = 0):
+        arr = (C.c_int * len(degrees))(*degrees)
+        self._check(self.lib.pmg_setup(self.h, len(degrees), arr, prec, smooth_its))
+        self.degrees = list(degrees)
+
+    def vcycle(self, r, z):
+        self._check(self.lib.pmg_vcycle(self.h, _ptr(r), _ptr(z)))
+
+    def spmv(self, level, x, y):
+        self._check(self.lib.hho_spmv(self.h, level, _ptr(x), _ptr(y)))
+
+    def solve(self, x, rtol=1e-8, maxit=1000, restart=50, raise_on_fail=True):
+        info = SolveInfo()
+        st = self.lib.hho_solve(self.h, rtol, maxit, restart, _ptr(x), C.byref(info))
+        if raise_on_fail:
+            self._check(st)
+        return info.as_dict()
+
+    def recover(self, x):
+        n_loc = self.local_size()
+        out = self._empty(n_loc)
+        self._check(self.lib.hho_recover(self.h, _ptr(x), _ptr(out)))
+        return out
+
+    def local_size(self):
+        d, k = self.dim, self.k
+        nE = _dimP(d, k)
+        nF = _dimP(d - 1, k)
+        N = np.diff(self.mesh.elem_face_ptr)
+        return int(np.sum(d * nE + N * d * nF + nE))
+
+    def errors(self, local, u, gu, p):
+        out = (C.c_double * 4)()
+        self._check(self.lib.hho_errors(self.h, _ptr(local), _ptr(u), _ptr(gu), _ptr(p), out))
+        return dict(u=out[0], gu=out[1], p=out[2], div=out[3])
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        self._check(self.lib.hho_launch_count(self.h, C.byref(n)))
+        return n.value
+
+    def element_schur(self) -> np.ndarray:
+        n = C.c_int64()
+        self._check(self.lib.hho_get_element_schur(self.h, None, C.byref(n)))
+        buf = np.empty(n.value, dtype=np.float64)
+        self._check(self.lib.hho_get_element_schur(self.h, buf.ctypes.data_as(C.c_void_p), C.byref(n)))
+        return buf
+
+    def set_element_schur(self, values: np.ndarray):
+        v = np.ascontiguousarray(values, np.float64)
+        self._check(self.lib.hho_set_element_schur(self.h, v.ctypes.data_as(C.c_void_p)))
+
+    def level_coo(self, level: int):
+        n = C.c_int64()
+        self._check(self.lib.hho_get_level_coo(self.h, level, None, None, None, C.byref(n)))
+        rows = np.empty(n.value, np.int64)
+        cols = np.empty(n.value, np.int64)
+        vals = np.empty(n.value, np.float64)
+        self._check(self.lib.hho_get_level_coo(self.h, level, rows.ctypes.data_as(C.c_void_p),
+                                               cols.ctypes.data_as(C.c_void_p), vals.ctypes.data_as(C.c_void_p),
+                                               C.byref(n)))
+        return rows, cols, vals
+
+
+def _dimP(nv, deg):
+    if nv == 1:
+        return deg + 1
+    if nv == 2:
+        return (deg + 1) * (deg + 2) // 2
+    return (deg + 1) * (deg + 2) * (deg + 3) // 6
+
+
+def data_arrays(ctx: Context, field):
+    """Evaluate a manufactured field at the library's data nodes; returns CUDA tensors (f, gD, gN)."""
+    import torch
+    xe = ctx.quad_nodes("elem").cpu().numpy()
+    xf, nf = ctx.quad_nodes("face")
+    xf, nf = xf.cpu().numpy(), nf.cpu().numpy()
+    f = torch.from_numpy(np.ascontiguousarray(field.f(xe))).cuda()
+    gD = torch.from_numpy(np.ascontiguousarray(field.u(xf))).cuda()
+    gN = torch.from_numpy(np.ascontiguousarray(field.g_neumann(xf, nf))).cuda()
+    return f, gD, gN

@@ -1,0 +1,193 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Sizes are chosen so the oracle finishes in seconds while the GPU path spans
+several thread blocks and ragged tails (13 x 11 grids, 286 or 572 elements).
+Tolerances: 1e-12 relative for operators and vectors built from identical
+inputs; element operators built independently on both sides (bases,
+quadrature, local solves) agree to 1e-11 relative to the largest entry.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.hho import HHO  # noqa: E402
+from oracle.pmg import PMG, fgmres  # noqa: E402
+from synthetic import quad_mesh, tri_mesh, hex_mesh, fields  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def hho_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_13840_gb300 import build, hho
+    build.build()
+    return hho
+
+
+CASES = [
+    ("tri13x11-neu", lambda: tri_mesh(13, 11, jitter=0.2, seed=3, neumann_sides=(1,))),
+    ("quad13x11-dir", lambda: quad_mesh(13, 11, jitter=0.15, seed=5)),
+]
+
+
+def _oracle(mesh, k, cond, fld):
+    h = HHO(mesh, k, cond)
+    rhs = h.assemble_rhs(*h.data_values(fld))
+    return h, rhs
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("cond", ["vp", "v"])
+@pytest.mark.parametrize("k", [0, 1, 3])
+def test_element_schur_and_rhs(hho_mod, name, mk, cond, k):
+    mesh = mk()
+    fld = fields.TrigStokes2D()
+    h, rhs_o = _oracle(mesh, k, cond, fld)
+    ctx = hho_mod.Context(mesh, k, cond)
+    S = ctx.element_schur()
+    ref = np.concatenate([s.ravel() for s in h.S_T])
+    assert S.shape == ref.shape
+    assert _rel(S, ref) < 1e-11
+    f, gD, gN = hho_mod.data_arrays(ctx, fld)
+    rhs = torch.empty(ctx.ndof(0), dtype=torch.float64, device="cuda")
+    ctx.assemble(f, gD, gN, rhs)
+    assert _rel(rhs.cpu().numpy(), rhs_o) < 1e-11
+    # assembled level-0 operator
+    r, c, v = ctx.level_coo(0)
+    A = sp.csr_matrix((v, (r, c)), shape=h.S.shape)
+    assert abs(A - h.S).max() / abs(h.S).max() < 1e-11
+    ctx.close()
+
+
+@pytest.mark.parametrize("cond", ["vp", "v"])
+def test_high_degree_triangles(hho_mod, cond):
+    mesh = tri_mesh(5, 4, jitter=0.2, seed=8, neumann_sides=(1,))
+    h, _ = _oracle(mesh, 5, cond, fields.TrigStokes2D())
+    ctx = hho_mod.Context(mesh, 5, cond)
+    ref = np.concatenate([s.ravel() for s in h.S_T])
+    assert _rel(ctx.element_schur(), ref) < 1e-11
+    ctx.close()
+
+
+def test_hex_elements(hho_mod):
+    mesh = hex_mesh(3, jitter=0.15, seed=2)
+    h, _ = _oracle(mesh, 1, "vp", fields.CurlStokes3D())
+    ctx = hho_mod.Context(mesh, 1, "vp")
+    ref = np.concatenate([s.ravel() for s in h.S_T])
+    assert _rel(ctx.element_schur(), ref) < 1e-11
+    ctx.close()
+
+
+def _exact_input_ctx(hho_mod, h, mesh, k, cond, degrees):
+    """GPU context fed with the oracle's element Schur complements (identical inputs)."""
+    ctx = hho_mod.Context(mesh, k, cond)
+    ctx.set_element_schur(np.concatenate([s.ravel() for s in h.S_T]))
+    ctx.pmg_setup(degrees, smooth_its=2)
+    return ctx
+
+
+@pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("cond", ["vp", "v"])
+def test_levels_spmv_vcycle(hho_mod, name, mk, cond):
+    mesh = mk()
+    k = 3
+    h, rhs_o = _oracle(mesh, k, cond, fields.TrigStokes2D())
+    degrees = [3, 2, 1, 0]
+    ctx = _exact_input_ctx(hho_mod, h, mesh, k, cond, degrees)
+    pmg = PMG(h, degrees)
+    for l in range(4):
+        r, c, v = ctx.level_coo(l)
+        S_ref = pmg.levels[l].S
+        A = sp.csr_matrix((v, (r, c)), shape=S_ref.shape)
+        assert abs(A - S_ref).max() == 0.0  # extraction is an exact copy of identical inputs
+    rng = np.random.default_rng(0)
+    for l in range(4):
+        n = ctx.ndof(l)
+        x = rng.standard_normal(n)
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.spmv(l, torch.from_numpy(x).cuda(), y)
+        ref = pmg.levels[l].S @ x
+        assert _rel(y.cpu().numpy(), ref) < 1e-13
+    for trial in range(2):
+        b = rng.standard_normal(ctx.ndof(0))
+        z = torch.empty_like(torch.from_numpy(b)).cuda()
+        ctx.vcycle(torch.from_numpy(b).cuda(), z)
+        ref = pmg.apply(b)
+        err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err < 1e-10, err
+    ctx.close()
+
+
+@pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("cond", ["vp", "v"])
+def test_fgmres_solution_and_errors(hho_mod, name, mk, cond):
+    mesh = mk()
+    k = 2
+    fld = fields.TrigStokes2D()
+    h, rhs_o = _oracle(mesh, k, cond, fld)
+    xd = h.direct_solve(rhs_o)
+    e_o = h.errors(fld, h.recover(xd))
+    ctx = hho_mod.Context(mesh, k, cond)
+    ctx.assemble(*hho_mod.data_arrays(ctx, fld))
+    ctx.pmg_setup([2, 1, 0])
+    x = torch.empty(ctx.ndof(0), dtype=torch.float64, device="cuda")
+    info = ctx.solve(x, rtol=1e-12, maxit=500)
+    assert info["rel_residual"] <= 1e-12
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(xs - xd) / np.linalg.norm(xd) < 1e-8
+    # oracle FGMRES on the same system takes a comparable number of iterations
+    _, it_o, _ = fgmres(h.S, PMG(h, [2, 1, 0]).apply, rhs_o, rtol=1e-12, null=h.null_vector())
+    assert abs(info["iterations"] - it_o) <= 2, (info["iterations"], it_o)
+    # recovered unknowns and error norms
+    loc = ctx.recover(x).cpu().numpy()
+    ref_loc = np.concatenate(h.recover(xd))
+    assert np.linalg.norm(loc - ref_loc) / np.linalg.norm(ref_loc) < 1e-8
+    xe = ctx.quad_nodes("elem").cpu().numpy()
+    u = torch.from_numpy(np.ascontiguousarray(fld.u(xe))).cuda()
+    gu = torch.from_numpy(np.ascontiguousarray(fld.grad_u(xe))).cuda()
+    p = torch.from_numpy(np.ascontiguousarray(fld.p(xe))).cuda()
+    e = ctx.errors(torch.from_numpy(loc).cuda(), u, gu, p)
+    for key in ("u", "gu", "p", "div"):
+        assert abs(e[key] - e_o[key]) <= 1e-6 * e_o[key] + 1e-13, (key, e[key], e_o[key])
+    ctx.close()
+
+
+def test_polynomial_reproduction_gpu(hho_mod):
+    """Exact consistency carried through the GPU path: P u_h = u, p_h = p for polynomial data."""
+    mesh = tri_mesh(6, 5, jitter=0.25, seed=4, neumann_sides=(1,))
+    k = 2
+    fld = fields.PolyStokes(2, k + 1, k, np.random.default_rng(7))
+    ctx = hho_mod.Context(mesh, k, "v")
+    ctx.assemble(*hho_mod.data_arrays(ctx, fld))
+    ctx.pmg_setup([2, 1, 0])
+    x = torch.empty(ctx.ndof(0), dtype=torch.float64, device="cuda")
+    ctx.solve(x, rtol=1e-13, maxit=500)
+    loc = ctx.recover(x)
+    xe = ctx.quad_nodes("elem").cpu().numpy()
+    e = ctx.errors(loc, torch.from_numpy(fld.u(xe)).cuda(), torch.from_numpy(np.ascontiguousarray(fld.grad_u(xe))).cuda(),
+                   torch.from_numpy(fld.p(xe)).cuda())
+    assert e["u"] < 1e-9 and e["gu"] < 1e-8 and e["p"] < 1e-8, e
+    ctx.close()
+
+
+def test_empty_and_invalid_inputs(hho_mod):
+    mesh = tri_mesh(2, jitter=0.0)
+    with pytest.raises(hho_mod.HHOError):
+        hho_mod.Context(mesh, 9, "v")  # degree not built
+    bad = tri_mesh(2)
+    bad.face_bc = bad.face_bc.copy()
+    bad.face_bc[0] = 0 if bad.face_elem[0, 1] < 0 else 1
+    with pytest.raises(hho_mod.HHOError):
+        hho_mod.Context(bad, 1, "v")
+    ctx = hho_mod.Context(mesh, 1, "v")
+    x = torch.zeros(ctx.ndof(0), dtype=torch.float64, device="cuda")
+    with pytest.raises(hho_mod.HHOError):
+        ctx.solve(x)  # before assemble / pmg_setup
+    ctx.close()
