@@ -165,9 +165,6 @@ def spmv_bytes(ctx, level=0):
     n = ctx.ndof(level)
     m = ctx.mesh
     nf, ne = m.n_face, m.n_elem
-    nslots = 0
-    for F in range(nf):
-        pass
     N = np.diff(m.elem_face_ptr)
     fe = m.face_elem
     # face slots per face row: 1 + sum over its elements of (|F_T| - 1)
@@ -209,10 +206,12 @@ def run_ours(args):
                 flush.fill_(1.0)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.nvtx.range_push("timed_step")
                 e0.record(stream)
                 info = ctx.solve(x, rtol=args.rtol)
                 e1.record(stream)
                 e1.synchronize()
+                torch.cuda.nvtx.range_pop()
                 times.append(e0.elapsed_time(e1))
                 infos.append(info)
             torch.cuda.synchronize()

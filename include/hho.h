@@ -123,6 +123,16 @@ hho_status hho_assemble(hho_ctx* ctx, const double* d_f, const double* d_gD, con
  * pre/post smoothing (the paper uses 2). */
 hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, int smooth_its);
 
+/* Solver options (take effect at the next pmg_setup).  Keys:
+ *   "coarse_dense_max"  largest coarse level solved by the dense inverse
+ *                       (default 10000 unknowns); larger coarse levels use
+ *                       the substructured direct solver
+ *   "dd_elements"       target number of elements per subdomain of the
+ *                       substructured coarse solver (default 128 in 2D, 64 in
+ *                       3D; rounded so the subdomain count is a power of two)
+ * Returns HHO_ERR_ARG for an unknown key or a non-positive value. */
+hho_status hho_set_option(hho_ctx* ctx, const char* key, double value);
+
 /* One V-cycle MG_V(0, r, 0) of the Algorithm of Sec. 3.3: d_z = MG(d_r).
  * d_r, d_z: device, ndof(0) doubles, may not alias. */
 hho_status pmg_vcycle(hho_ctx* ctx, const double* d_r, double* d_z);

@@ -16,9 +16,13 @@
   ILU(0) with faces ordered before pressures would produce when only the face
   diagonal blocks are kept: M_T = S_TT - sum_{F in F_T} S_TF S_FF^{-1} S_FT.
   Right preconditioning, initial guess = current iterate.
-* Coarse solver (Sec. 5.2.2): dense LU when n_L <= 10^4 (with a rank-one fix
-  on the constant-pressure kernel of all-Dirichlet problems), otherwise the same
-  block-Jacobi right-preconditioned GMRES to a 1e-3 relative residual decrease.
+* Coarse solver (Sec. 5.2.2 uses LU in 2D): an exact solve of the coarse
+  system, c = S_L^{-1} d.  Dense LU when n_L <= 10^4 (with a rank-one fix
+  alpha n n^T on the constant-pressure kernel n of all-Dirichlet problems),
+  otherwise a sparse LU of S_L (the kernel pinned by alpha on the diagonal of
+  the first mean-pressure unknown, then the result projected on the complement
+  of n).  Both give the unique solution orthogonal to n.  The block-Jacobi
+  GMRES variant (to a 1e-3 relative residual) is kept as an option.
 * FGMRES (Sec. 3.3): right-preconditioned flexible GMRES, one V-cycle per
   iteration, classical Gram-Schmidt applied twice (CGS2), x0 = 0, restart 50.
 """
@@ -27,6 +31,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from .basis import dim_P
 
@@ -212,7 +217,7 @@ class PMG:
         L = self.levels[-1]
         self.coarse_rtol = coarse_rtol
         if coarse == "auto":
-            coarse = "lu" if L.n <= lu_max else "gmres"
+            coarse = "lu" if L.n <= lu_max else "splu"
         self.coarse = coarse
         self.null = None
         if not mesh.has_neumann():
@@ -226,12 +231,25 @@ class PMG:
                 alpha = float(np.mean(np.abs(np.diag(A))))
                 A = A + alpha * np.outer(self.null, self.null)
             self.lu = sla.lu_factor(A)
+        elif coarse == "splu":
+            A = L.S.tocsc().astype(np.float64)
+            if self.null is not None:
+                alpha = float(np.mean(np.abs(A.diagonal())))
+                pin = L.elem_slice(0).start
+                A = (A + sp.csc_matrix(([alpha], ([pin], [pin])), shape=A.shape)).tocsc()
+            self.splu = spla.splu(A)
         self.coarse_its = []
 
     def coarse_solve(self, d):
         L = self.levels[-1]
         if self.coarse == "lu":
             return sla.lu_solve(self.lu, d)
+        if self.coarse == "splu":
+            c = self.splu.solve(d)
+            if self.null is not None:
+                c = c - (self.null @ c) * self.null
+            self.coarse_its.append(1)
+            return c
         c, its = gmres_solve(L.S, L.precond, d, self.coarse_rtol)
         self.coarse_its.append(its)
         return c

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhho.so")
-SOURCES = ["setup.cu", "assemble.cu", "solve.cu", "capi.cu"]
+SOURCES = ["setup.cu", "assemble.cu", "solve.cu", "coarse.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -32,7 +32,8 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "internal.h"), os.path.join(HERE, "..", "include", "hho.h")]
+    deps = [src, os.path.join(HERE, "..", "include", "hho.h")]
+    deps += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

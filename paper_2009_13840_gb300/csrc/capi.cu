@@ -162,6 +162,22 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
     return HHO_OK;
 }
 
+hho_status hho_set_option(hho_ctx* ctx, const char* key, double value) {
+    if (!ctx || !key) return HHO_ERR_ARG;
+    std::string k(key);
+    if (!(value > 0.0) || value > 9.0e18) {
+        ctx->err = "hho_set_option: value must be positive";
+        return HHO_ERR_ARG;
+    }
+    if (k == "coarse_dense_max") ctx->coarse_dense_max = (int64_t)value;
+    else if (k == "dd_elements") ctx->dd_elements = (int64_t)value;
+    else {
+        ctx->err = "hho_set_option: unknown key " + k;
+        return HHO_ERR_ARG;
+    }
+    return HHO_OK;
+}
+
 hho_status pmg_vcycle(hho_ctx* ctx, const double* d_r, double* d_z) {
     if (!ctx) return HHO_ERR_ARG;
     if (!ctx->have_pmg) {
@@ -245,6 +261,7 @@ hho_status hho_launch_count(const hho_ctx* ctx, int64_t* launches) {
 hho_status hho_destroy(hho_ctx* ctx) {
     if (!ctx) return HHO_OK;
     free_workspace(ctx);
+    coarse_free(ctx);
     for (auto& L : ctx->levels) free_level(L);
     Disc& D = ctx->disc;
     void* ps[] = {D.xyz, D.ef_ptr, D.ef, D.fv_ptr, D.fv, D.fe, D.flf, D.fbc, D.fgeo, D.fC, D.eC, D.emeas,
@@ -256,7 +273,6 @@ hho_status hho_destroy(hho_ctx* ctx) {
     for (void* p : pt) dfree(p);
     dfree(ctx->rhs);
     dfree(ctx->null_vec0);
-    dfree(ctx->null_vec);
     dfree(ctx->d_flag);
     delete ctx;
     return HHO_OK;

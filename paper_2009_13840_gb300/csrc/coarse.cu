@@ -1,0 +1,779 @@
+// Exact solve on the coarsest p-level (Sec. 3.3, Algorithm MG_V: c = A_L^{-1} d;
+// Sec. 5.2.2 uses an LU factorisation in 2D).
+//
+// Two exact solvers, chosen by the size n_L of the coarse level:
+//  * n_L <= 10^4: explicit inverse of the dense coarse matrix by Gauss-Jordan
+//    with partial pivoting; the constant-pressure kernel n of an all-Dirichlet
+//    problem is removed by the rank-one term alpha n n^T (alpha = mean |diag|).
+//  * larger levels: two-level substructuring.  The elements are split into
+//    subdomains by recursive coordinate bisection; the unknowns of faces inside
+//    a subdomain and all element pressures except one mean-pressure unknown per
+//    component (below) are eliminated subdomain by subdomain (batched dense
+//    Gauss-Jordan, one CTA per subdomain), and the dense interface Schur
+//    complement (faces shared by two subdomains plus the kept pressures) is
+//    inverted.  One mean-pressure unknown is kept on the interface for every
+//    connected component of a subdomain's element graph over its interior
+//    faces: the constant pressure of such a component is not controlled by the
+//    interior unknowns and would make the interior block singular.  With a pressure kernel the
+//    diagonal of one kept pressure is shifted by alpha and the result is
+//    projected on the complement of n, which gives the same solution as the
+//    rank-one fix.
+// Both are exact up to rounding.  Partitioning and index maps are integer
+// bookkeeping done once on the host; every floating-point operation runs in
+// the kernels below.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "dense.cuh"
+#include "internal.h"
+
+namespace hho {
+
+namespace {
+
+int grid1d(int64_t n, int tpb) {
+    int64_t g = (n + tpb - 1) / tpb;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152LL * 64));
+}
+
+// ---------------------------------------------------------------------------
+// dense path
+// ---------------------------------------------------------------------------
+__global__ void k_dense_from_level(int64_t nf, int64_t ne, int b, int nP, const int32_t* __restrict__ ff_col,
+                                   const int32_t* __restrict__ ff_nsl, const int32_t* __restrict__ fp_col,
+                                   const int32_t* __restrict__ pf_col, const int32_t* __restrict__ pf_nsl,
+                                   const double* __restrict__ ff, const double* __restrict__ fp,
+                                   const double* __restrict__ pf, const double* __restrict__ pp, double* __restrict__ A,
+                                   int64_t n) {
+    const int64_t nfr = nf * b, ner = ne * nP;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < nfr) {
+            int r = (int)(i / nf);
+            int64_t F = i % nf, row = F * b + r;
+            for (int s = 0; s < ff_nsl[F]; ++s) {
+                int64_t G = ff_col[s * nf + F];
+                for (int c = 0; c < b; ++c) A[row * n + G * b + c] = ff[(((int64_t)s * b + c) * b + r) * nf + F];
+            }
+            for (int p = 0; p < 2; ++p) {
+                int T = fp_col[p * nf + F];
+                if (T < 0) continue;
+                for (int c = 0; c < nP; ++c)
+                    A[row * n + nfr + (int64_t)T * nP + c] = fp[(((int64_t)p * nP + c) * b + r) * nf + F];
+            }
+        } else {
+            int64_t j = i - nfr;
+            int r = (int)(j / ne);
+            int64_t T = j % ne, row = nfr + T * nP + r;
+            for (int f = 0; f < pf_nsl[T]; ++f) {
+                int64_t G = pf_col[f * ne + T];
+                for (int c = 0; c < b; ++c) A[row * n + G * b + c] = pf[(((int64_t)f * b + c) * nP + r) * ne + T];
+            }
+            for (int c = 0; c < nP; ++c) A[row * n + nfr + T * nP + c] = pp[((int64_t)c * nP + r) * ne + T];
+        }
+    }
+}
+
+__global__ void k_mean_abs_diag_dense(const double* __restrict__ A, int64_t n, double* __restrict__ alpha) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += fabs(A[i * n + i]);
+        *alpha = s / (double)n;
+    }
+}
+
+__global__ void k_rank1(double* __restrict__ A, int64_t n, const double* __restrict__ nv, const double* __restrict__ alpha) {
+    double a = *alpha;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i / n, c = i % n;
+        if (nv[r] != 0.0 && nv[c] != 0.0) A[i] += a * nv[r] * nv[c];
+    }
+}
+
+__global__ void k_eye(double* __restrict__ A, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * n; i += (int64_t)gridDim.x * blockDim.x)
+        A[i] = (i / n == i % n) ? 1.0 : 0.0;
+}
+
+__global__ void k_gj_pivot(double* __restrict__ A, double* __restrict__ Ai, int64_t n, int64_t j, double* __restrict__ f,
+                           int* __restrict__ status) {
+    __shared__ double bv[256];
+    __shared__ int64_t bi[256];
+    double best = -1.0;
+    int64_t arg = n;
+    for (int64_t i = j + threadIdx.x; i < n; i += blockDim.x) {
+        double v = fabs(A[i * n + j]);
+        if (v > best) {
+            best = v;
+            arg = i;
+        }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = arg;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 1; t < (int)blockDim.x; ++t)
+            if (bv[t] > bv[0] || (bv[t] == bv[0] && bi[t] < bi[0])) {
+                bv[0] = bv[t];
+                bi[0] = bi[t];
+            }
+        if (!(bv[0] > 0.0)) atomicExch(status, (int)HHO_ERR_SINGULAR);
+    }
+    __syncthreads();
+    if (!(bv[0] > 0.0)) return;
+    int64_t p = bi[0];
+    if (p != j)
+        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+            double t = A[j * n + c];
+            A[j * n + c] = A[p * n + c];
+            A[p * n + c] = t;
+            t = Ai[j * n + c];
+            Ai[j * n + c] = Ai[p * n + c];
+            Ai[p * n + c] = t;
+        }
+    __syncthreads();
+    double inv = 1.0 / A[j * n + j];
+    __syncthreads();
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+        A[j * n + c] *= inv;
+        Ai[j * n + c] *= inv;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) f[i] = (i == j) ? 0.0 : A[i * n + j];
+}
+
+__global__ void k_gj_elim(double* __restrict__ A, double* __restrict__ Ai, int64_t n, int64_t j,
+                          const double* __restrict__ f) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * n * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = idx % (n * n);
+        int64_t i = k / n, c = k % n;
+        double fi = f[i];
+        if (fi == 0.0) continue;
+        if (idx < n * n) A[k] -= fi * A[j * n + c];
+        else Ai[k] -= fi * Ai[j * n + c];
+    }
+}
+
+// y = A x (row-major dense), one warp per row
+__global__ void k_gemv(const double* __restrict__ A, int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    for (int64_t r = w; r < n; r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        double s = 0.0;
+        for (int64_t c = lane; c < n; c += 32) s += A[r * n + c] * x[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) y[r] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// substructuring path
+// ---------------------------------------------------------------------------
+struct DDView {
+    int P;
+    int64_t nG;
+    const int32_t *sub_elem_ptr, *sub_elem, *nI, *nGs;
+    const int64_t *offI, *offA, *offX, *offAG, *offW, *offGam;
+    const int32_t *gam_list;
+    const int64_t* elem_loc_off;
+    const int32_t* elem_loc;
+    const int32_t* ef_ptr;
+    const int64_t* off_S;
+    const double* S;
+    int b0, nF0, nP0, bL, nFL, nPL;
+};
+
+// Assemble, factor and Schur-reduce one subdomain per CTA.
+__global__ void __launch_bounds__(256) k_dd_factor(DDView V, double* __restrict__ scratch, double* __restrict__ AinvT,
+                                                   double* __restrict__ XT, double* __restrict__ AGI,
+                                                   double* __restrict__ G, const double* __restrict__ alpha, int pin_s,
+                                                   int pin_j, int* __restrict__ status) {
+    __shared__ int s_piv;
+    for (int s = blockIdx.x; s < V.P; s += gridDim.x) {
+        const int nI = V.nI[s], nGs = V.nGs[s];
+        const int ldw = 2 * nI + nGs;
+        double* W = scratch + V.offW[s];                 // nI x ldw
+        double* AGG = W + (int64_t)nI * ldw;             // nGs x nGs
+        double* AG = AGI + V.offAG[s];                   // nGs x nI (persistent)
+        for (int64_t i = threadIdx.x; i < (int64_t)nI * ldw; i += blockDim.x) {
+            int r = (int)(i / ldw), c = (int)(i % ldw);
+            W[i] = (c >= nI + nGs && c - nI - nGs == r) ? 1.0 : 0.0;
+        }
+        for (int64_t i = threadIdx.x; i < (int64_t)nGs * nGs; i += blockDim.x) AGG[i] = 0.0;
+        for (int64_t i = threadIdx.x; i < (int64_t)nGs * nI; i += blockDim.x) AG[i] = 0.0;
+        __syncthreads();
+        // element contributions (prefix of the fine element Schur complements), elements in order
+        for (int e = V.sub_elem_ptr[s]; e < V.sub_elem_ptr[s + 1]; ++e) {
+            const int T = V.sub_elem[e];
+            const int N = V.ef_ptr[T + 1] - V.ef_ptr[T];
+            const int nk0 = N * V.b0 + V.nP0, nkL = N * V.bL + V.nPL;
+            const double* ST = V.S + V.off_S[T];
+            const int32_t* loc = V.elem_loc + V.elem_loc_off[T];
+            for (int idx = threadIdx.x; idx < nkL * nkL; idx += blockDim.x) {
+                int a = idx / nkL, bb = idx % nkL;
+                int fa = a < N * V.bL ? (a / V.bL) * V.b0 + ((a % V.bL) / V.nFL) * V.nF0 + (a % V.bL) % V.nFL
+                                      : N * V.b0 + (a - N * V.bL);
+                int fb = bb < N * V.bL ? (bb / V.bL) * V.b0 + ((bb % V.bL) / V.nFL) * V.nF0 + (bb % V.bL) % V.nFL
+                                       : N * V.b0 + (bb - N * V.bL);
+                double v = ST[(int64_t)fa * nk0 + fb];
+                int la = loc[a], lb = loc[bb];
+                if (la < nI && lb < nI) W[(int64_t)la * ldw + lb] += v;
+                else if (la < nI) W[(int64_t)la * ldw + nI + (lb - nI)] += v;
+                else if (lb < nI) AG[(int64_t)(la - nI) * nI + lb] += v;
+                else AGG[(int64_t)(la - nI) * nGs + (lb - nI)] += v;
+            }
+            __syncthreads();
+        }
+        if (s == pin_s && threadIdx.x == 0) AGG[(int64_t)pin_j * nGs + pin_j] += *alpha;
+        __syncthreads();
+        if (!cta_gauss_jordan(W, ldw, nI, nGs + nI, &s_piv)) {
+            if (threadIdx.x == 0) atomicExch(status, (int)HHO_ERR_SINGULAR);
+            continue;
+        }
+        double* At = AinvT + V.offA[s];
+        double* Xt = XT + V.offX[s];
+        for (int64_t idx = threadIdx.x; idx < (int64_t)nI * nI; idx += blockDim.x) {
+            int i = (int)(idx / nI), j = (int)(idx % nI);
+            At[(int64_t)j * nI + i] = W[(int64_t)i * ldw + nI + nGs + j];
+        }
+        for (int64_t idx = threadIdx.x; idx < (int64_t)nI * nGs; idx += blockDim.x) {
+            int i = (int)(idx / nGs), j = (int)(idx % nGs);
+            Xt[(int64_t)j * nI + i] = W[(int64_t)i * ldw + nI + j];
+        }
+        // S_s = AGG - AG X, scattered into the interface matrix (at most two contributions per entry)
+        const int32_t* gam = V.gam_list + V.offGam[s];
+        for (int64_t idx = threadIdx.x; idx < (int64_t)nGs * nGs; idx += blockDim.x) {
+            int i = (int)(idx / nGs), j = (int)(idx % nGs);
+            double acc = 0.0;
+            for (int l = 0; l < nI; ++l) acc += AG[(int64_t)i * nI + l] * W[(int64_t)l * ldw + nI + j];
+            atomicAdd(&G[(int64_t)gam[i] * V.nG + gam[j]], AGG[idx] - acc);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_mean_abs_diag_level(int64_t nf, int64_t ne, int b, int nP, const double* __restrict__ ff,
+                                      const double* __restrict__ pp, double* __restrict__ alpha) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int64_t F = 0; F < nf; ++F)
+            for (int r = 0; r < b; ++r) s += fabs(ff[(((int64_t)0 * b + r) * b + r) * nf + F]);
+        for (int64_t T = 0; T < ne; ++T)
+            for (int r = 0; r < nP; ++r) s += fabs(pp[((int64_t)r * nP + r) * ne + T]);
+        *alpha = s / (double)(nf * b + ne * nP);
+    }
+}
+
+// dI = d[interior unknowns]
+__global__ void k_dd_gather(int64_t nIt, const int32_t* __restrict__ flat_glob, const double* __restrict__ d,
+                            double* __restrict__ dI) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nIt; i += (int64_t)gridDim.x * blockDim.x)
+        dI[i] = d[flat_glob[i]];
+}
+
+// yI = A_II^{-1} dI per subdomain (thread per interior unknown)
+__global__ void k_dd_yI(int64_t nIt, const int32_t* __restrict__ flat_sub, const int64_t* __restrict__ offI,
+                        const int32_t* __restrict__ nI, const int64_t* __restrict__ offA, const double* __restrict__ AinvT,
+                        const double* __restrict__ dI, double* __restrict__ yI) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nIt; f += (int64_t)gridDim.x * blockDim.x) {
+        int s = flat_sub[f];
+        int64_t o = offI[s];
+        int n = nI[s], i = (int)(f - o);
+        const double* A = AinvT + offA[s] + i;
+        const double* x = dI + o;
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += A[(int64_t)j * n] * x[j];
+        yI[f] = acc;
+    }
+}
+
+// rG[g] = d[gam_glob[g]] - sum over its subdomains of (A_GI yI)[j], warp per g, fixed order
+__global__ void k_dd_rG(int64_t nG, const int32_t* __restrict__ gam_glob, const int32_t* __restrict__ g_ptr,
+                        const int32_t* __restrict__ g_s, const int32_t* __restrict__ g_j, const int32_t* __restrict__ nI,
+                        const int64_t* __restrict__ offI, const int64_t* __restrict__ offAG,
+                        const double* __restrict__ AGI, const double* __restrict__ yI, const double* __restrict__ d,
+                        double* __restrict__ rG) {
+    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    for (int64_t g = w; g < nG; g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        double v = d[gam_glob[g]];
+        for (int c = g_ptr[g]; c < g_ptr[g + 1]; ++c) {
+            int s = g_s[c], j = g_j[c], n = nI[s];
+            const double* a = AGI + offAG[s] + (int64_t)j * n;
+            const double* y = yI + offI[s];
+            double acc = 0.0;
+            for (int i = lane; i < n; i += 32) acc += a[i] * y[i];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            v -= acc;
+        }
+        if (lane == 0) rG[g] = v;
+    }
+}
+
+// c[interior] = yI - X cG_s
+__global__ void k_dd_cI(int64_t nIt, const int32_t* __restrict__ flat_sub, const int32_t* __restrict__ flat_glob,
+                        const int64_t* __restrict__ offI, const int32_t* __restrict__ nI, const int32_t* __restrict__ nGs,
+                        const int64_t* __restrict__ offX, const int64_t* __restrict__ offGam,
+                        const int32_t* __restrict__ gam_list, const double* __restrict__ XT,
+                        const double* __restrict__ yI, const double* __restrict__ cG, double* __restrict__ c) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nIt; f += (int64_t)gridDim.x * blockDim.x) {
+        int s = flat_sub[f];
+        int n = nI[s], i = (int)(f - offI[s]), m = nGs[s];
+        const double* X = XT + offX[s] + i;
+        const int32_t* gam = gam_list + offGam[s];
+        double acc = yI[f];
+        for (int j = 0; j < m; ++j) acc -= X[(int64_t)j * n] * cG[gam[j]];
+        c[flat_glob[f]] = acc;
+    }
+}
+
+__global__ void k_dd_scatter_G(int64_t nG, const int32_t* __restrict__ gam_glob, const double* __restrict__ cG,
+                               double* __restrict__ c) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nG; g += (int64_t)gridDim.x * blockDim.x)
+        c[gam_glob[g]] = cG[g];
+}
+
+__global__ void k_null_dot(int64_t n, const double* __restrict__ nv, const double* __restrict__ x, double* __restrict__ out) {
+    // single block, fixed order tree
+    __shared__ double sm[256];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += nv[i] * x[i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sm[0];
+}
+
+__global__ void k_null_sub(int64_t n, const double* __restrict__ nv, const double* __restrict__ dot, double* __restrict__ x) {
+    double a = *dot;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] -= a * nv[i];
+}
+
+}  // namespace
+
+struct CoarseSolver {
+    int kind = 0;  // 0 dense inverse, 1 substructuring
+    int64_t n = 0;
+    double* Ainv = nullptr;   // dense path (n x n) or interface inverse (nG x nG)
+    double* nullv = nullptr;  // unit kernel vector at the coarse level (or null)
+    double* scal = nullptr;   // device scalars
+    // substructuring
+    int P = 0;
+    int64_t nG = 0, nIt = 0;
+    int32_t *sub_elem_ptr = nullptr, *sub_elem = nullptr, *nI = nullptr, *nGs = nullptr, *flat_sub = nullptr,
+            *flat_glob = nullptr, *gam_list = nullptr, *gam_glob = nullptr, *g_ptr = nullptr, *g_s = nullptr,
+            *g_j = nullptr, *elem_loc = nullptr;
+    int64_t *offI = nullptr, *offA = nullptr, *offX = nullptr, *offAG = nullptr, *offGam = nullptr,
+            *elem_loc_off = nullptr;
+    double *AinvT = nullptr, *XT = nullptr, *AGI = nullptr, *dI = nullptr, *yI = nullptr, *rG = nullptr, *cG = nullptr;
+};
+
+void coarse_free(hho_ctx* ctx) {
+    CoarseSolver* C = ctx->coarse;
+    if (!C) return;
+    void* ps[] = {C->Ainv, C->nullv, C->scal, C->sub_elem_ptr, C->sub_elem, C->nI, C->nGs, C->flat_sub, C->flat_glob,
+                  C->gam_list, C->gam_glob, C->g_ptr, C->g_s, C->g_j, C->elem_loc, C->offI, C->offA, C->offX,
+                  C->offAG, C->offGam, C->elem_loc_off, C->AinvT, C->XT, C->AGI, C->dI, C->yI, C->rG, C->cG};
+    for (void* p : ps) dfree(p);
+    delete C;
+    ctx->coarse = nullptr;
+}
+
+static hho_status dense_inverse(hho_ctx* ctx, double* A, double* Ainv, int64_t n) {
+    double* f = nullptr;
+    HHO_TRY(dalloc(ctx, &f, n));
+    k_eye<<<grid1d(n * n, 256), 256, 0, ctx->stream>>>(Ainv, n);
+    HHO_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    for (int64_t j = 0; j < n; ++j) {
+        k_gj_pivot<<<1, 256, 0, ctx->stream>>>(A, Ainv, n, j, f, ctx->d_flag);
+        k_gj_elim<<<grid1d(2 * n * n, 256), 256, 0, ctx->stream>>>(A, Ainv, n, j, f);
+    }
+    cudaError_t le = cudaGetLastError();
+    int flag = 0;
+    cudaError_t ce = cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    dfree(f);
+    HHO_CUDA(le);
+    HHO_CUDA(ce);
+    HHO_CUDA(se);
+    if (flag) {
+        ctx->err = "pmg_setup: singular coarse operator";
+        return HHO_ERR_SINGULAR;
+    }
+    return HHO_OK;
+}
+
+template <class T>
+static hho_status upload(hho_ctx* ctx, T** dst, const std::vector<T>& v) {
+    HHO_TRY(dalloc(ctx, dst, std::max<size_t>(v.size(), 1)));
+    if (!v.empty()) HHO_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return HHO_OK;
+}
+
+// Recursive coordinate bisection of the elements into nparts (a power of two) parts.
+static void rcb(std::vector<int32_t>& ids, size_t lo, size_t hi, int nparts, int part0, const std::vector<double>& cen,
+                int d, std::vector<int32_t>& part) {
+    if (nparts == 1 || hi - lo <= 1) {
+        for (size_t i = lo; i < hi; ++i) part[ids[i]] = part0;
+        return;
+    }
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (size_t i = lo; i < hi; ++i)
+        for (int j = 0; j < d; ++j) {
+            mn[j] = std::min(mn[j], cen[(size_t)ids[i] * d + j]);
+            mx[j] = std::max(mx[j], cen[(size_t)ids[i] * d + j]);
+        }
+    int ax = 0;
+    for (int j = 1; j < d; ++j)
+        if (mx[j] - mn[j] > mx[ax] - mn[ax]) ax = j;
+    std::stable_sort(ids.begin() + lo, ids.begin() + hi, [&](int32_t a, int32_t b) {
+        double ca = cen[(size_t)a * d + ax], cb = cen[(size_t)b * d + ax];
+        return ca < cb || (ca == cb && a < b);
+    });
+    size_t mid = lo + (hi - lo) / 2;
+    rcb(ids, lo, mid, nparts / 2, part0, cen, d, part);
+    rcb(ids, mid, hi, nparts / 2, part0 + nparts / 2, cen, d, part);
+}
+
+static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
+    const Disc& D = ctx->disc;
+    const LevelMat& L = ctx->levels.back();
+    const int d = D.d;
+    const int64_t ne = D.ne, nf = D.nf;
+    const int bL = L.b, nFL = L.nF, nPL = L.nP;
+    // element centroids (vertex averages) from the host copy of the mesh
+    std::vector<double> cen((size_t)ne * d, 0.0);
+    for (int64_t T = 0; T < ne; ++T) {
+        std::vector<int32_t> vs;
+        for (int i = D.h_ef_ptr[T]; i < D.h_ef_ptr[T + 1]; ++i) {
+            int F = D.h_ef[i];
+            for (int v = D.h_fv_ptr[F]; v < D.h_fv_ptr[F + 1]; ++v) vs.push_back(D.h_fv[v]);
+        }
+        std::sort(vs.begin(), vs.end());
+        vs.erase(std::unique(vs.begin(), vs.end()), vs.end());
+        for (int32_t v : vs)
+            for (int j = 0; j < d; ++j) cen[(size_t)T * d + j] += D.h_xyz[(size_t)v * d + j];
+        for (int j = 0; j < d; ++j) cen[(size_t)T * d + j] /= (double)vs.size();
+    }
+    const int64_t target = ctx->dd_elements > 0 ? ctx->dd_elements : ((d == 2) ? 128 : 64);
+    int P = 1;
+    while ((int64_t)P * 2 * target <= ne) P *= 2;
+    std::vector<int32_t> ids(ne), part(ne);
+    std::iota(ids.begin(), ids.end(), 0);
+    rcb(ids, 0, ids.size(), P, 0, cen, d, part);
+    // subdomain element lists (increasing ids)
+    std::vector<std::vector<int32_t>> elems(P);
+    for (int64_t T = 0; T < ne; ++T) elems[part[T]].push_back((int32_t)T);
+    // faces: interior to one subdomain or interface
+    std::vector<int32_t> face_owner(nf);
+    for (int64_t F = 0; F < nf; ++F) {
+        int T1 = D.h_fe[2 * F], T2 = D.h_fe[2 * F + 1];
+        int s1 = part[T1], s2 = T2 >= 0 ? part[T2] : -1;
+        face_owner[F] = (s2 < 0 || s1 == s2) ? s1 : -1;
+    }
+    // one kept mean pressure per connected component of each subdomain's
+    // element graph over its interior faces (each component's constant
+    // pressure mode is otherwise not controlled by the interior unknowns)
+    std::vector<int32_t> uf(ne);
+    std::iota(uf.begin(), uf.end(), 0);
+    auto find = [&](int32_t a) {
+        while (uf[a] != a) {
+            uf[a] = uf[uf[a]];
+            a = uf[a];
+        }
+        return a;
+    };
+    for (int64_t F = 0; F < nf; ++F) {
+        int T1 = D.h_fe[2 * F], T2 = D.h_fe[2 * F + 1];
+        if (T2 >= 0 && face_owner[F] >= 0) {
+            int a = find(T1), b = find(T2);
+            if (a != b) uf[std::max(a, b)] = std::min(a, b);
+        }
+    }
+    std::vector<std::vector<int32_t>> kept(P);
+    std::vector<char> is_kept(ne, 0);
+    for (int s = 0; s < P; ++s)
+        for (int32_t T : elems[s])
+            if (find(T) == T) {
+                kept[s].push_back(T);
+                is_kept[T] = 1;
+            }
+    std::vector<int32_t> gface(nf, -1);
+    int64_t nG = 0;
+    for (int64_t F = 0; F < nf; ++F)
+        if (face_owner[F] < 0) {
+            gface[F] = (int32_t)nG;
+            nG += bL;
+        }
+    std::vector<int64_t> gp0(P + 1);
+    gp0[0] = nG;
+    for (int s = 0; s < P; ++s) gp0[s + 1] = gp0[s] + (int64_t)kept[s].size();
+    nG = gp0[P];
+    std::vector<int32_t> gam_glob(nG);
+    for (int64_t F = 0; F < nf; ++F)
+        if (gface[F] >= 0)
+            for (int r = 0; r < bL; ++r) gam_glob[gface[F] + r] = (int32_t)(F * bL + r);
+    for (int s = 0; s < P; ++s)
+        for (size_t q = 0; q < kept[s].size(); ++q)
+            gam_glob[gp0[s] + q] = (int32_t)(nf * bL + (int64_t)kept[s][q] * nPL);
+    // per-subdomain unknown lists and element local maps
+    std::vector<int32_t> h_nI(P), h_nGs(P), flat_sub, flat_glob, gam_list, h_elem_loc, sub_elem_ptr(P + 1, 0),
+        sub_elem;
+    std::vector<int64_t> offI(P + 1, 0), offA(P), offX(P), offAG(P), offW(P), offGam(P + 1, 0),
+        elem_loc_off(ne, 0);
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> gcontrib(nG);
+    std::vector<int32_t> loc_of((size_t)L.n, -1);
+    int pin_j = -1;  // local interface index, in subdomain 0, of the pinned kept pressure
+    auto nGss_faces = [](size_t total, size_t nk) { return (int)(total - nk); };
+    int64_t tA = 0, tX = 0, tAG = 0, tW = 0;
+    std::vector<int64_t> elem_loc_size(ne);
+    for (int64_t T = 0; T < ne; ++T) elem_loc_size[T] = (D.h_ef_ptr[T + 1] - D.h_ef_ptr[T]) * bL + nPL;
+    {
+        int64_t o = 0;
+        for (int64_t T = 0; T < ne; ++T) {
+            elem_loc_off[T] = o;
+            o += elem_loc_size[T];
+        }
+        h_elem_loc.assign(o, -1);
+    }
+    for (int s = 0; s < P; ++s) {
+        std::vector<int32_t> faces_in, faces_if;
+        for (int32_t T : elems[s]) {
+            sub_elem.push_back(T);
+            for (int i = D.h_ef_ptr[T]; i < D.h_ef_ptr[T + 1]; ++i) {
+                int F = D.h_ef[i];
+                if (face_owner[F] == s) faces_in.push_back(F);
+                else faces_if.push_back(F);
+            }
+        }
+        sub_elem_ptr[s + 1] = (int32_t)sub_elem.size();
+        std::sort(faces_in.begin(), faces_in.end());
+        faces_in.erase(std::unique(faces_in.begin(), faces_in.end()), faces_in.end());
+        std::sort(faces_if.begin(), faces_if.end());
+        faces_if.erase(std::unique(faces_if.begin(), faces_if.end()), faces_if.end());
+        std::vector<int32_t> unk;  // global coarse indices in local order
+        for (int F : faces_in)
+            for (int r = 0; r < bL; ++r) unk.push_back((int32_t)(F * bL + r));
+        for (int32_t T : elems[s])
+            for (int i = 0; i < nPL; ++i)
+                if (!(is_kept[T] && i == 0)) unk.push_back((int32_t)(nf * bL + (int64_t)T * nPL + i));
+        const int nIs = (int)unk.size();
+        std::vector<int32_t> gl;  // interface indices
+        for (int F : faces_if)
+            for (int r = 0; r < bL; ++r) {
+                unk.push_back((int32_t)(F * bL + r));
+                gl.push_back(gface[F] + r);
+            }
+        for (size_t q = 0; q < kept[s].size(); ++q) {
+            unk.push_back((int32_t)(nf * bL + (int64_t)kept[s][q] * nPL));
+            gl.push_back((int32_t)(gp0[s] + q));
+        }
+        if (s == 0) pin_j = nGss_faces(gl.size(), kept[s].size());
+        const int nGss = (int)gl.size();
+        h_nI[s] = nIs;
+        h_nGs[s] = nGss;
+        for (int i = 0; i < nIs; ++i) {
+            flat_sub.push_back(s);
+            flat_glob.push_back(unk[i]);
+        }
+        offI[s + 1] = offI[s] + nIs;
+        for (int j = 0; j < nGss; ++j) {
+            gam_list.push_back(gl[j]);
+            gcontrib[gl[j]].push_back({s, j});
+        }
+        offGam[s + 1] = offGam[s] + nGss;
+        offA[s] = tA;
+        tA += (int64_t)nIs * nIs;
+        offX[s] = tX;
+        tX += (int64_t)nIs * nGss;
+        offAG[s] = tAG;
+        tAG += (int64_t)nGss * nIs;
+        offW[s] = tW;
+        tW += (int64_t)nIs * (2 * nIs + nGss) + (int64_t)nGss * nGss;
+        for (int i = 0; i < (int)unk.size(); ++i) loc_of[unk[i]] = i;
+        for (int32_t T : elems[s]) {
+            int N = D.h_ef_ptr[T + 1] - D.h_ef_ptr[T];
+            int32_t* lo = h_elem_loc.data() + elem_loc_off[T];
+            for (int f = 0; f < N; ++f) {
+                int F = D.h_ef[D.h_ef_ptr[T] + f];
+                for (int r = 0; r < bL; ++r) lo[f * bL + r] = loc_of[F * bL + r];
+            }
+            for (int i = 0; i < nPL; ++i) lo[N * bL + i] = loc_of[nf * bL + (int64_t)T * nPL + i];
+        }
+        for (int32_t u : unk) loc_of[u] = -1;
+    }
+    for (int32_t v : h_elem_loc)
+        if (v < 0) {
+            ctx->err = "pmg_setup: inconsistent coarse substructuring maps";
+            return HHO_ERR_MESH;
+        }
+    std::vector<int32_t> g_ptr(nG + 1, 0), g_s, g_j;
+    for (int64_t g = 0; g < nG; ++g) {
+        for (auto& c : gcontrib[g]) {
+            g_s.push_back(c.first);
+            g_j.push_back(c.second);
+        }
+        g_ptr[g + 1] = (int32_t)g_s.size();
+    }
+    C->P = P;
+    C->nG = nG;
+    C->nIt = offI[P];
+    HHO_TRY(upload(ctx, &C->sub_elem_ptr, sub_elem_ptr));
+    HHO_TRY(upload(ctx, &C->sub_elem, sub_elem));
+    HHO_TRY(upload(ctx, &C->nI, h_nI));
+    HHO_TRY(upload(ctx, &C->nGs, h_nGs));
+    HHO_TRY(upload(ctx, &C->flat_sub, flat_sub));
+    HHO_TRY(upload(ctx, &C->flat_glob, flat_glob));
+    HHO_TRY(upload(ctx, &C->gam_list, gam_list));
+    HHO_TRY(upload(ctx, &C->gam_glob, gam_glob));
+    HHO_TRY(upload(ctx, &C->g_ptr, g_ptr));
+    HHO_TRY(upload(ctx, &C->g_s, g_s));
+    HHO_TRY(upload(ctx, &C->g_j, g_j));
+    HHO_TRY(upload(ctx, &C->elem_loc, h_elem_loc));
+    HHO_TRY(upload(ctx, &C->offI, offI));
+    HHO_TRY(upload(ctx, &C->offA, offA));
+    HHO_TRY(upload(ctx, &C->offX, offX));
+    HHO_TRY(upload(ctx, &C->offAG, offAG));
+    HHO_TRY(upload(ctx, &C->offGam, offGam));
+    HHO_TRY(upload(ctx, &C->elem_loc_off, elem_loc_off));
+    int64_t* d_offW = nullptr;
+    HHO_TRY(upload(ctx, &d_offW, offW));
+    HHO_TRY(dalloc(ctx, &C->AinvT, std::max<int64_t>(tA, 1)));
+    HHO_TRY(dalloc(ctx, &C->XT, std::max<int64_t>(tX, 1)));
+    HHO_TRY(dalloc(ctx, &C->AGI, std::max<int64_t>(tAG, 1)));
+    HHO_TRY(dalloc(ctx, &C->dI, std::max<int64_t>(C->nIt, 1)));
+    HHO_TRY(dalloc(ctx, &C->yI, std::max<int64_t>(C->nIt, 1)));
+    HHO_TRY(dalloc(ctx, &C->rG, nG));
+    HHO_TRY(dalloc(ctx, &C->cG, nG));
+    double *scratch = nullptr, *G = nullptr;
+    HHO_TRY(dalloc(ctx, &scratch, std::max<int64_t>(tW, 1)));
+    HHO_TRY(dalloc(ctx, &G, (size_t)nG * nG));
+    HHO_TRY(dalloc(ctx, &C->Ainv, (size_t)nG * nG));
+    HHO_CUDA(cudaMemsetAsync(G, 0, (size_t)nG * nG * sizeof(double), ctx->stream));
+    // pin of the pressure kernel (all-Dirichlet problems)
+    int pin_s = -1;
+    if (ctx->has_null) {
+        pin_s = 0;  // first kept pressure of subdomain 0
+        k_mean_abs_diag_level<<<1, 32, 0, ctx->stream>>>(L.nf, L.ne, L.b, L.nP, L.ff, L.pp, C->scal);
+    } else {
+        HHO_CUDA(cudaMemsetAsync(C->scal, 0, sizeof(double), ctx->stream));
+    }
+    DDView V;
+    V.P = P;
+    V.nG = nG;
+    V.sub_elem_ptr = C->sub_elem_ptr;
+    V.sub_elem = C->sub_elem;
+    V.nI = C->nI;
+    V.nGs = C->nGs;
+    V.offI = C->offI;
+    V.offA = C->offA;
+    V.offX = C->offX;
+    V.offAG = C->offAG;
+    V.offW = d_offW;
+    V.offGam = C->offGam;
+    V.gam_list = C->gam_list;
+    V.elem_loc_off = C->elem_loc_off;
+    V.elem_loc = C->elem_loc;
+    V.ef_ptr = D.ef_ptr;
+    V.off_S = D.off_S;
+    V.S = D.S;
+    V.b0 = D.b;
+    V.nF0 = D.nF;
+    V.nP0 = D.nP;
+    V.bL = bL;
+    V.nFL = nFL;
+    V.nPL = nPL;
+    HHO_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    k_dd_factor<<<P, 256, 0, ctx->stream>>>(V, scratch, C->AinvT, C->XT, C->AGI, G, C->scal, pin_s, pin_j,
+                                            ctx->d_flag);
+    cudaError_t le = cudaGetLastError();
+    int flag = 0;
+    cudaError_t ce = cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    dfree(scratch);
+    dfree(d_offW);
+    HHO_CUDA(le);
+    HHO_CUDA(ce);
+    HHO_CUDA(se);
+    if (flag) {
+        dfree(G);
+        ctx->err = "pmg_setup: singular subdomain block in the coarse solver";
+        return HHO_ERR_SINGULAR;
+    }
+    hho_status st = dense_inverse(ctx, G, C->Ainv, nG);
+    dfree(G);
+    return st;
+}
+
+hho_status coarse_setup(hho_ctx* ctx) {
+    coarse_free(ctx);
+    CoarseSolver* C = new CoarseSolver();
+    ctx->coarse = C;
+    const LevelMat& L = ctx->levels.back();
+    C->n = L.n;
+    HHO_TRY(dalloc(ctx, &C->scal, 8));
+    if (ctx->has_null) {
+        std::vector<double> meas(L.ne), v(L.n, 0.0);
+        HHO_CUDA(cudaMemcpy(meas.data(), ctx->disc.emeas, L.ne * sizeof(double), cudaMemcpyDeviceToHost));
+        double s = 0.0;
+        for (int64_t T = 0; T < L.ne; ++T) s += meas[T];
+        double inv = 1.0 / std::sqrt(s);
+        for (int64_t T = 0; T < L.ne; ++T) v[L.nf * L.b + T * L.nP] = std::sqrt(meas[T]) * inv;
+        HHO_TRY(upload(ctx, &C->nullv, v));
+    }
+    if (L.n <= ctx->coarse_dense_max) {
+        C->kind = 0;
+        const int64_t n = L.n;
+        double* A = nullptr;
+        HHO_TRY(dalloc(ctx, &A, (size_t)n * n));
+        HHO_TRY(dalloc(ctx, &C->Ainv, (size_t)n * n));
+        HHO_CUDA(cudaMemsetAsync(A, 0, (size_t)n * n * sizeof(double), ctx->stream));
+        k_dense_from_level<<<grid1d(n, 128), 128, 0, ctx->stream>>>(L.nf, L.ne, L.b, L.nP, L.ff_col, L.ff_nsl, L.fp_col,
+                                                                     L.pf_col, L.pf_nsl, L.ff, L.fp, L.pf, L.pp, A, n);
+        if (ctx->has_null) {
+            k_mean_abs_diag_dense<<<1, 32, 0, ctx->stream>>>(A, n, C->scal);
+            k_rank1<<<grid1d(n * n, 256), 256, 0, ctx->stream>>>(A, n, C->nullv, C->scal);
+        }
+        HHO_CUDA(cudaGetLastError());
+        hho_status st = dense_inverse(ctx, A, C->Ainv, n);
+        dfree(A);
+        return st;
+    }
+    C->kind = 1;
+    return build_dd(ctx, C);
+}
+
+hho_status coarse_apply(hho_ctx* ctx, const double* d, double* c) {
+    CoarseSolver* C = ctx->coarse;
+    if (C->kind == 0) {
+        k_gemv<<<grid1d(C->n * 32, 256), 256, 0, ctx->stream>>>(C->Ainv, C->n, d, c);
+        ++ctx->launches;
+    } else {
+        k_dd_gather<<<grid1d(C->nIt, 256), 256, 0, ctx->stream>>>(C->nIt, C->flat_glob, d, C->dI);
+        k_dd_yI<<<grid1d(C->nIt, 128), 128, 0, ctx->stream>>>(C->nIt, C->flat_sub, C->offI, C->nI, C->offA, C->AinvT,
+                                                              C->dI, C->yI);
+        k_dd_rG<<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(C->nG, C->gam_glob, C->g_ptr, C->g_s, C->g_j, C->nI,
+                                                                  C->offI, C->offAG, C->AGI, C->yI, d, C->rG);
+        k_gemv<<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(C->Ainv, C->nG, C->rG, C->cG);
+        k_dd_cI<<<grid1d(C->nIt, 128), 128, 0, ctx->stream>>>(C->nIt, C->flat_sub, C->flat_glob, C->offI, C->nI,
+                                                              C->nGs, C->offX, C->offGam, C->gam_list, C->XT, C->yI,
+                                                              C->cG, c);
+        k_dd_scatter_G<<<grid1d(C->nG, 256), 256, 0, ctx->stream>>>(C->nG, C->gam_glob, C->cG, c);
+        ctx->launches += 6;
+        if (C->nullv) {
+            k_null_dot<<<1, 256, 0, ctx->stream>>>(C->n, C->nullv, c, C->scal + 1);
+            k_null_sub<<<grid1d(C->n, 256), 256, 0, ctx->stream>>>(C->n, C->nullv, C->scal + 1, c);
+            ctx->launches += 2;
+        }
+    }
+    HHO_CUDA(cudaGetLastError());
+    ctx->coarse_its_total += 1;
+    return HHO_OK;
+}
+
+}  // namespace hho

@@ -81,7 +81,8 @@ struct Disc {
     // Gauss-Legendre tables on [0,1]
     double* gl = nullptr;         // [MAX_GL+1][MAX_GL] nodes then weights
     // host copies of topology
-    std::vector<int32_t> h_ef_ptr, h_ef, h_fe, h_flf;
+    std::vector<int32_t> h_ef_ptr, h_ef, h_fe, h_flf, h_fv_ptr, h_fv;
+    std::vector<double> h_xyz;
     std::vector<int8_t> h_fbc;
 };
 
@@ -117,7 +118,8 @@ struct Topo {
     std::vector<int32_t> h_ff_col, h_ff_nsl, h_fp_col, h_pf_col, h_pf_nsl;
 };
 
-struct Workspace;  // solver work vectors (solve.cu)
+struct Workspace;     // solver work vectors (solve.cu)
+struct CoarseSolver;  // coarse-level solver (coarse.cu)
 
 }  // namespace hho
 
@@ -133,19 +135,15 @@ struct hho_ctx {
     int smooth_its = 2;
     int prec = 0;
     std::vector<int> degrees;
-    // coarse solver
-    int coarse_kind = 0;                 // 0 = dense LU, 1 = block-Jacobi GMRES
-    double coarse_rtol = 1e-3;
-    int coarse_restart = 50, coarse_maxit = 1000;
-    double* lu = nullptr;                // dense LU factors (column-major n*n)
-    int32_t* piv = nullptr;
-    double* null_vec = nullptr;          // unit constant-pressure vector at the coarse level (or null)
-    double* null_vec0 = nullptr;         // same at level 0
+    double* null_vec0 = nullptr;         // unit constant-pressure vector at level 0 (or null)
     bool has_null = false;
     hho::Workspace* ws = nullptr;
+    hho::CoarseSolver* coarse = nullptr;
     int64_t coarse_its_total = 0;
     int* d_flag = nullptr;               // device status word for bounded waits / breakdowns
     int64_t launches = 0;                // kernels launched by the solver entry points
+    int64_t coarse_dense_max = 10000;    // options
+    int64_t dd_elements = 0;             // 0 = default per dimension
 };
 
 // ---- helpers shared across units ----
@@ -193,4 +191,8 @@ hho_status spmv(hho_ctx* ctx, int l, const double* x, double* y);
 hho_status vcycle(hho_ctx* ctx, const double* r, double* z);
 hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, hho_solve_info* info);
 void free_workspace(hho_ctx* ctx);
+// coarse.cu
+hho_status coarse_setup(hho_ctx* ctx);
+hho_status coarse_apply(hho_ctx* ctx, const double* d, double* c);
+void coarse_free(hho_ctx* ctx);
 }  // namespace hho

@@ -32,6 +32,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "dense.cuh"
 
 namespace hho {
 
@@ -291,53 +292,6 @@ __device__ void cta_mm(double* C, int ldc, const double* A, int lda, bool tA, co
 __device__ void cta_zero(double* A, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) A[i] = 0.0;
     __syncthreads();
-}
-
-// Gauss-Jordan with partial pivoting on the n x (n+m) row-major matrix W (ld):
-// on return the right block holds A^{-1} B.  Returns false on a zero pivot.
-__device__ bool cta_gauss_jordan(double* W, int ld, int n, int m, int* s_piv) {
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) s_ok = 1;
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-        if (threadIdx.x == 0) {
-            int p = j;
-            double best = fabs(W[j * ld + j]);
-            for (int i = j + 1; i < n; ++i) {
-                double v = fabs(W[i * ld + j]);
-                if (v > best) {
-                    best = v;
-                    p = i;
-                }
-            }
-            *s_piv = p;
-            if (best == 0.0) s_ok = 0;
-        }
-        __syncthreads();
-        if (!s_ok) return false;
-        int p = *s_piv;
-        if (p != j)
-            for (int c = threadIdx.x; c < n + m; c += blockDim.x) {
-                double t = W[j * ld + c];
-                W[j * ld + c] = W[p * ld + c];
-                W[p * ld + c] = t;
-            }
-        __syncthreads();
-        double inv = 1.0 / W[j * ld + j];
-        __syncthreads();
-        for (int c = threadIdx.x; c < n + m; c += blockDim.x) W[j * ld + c] *= inv;
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < n * (n + m); idx += blockDim.x) {
-            int i = idx / (n + m), c = idx % (n + m);
-            if (i == j || c == j) continue;
-            W[i * ld + c] -= W[i * ld + j] * W[j * ld + c];
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x)
-            if (i != j) W[i * ld + j] = 0.0;
-        __syncthreads();
-    }
-    return true;
 }
 
 // Modified Gram-Schmidt applied twice in the Gram metric G (n x n): rows of C.
@@ -1402,6 +1356,9 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
     std::vector<int32_t> h_fv_ptr(D.nf + 1), h_fv(m->face_vert_ptr[D.nf]);
     for (int64_t i = 0; i <= D.nf; ++i) h_fv_ptr[i] = (int32_t)m->face_vert_ptr[i];
     for (int64_t i = 0; i < (int64_t)h_fv.size(); ++i) h_fv[i] = (int32_t)m->face_vert[i];
+    D.h_fv_ptr = h_fv_ptr;
+    D.h_fv = h_fv;
+    D.h_xyz.assign(m->xyz, m->xyz + D.nv * d);
     D.h_fe.resize(2 * D.nf);
     for (int64_t i = 0; i < 2 * D.nf; ++i) D.h_fe[i] = (int32_t)m->face_elem[i];
     D.h_fbc.assign(m->face_bc, m->face_bc + D.nf);

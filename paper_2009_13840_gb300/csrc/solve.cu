@@ -360,134 +360,6 @@ __global__ void k_gs_solve(double* sc, GS L) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// Dense coarse inverse (Gauss-Jordan with partial pivoting, row-major n x n)
-// ---------------------------------------------------------------------------
-__global__ void k_dense_from_level(LevelView L, double* __restrict__ A, int64_t n) {
-    const int64_t nfr = L.nf * L.b, ner = L.ne * L.nP;
-    const int b = L.b, nP = L.nP;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < nfr) {
-            int r = (int)(i / L.nf);
-            int64_t F = i % L.nf, row = F * b + r;
-            for (int s = 0; s < L.ff_nsl[F]; ++s) {
-                int64_t G = L.ff_col[s * L.nf + F];
-                for (int c = 0; c < b; ++c) A[row * n + G * b + c] = L.ff[(((int64_t)s * b + c) * b + r) * L.nf + F];
-            }
-            for (int p = 0; p < 2; ++p) {
-                int T = L.fp_col[p * L.nf + F];
-                if (T < 0) continue;
-                for (int c = 0; c < nP; ++c)
-                    A[row * n + nfr + (int64_t)T * nP + c] = L.fp[(((int64_t)p * nP + c) * b + r) * L.nf + F];
-            }
-        } else {
-            int64_t j = i - nfr;
-            int r = (int)(j / L.ne);
-            int64_t T = j % L.ne, row = nfr + T * nP + r;
-            for (int f = 0; f < L.pf_nsl[T]; ++f) {
-                int64_t G = L.pf_col[f * L.ne + T];
-                for (int c = 0; c < b; ++c) A[row * n + G * b + c] = L.pf[(((int64_t)f * b + c) * nP + r) * L.ne + T];
-            }
-            for (int c = 0; c < nP; ++c) A[row * n + nfr + T * nP + c] = L.pp[((int64_t)c * nP + r) * L.ne + T];
-        }
-    }
-}
-
-// alpha = mean |diag A| (one block, fixed order)
-__global__ void k_mean_abs_diag(const double* __restrict__ A, int64_t n, double* __restrict__ alpha) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int64_t i = 0; i < n; ++i) s += fabs(A[i * n + i]);
-        *alpha = s / (double)n;
-    }
-}
-
-// A += alpha * nv nv^T
-__global__ void k_rank1(double* __restrict__ A, int64_t n, const double* __restrict__ nv, const double* __restrict__ alpha) {
-    double a = *alpha;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * n; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = i / n, c = i % n;
-        if (nv[r] != 0.0 && nv[c] != 0.0) A[i] += a * nv[r] * nv[c];
-    }
-}
-
-__global__ void k_eye(double* __restrict__ A, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * n; i += (int64_t)gridDim.x * blockDim.x)
-        A[i] = (i / n == i % n) ? 1.0 : 0.0;
-}
-
-__global__ void k_gj_pivot(double* __restrict__ A, double* __restrict__ Ai, int64_t n, int64_t j, double* __restrict__ f,
-                           int* __restrict__ status) {
-    __shared__ double bv[256];
-    __shared__ int64_t bi[256];
-    double best = -1.0;
-    int64_t arg = j;
-    for (int64_t i = j + threadIdx.x; i < n; i += blockDim.x) {
-        double v = fabs(A[i * n + j]);
-        if (v > best) {
-            best = v;
-            arg = i;
-        }
-    }
-    bv[threadIdx.x] = best;
-    bi[threadIdx.x] = arg;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int t = 1; t < (int)blockDim.x; ++t)
-            if (bv[t] > bv[0] || (bv[t] == bv[0] && bi[t] < bi[0])) {
-                bv[0] = bv[t];
-                bi[0] = bi[t];
-            }
-        if (bv[0] <= 0.0) atomicExch(status, (int)HHO_ERR_SINGULAR);
-    }
-    __syncthreads();
-    int64_t p = bi[0];
-    if (p != j)
-        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
-            double t = A[j * n + c];
-            A[j * n + c] = A[p * n + c];
-            A[p * n + c] = t;
-            t = Ai[j * n + c];
-            Ai[j * n + c] = Ai[p * n + c];
-            Ai[p * n + c] = t;
-        }
-    __syncthreads();
-    double piv = A[j * n + j];
-    double inv = (piv == 0.0) ? 0.0 : 1.0 / piv;
-    __syncthreads();
-    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
-        A[j * n + c] *= inv;
-        Ai[j * n + c] *= inv;
-    }
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) f[i] = (i == j) ? 0.0 : A[i * n + j];
-}
-
-__global__ void k_gj_elim(double* __restrict__ A, double* __restrict__ Ai, int64_t n, int64_t j,
-                          const double* __restrict__ f) {
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * n * n;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t k = idx % (n * n);
-        int64_t i = k / n, c = k % n;
-        double fi = f[i];
-        if (fi == 0.0) continue;
-        if (idx < n * n) A[k] -= fi * A[j * n + c];
-        else Ai[k] -= fi * Ai[j * n + c];
-    }
-}
-
-// y = A x (row-major dense), one warp per row
-__global__ void k_gemv(const double* __restrict__ A, int64_t n, const double* __restrict__ x, double* __restrict__ y) {
-    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    for (int64_t r = w; r < n; r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        double s = 0.0;
-        for (int64_t c = lane; c < n; c += 32) s += A[r * n + c] * x[c];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) y[r] = s;
-    }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -503,9 +375,6 @@ struct Workspace {
     // FGMRES
     int restart = 0;
     double *fV = nullptr, *fZ = nullptr, *fw = nullptr, *fr = nullptr, *fsc = nullptr;
-    // coarse GMRES
-    double *cV = nullptr, *cZ = nullptr, *cw = nullptr, *csc = nullptr;
-    double* Ainv = nullptr;
     double* h_sc = nullptr;  // pinned host scalars
 };
 
@@ -527,11 +396,6 @@ void free_workspace(hho_ctx* ctx) {
     dfree(W->fw);
     dfree(W->fr);
     dfree(W->fsc);
-    dfree(W->cV);
-    dfree(W->cZ);
-    dfree(W->cw);
-    dfree(W->csc);
-    dfree(W->Ainv);
     if (W->h_sc) cudaFreeHost(W->h_sc);
     delete W;
     ctx->ws = nullptr;
@@ -636,74 +500,9 @@ static hho_status host_read(hho_ctx* ctx, const double* dsrc, double* hdst, int 
     return HHO_OK;
 }
 
-// Right-preconditioned GMRES(restart) from x = 0 to ||r|| <= rtol ||b|| on level l
-// with the block-Jacobi preconditioner (coarse solver for large coarse levels).
-static hho_status coarse_gmres(hho_ctx* ctx, int l, const double* bv, double* x, int* its_out) {
-    const LevelMat& L = ctx->levels[l];
-    Workspace* W = ctx->ws;
-    const int64_t n = L.n;
-    const int m = ctx->coarse_restart;
-    GS G = gs_layout(m);
-    double* sc = W->csc;
-    double* hs = W->h_sc;
-    k_zero<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x);
-    ++ctx->launches;
-    HHO_TRY(mdot(ctx, n, bv, n, 1, bv, sc + 0));
-    HHO_TRY(host_read(ctx, sc, hs, 1));
-    double bnorm = std::sqrt(hs[0]);
-    int it = 0;
-    if (bnorm == 0.0) {
-        *its_out = 0;
-        return HHO_OK;
-    }
-    k_copy<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, bv, W->cw);
-    ++ctx->launches;
-    double* r = W->cw;
-    bool done = false;
-    while (it < ctx->coarse_maxit && !done) {
-        HHO_TRY(mdot(ctx, n, r, n, 1, r, sc + 0));
-        k_gs_start<<<1, 1, 0, ctx->stream>>>(sc, G);
-        ++ctx->launches;
-        HHO_TRY(host_read(ctx, sc + 1, hs, 1));
-        if (hs[0] <= ctx->coarse_rtol * bnorm) break;
-        k_scale<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, r, W->cV, sc + 1);
-        ++ctx->launches;
-        int j = 0;
-        for (; j < m; ++j) {
-            HHO_TRY(jacobi(ctx, l, W->cV + (int64_t)j * n, W->cZ + (int64_t)j * n));
-            HHO_TRY(spmv(ctx, l, W->cZ + (int64_t)j * n, r));
-            HHO_TRY(arnoldi_finish(ctx, n, W->cV, r, sc, G, j));
-            ++it;
-            HHO_TRY(host_read(ctx, sc + 3, hs, 2));
-            if (hs[0] <= ctx->coarse_rtol * bnorm || hs[1] != 0.0 || it >= ctx->coarse_maxit) {
-                done = hs[0] <= ctx->coarse_rtol * bnorm;
-                break;
-            }
-        }
-        k_gs_solve<<<1, 1, 0, ctx->stream>>>(sc, G);
-        ++ctx->launches;
-        k_combine<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x, 1.0, W->cZ, n, (int)std::min(j + 1, m), sc + G.y, 1.0);
-        ++ctx->launches;
-        HHO_TRY(residual(ctx, l, x, bv, r));
-    }
-    *its_out = it;
-    HHO_CUDA(cudaGetLastError());
-    return HHO_OK;
-}
-
 static hho_status coarse_solve(hho_ctx* ctx, int l, const double* d, double* c) {
-    const LevelMat& L = ctx->levels[l];
-    if (ctx->coarse_kind == 0) {
-        k_gemv<<<grid1d(L.n * 32, 256), 256, 0, ctx->stream>>>(ctx->ws->Ainv, L.n, d, c);
-        ++ctx->launches;
-        HHO_CUDA(cudaGetLastError());
-        ctx->coarse_its_total += 1;
-        return HHO_OK;
-    }
-    int its = 0;
-    HHO_TRY(coarse_gmres(ctx, l, d, c, &its));
-    ctx->coarse_its_total += its;
-    return HHO_OK;
+    (void)l;
+    return coarse_apply(ctx, d, c);
 }
 
 // MG_V(l, b, w) with the iterate held in lv[l].x (zero initial guess when x_zero).
@@ -786,57 +585,7 @@ hho_status pmg_build(hho_ctx* ctx) {
         HHO_TRY(dalloc(ctx, &ctx->null_vec0, v.size()));
         HHO_CUDA(cudaMemcpy(ctx->null_vec0, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
-    // coarse solver
-    const LevelMat& Lc = ctx->levels[nl - 1];
-    ctx->coarse_kind = (Lc.n <= 10000) ? 0 : 1;
-    if (ctx->coarse_kind == 0) {
-        const int64_t n = Lc.n;
-        double *A = nullptr, *f = nullptr;
-        HHO_TRY(dalloc(ctx, &A, (size_t)n * n));
-        HHO_TRY(dalloc(ctx, &W->Ainv, (size_t)n * n));
-        HHO_TRY(dalloc(ctx, &f, n));
-        HHO_CUDA(cudaMemsetAsync(A, 0, (size_t)n * n * sizeof(double), ctx->stream));
-        k_dense_from_level<<<grid1d(n, 128), 128, 0, ctx->stream>>>(view(Lc), A, n);
-        ++ctx->launches;
-        if (ctx->has_null) {
-            auto v = null_vector_host(ctx, Lc);
-            double* dv = nullptr;
-            HHO_TRY(dalloc(ctx, &dv, n + 1));
-            HHO_CUDA(cudaMemcpy(dv, v.data(), n * sizeof(double), cudaMemcpyHostToDevice));
-            k_mean_abs_diag<<<1, 32, 0, ctx->stream>>>(A, n, dv + n);
-            ++ctx->launches;
-            k_rank1<<<grid1d(n * n, 256), 256, 0, ctx->stream>>>(A, n, dv, dv + n);
-            ++ctx->launches;
-            HHO_CUDA(cudaStreamSynchronize(ctx->stream));
-            dfree(dv);
-        }
-        k_eye<<<grid1d(n * n, 256), 256, 0, ctx->stream>>>(W->Ainv, n);
-        ++ctx->launches;
-        HHO_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
-        for (int64_t j = 0; j < n; ++j) {
-            k_gj_pivot<<<1, 256, 0, ctx->stream>>>(A, W->Ainv, n, j, f, ctx->d_flag);
-            ++ctx->launches;
-            k_gj_elim<<<grid1d(2 * n * n, 256), 256, 0, ctx->stream>>>(A, W->Ainv, n, j, f);
-            ++ctx->launches;
-        }
-        int flag = 0;
-        HHO_CUDA(cudaGetLastError());
-        HHO_CUDA(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-        HHO_CUDA(cudaStreamSynchronize(ctx->stream));
-        dfree(A);
-        dfree(f);
-        if (flag) {
-            ctx->err = "pmg_setup: singular coarse operator";
-            return HHO_ERR_SINGULAR;
-        }
-    } else {
-        const int64_t n = Lc.n;
-        const int mc = ctx->coarse_restart;
-        HHO_TRY(dalloc(ctx, &W->cV, (size_t)(mc + 1) * n));
-        HHO_TRY(dalloc(ctx, &W->cZ, (size_t)mc * n));
-        HHO_TRY(dalloc(ctx, &W->cw, n));
-        HHO_TRY(dalloc(ctx, &W->csc, gs_layout(mc).total));
-    }
+    HHO_TRY(coarse_setup(ctx));
     return HHO_OK;
 }
 

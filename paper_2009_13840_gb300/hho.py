@@ -26,7 +26,8 @@ NODES = {"elem": 0, "face": 1}
 # every entry point declared in include/hho.h
 SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "pmg_setup", "pmg_vcycle", "hho_spmv",
            "hho_solve", "hho_recover", "hho_errors", "hho_get_element_schur", "hho_get_level_coo",
-           "hho_set_element_schur", "hho_launch_count", "hho_destroy", "hho_last_error"]
+           "hho_set_element_schur", "hho_launch_count", "hho_set_option", "hho_destroy",
+           "hho_last_error"]
 
 
 class HHOError(RuntimeError):
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
         "hho_get_level_coo": (C.c_int, [P, C.c_int, P, P, P, C.POINTER(C.c_int64)]),
         "hho_set_element_schur": (C.c_int, [P, P]),
         "hho_launch_count": (C.c_int, [P, C.POINTER(C.c_int64)]),
+        "hho_set_option": (C.c_int, [P, C.c_char_p, C.c_double]),
         "hho_destroy": (C.c_int, [P]),
         "hho_last_error": (C.c_char_p, [P]),
     }
@@ -212,6 +214,9 @@ class Context:
         out = (C.c_double * 4)()
         self._check(self.lib.hho_errors(self.h, _ptr(local), _ptr(u), _ptr(gu), _ptr(p), out))
         return dict(u=out[0], gu=out[1], p=out[2], div=out[3])
+
+    def set_option(self, key: str, value: float):
+        self._check(self.lib.hho_set_option(self.h, key.encode(), float(value)))
 
     def launch_count(self) -> int:
         n = C.c_int64()
