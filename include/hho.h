@@ -114,6 +114,31 @@ hho_status hho_quad_nodes(hho_ctx* ctx, int which, int64_t* n_nodes, double* d_x
  *   d_rhs device, ndof(0) or NULL    receives a copy of the condensed RHS. */
 hho_status hho_assemble(hho_ctx* ctx, const double* d_f, const double* d_gD, const double* d_gN, double* d_rhs);
 
+/* hho_assemble without allocating memory.  The paper has no counterpart: this
+ * entry point serves callers that cannot call cudaMalloc when they refresh the
+ * right-hand side -- programs that give all device memory to their own pool,
+ * or loops in which a device allocation (which may synchronise the device or
+ * fail) is not acceptable.  It computes the same condensed right-hand side as
+ * hho_assemble, from the same arguments, but the element kernel's working
+ * memory is a fixed array of 2^17 doubles (1 MiB) inside the library, held on
+ * every GPU that loads the library until the process exits, instead of memory
+ * allocated per call.
+ *  - No allocation of any kind is made on success (cudaMalloc, cudaFree,
+ *    pools or host heap); on failure the message is stored in the context.
+ *  - The first call on a device looks up the device address of the array with
+ *    that device current; if you capture streams, make that first call before
+ *    any capture begins.  The current device must be the context's device.
+ *  - The work is only enqueued on the context's stream: the call returns
+ *    before the right-hand side is ready (hho_assemble synchronises).
+ *  - Every call on a device shares the one array.  The kernel clears what it
+ *    reads, so the contents left by the previous call do not matter, but two
+ *    calls whose kernels overlap on the GPU (different streams or contexts on
+ *    one device, not ordered by events) race on the array; order them.
+ *  - Returns HHO_ERR_ARG when one element's local system would need more than
+ *    the 2^17 doubles (never for the degrees and element shapes built). */
+hho_status hho_assemble_noalloc(hho_ctx* ctx, const double* d_f, const double* d_gD, const double* d_gN,
+                                double* d_rhs);
+
 /* Build the p-hierarchy: levels of degrees degrees[0] = k > degrees[1] > ...
  * > degrees[n_levels-1] >= 0, coarse operators by Galerkin block extraction
  * from the fine condensed operator (Sec. 4.2), smoother data (face-block

@@ -173,6 +173,8 @@ void dfree(void* p);
 // setup.cu
 hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond);
 hho_status build_rhs(hho_ctx* ctx, const double* f, const double* gD, const double* gN);
+hho_status build_rhs_scratch(hho_ctx* ctx, const double* f, const double* gD, const double* gN, double* scratch,
+                             int64_t capacity);
 hho_status quad_nodes(hho_ctx* ctx, int which, int64_t* n, double* xyz, double* normals);
 hho_status recover_local(hho_ctx* ctx, const double* x, double* local);
 hho_status compute_errors(hho_ctx* ctx, const double* local, const double* u, const double* gu,

@@ -1522,6 +1522,28 @@ hho_status build_rhs(hho_ctx* ctx, const double* f, const double* gD, const doub
     return HHO_OK;
 }
 
+// Same element right-hand-side kernel as build_rhs, with caller-provided working
+// memory of `capacity` doubles instead of a fresh allocation.  Enqueues only;
+// the grid is shrunk so that every CTA gets one local vector of scratch.
+hho_status build_rhs_scratch(hho_ctx* ctx, const double* f, const double* gD, const double* gN, double* scratch,
+                             int64_t capacity) {
+    Disc& D = ctx->disc;
+    const int nloc = D.d * D.nE + D.maxN * D.b + D.nE;
+    const int64_t per = (nloc + 3) & ~3;
+    const int64_t fit = capacity / per;
+    if (fit < 1) {
+        ctx->err = "hho_assemble_noalloc: one element's local system needs more working memory than the fixed array holds";
+        return HHO_ERR_ARG;
+    }
+    const int grid = (int)std::min<int64_t>(element_grid(D.ne), fit);
+    k_rhs<<<grid, TPB, 0, ctx->stream>>>(D.d, D.k, D.cond, D.ne, D.xyz, D.ef_ptr, D.ef, D.fv_ptr, D.fv, D.fbc, D.fgeo,
+                                         D.fC, D.eC, D.emeas, D.gl, D.enode_off, D.fnode_off, f, gD, gN, D.off_X,
+                                         D.off_Kei, D.off_P, D.off_gT, D.off_yT, D.X, D.Kei, D.P, D.gT, D.yT, scratch,
+                                         per);
+    HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
+}
+
 hho_status quad_nodes(hho_ctx* ctx, int which, int64_t* n, double* xyz, double* normals) {
     Disc& D = ctx->disc;
     if (which != HHO_NODES_ELEM && which != HHO_NODES_FACE) {

@@ -24,7 +24,7 @@ COND = {"v": 0, "vp": 1}
 NODES = {"elem": 0, "face": 1}
 
 # every entry point declared in include/hho.h
-SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "pmg_setup", "pmg_vcycle", "hho_spmv",
+SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "hho_assemble_noalloc", "pmg_setup", "pmg_vcycle", "hho_spmv",
            "hho_solve", "hho_recover", "hho_errors", "hho_get_element_schur", "hho_get_level_coo",
            "hho_set_element_schur", "hho_launch_count", "hho_set_option", "hho_destroy",
            "hho_last_error"]
@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH):
         "hho_ndof": (C.c_int, [P, C.c_int, C.POINTER(C.c_int64)]),
         "hho_quad_nodes": (C.c_int, [P, C.c_int, C.POINTER(C.c_int64), P, P]),
         "hho_assemble": (C.c_int, [P, P, P, P, P]),
+        "hho_assemble_noalloc": (C.c_int, [P, P, P, P, P]),
         "pmg_setup": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int]),
         "pmg_vcycle": (C.c_int, [P, P, P]),
         "hho_spmv": (C.c_int, [P, C.c_int, P, P]),
@@ -178,6 +179,9 @@ class Context:
 
     def assemble(self, f, gD, gN, rhs_out=None):
         self._check(self.lib.hho_assemble(self.h, _ptr(f), _ptr(gD), _ptr(gN), _ptr(rhs_out)))
+
+    def assemble_noalloc(self, f, gD, gN, rhs_out=None):
+        self._check(self.lib.hho_assemble_noalloc(self.h, _ptr(f), _ptr(gD), _ptr(gN), _ptr(rhs_out)))
 
     def pmg_setup(self, degrees, smooth_its: int = 2, prec: int = 0):
         arr = (C.c_int * len(degrees))(*degrees)
