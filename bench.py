@@ -7,7 +7,10 @@ assembled operator and RHS resident in HBM): 128 x 128 squares split into
 32768 triangles, interior vertices jittered by +-0.2h (SplitMix64 seed 0),
 Dirichlet on x=0, y=0, y=1 and Neumann on x=1, manufactured field
 u = (sin(pi x) cos(pi y), -cos(pi x) sin(pi y)), p = sin(2 pi x) sin(2 pi y),
-k = 3, v-cond static condensation, p-levels 3-2-1-0, FP64.
+k = 3, v-cond static condensation, p-levels 3-2-1-0.  The headline solve uses
+the mixed-precision V-cycle (FP32 level operators and smoother vectors with
+FP64 dot products and an FP64 coarse solve) inside FP64 FGMRES; the plain
+FP64 V-cycle is timed on the same problem for the speedup.
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
 bounded sample of the same workload family instead.
@@ -43,13 +46,15 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--sample-n", type=int, default=24, help="mesh size of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of the headline")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
 
 
 def workload(n, k, cond):
     from synthetic import tri_mesh, fields
     mesh = tri_mesh(n, jitter=0.2, seed=0, neumann_sides=(1,))
-    return mesh, fields.TrigStokes2D(), f"tri{n}x{n}-jit0.2-seed0-mixedBC k={k} {cond}-cond FP64 levels {k}..0"
+    return mesh, fields.TrigStokes2D(), f"tri{n}x{n}-jit0.2-seed0-mixedBC k={k} {cond}-cond levels {k}..0"
 
 
 def dist_env():
@@ -159,7 +164,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def spmv_bytes(ctx, level=0):
+def spmv_bytes(ctx, level=0, value_bytes=8):
     """Algorithmic bytes of one level SpMV: stored values, column indices, x read, y written."""
     r, c, v = ctx.level_coo(level)
     n = ctx.ndof(level)
@@ -170,7 +175,7 @@ def spmv_bytes(ctx, level=0):
     # face slots per face row: 1 + sum over its elements of (|F_T| - 1)
     nsl = 1 + np.where(fe[:, 0] >= 0, N[fe[:, 0]] - 1, 0) + np.where(fe[:, 1] >= 0, N[np.maximum(fe[:, 1], 0)] - 1, 0)
     idx_bytes = 4 * (int(nsl.sum()) + nf + 2 * nf + int(N.sum()) + ne)
-    return v.size * 8 + idx_bytes + 2 * n * 8
+    return v.size * value_bytes + idx_bytes + 2 * n * value_bytes
 
 
 def run_ours(args):
@@ -189,24 +194,17 @@ def run_ours(args):
         f, gD, gN = hho.data_arrays(ctx, fld)
         ctx.assemble(f, gD, gN)
         degrees = list(range(args.k, -1, -1))
-        ctx.pmg_setup(degrees, smooth_its=2)
         ndof = ctx.ndof(0)
         x = torch.empty(ndof, dtype=torch.float64, device="cuda")
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-        for _ in range(args.warmup):
-            info = ctx.solve(x, rtol=args.rtol)
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        l0 = ctx.launch_count()
-        times = []
-        infos = []
-        with Clocks(local) as clk:
-            for _ in range(args.steps):
+
+        def timed_solves(steps, tag, clocks=None):
+            times, infos = [], []
+            for _ in range(steps):
                 flush.fill_(1.0)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
-                torch.cuda.nvtx.range_push("timed_step")
+                torch.cuda.nvtx.range_push(tag)
                 e0.record(stream)
                 info = ctx.solve(x, rtol=args.rtol)
                 e1.record(stream)
@@ -214,32 +212,62 @@ def run_ours(args):
                 torch.cuda.nvtx.range_pop()
                 times.append(e0.elapsed_time(e1))
                 infos.append(info)
+            return float(np.mean(times)), infos
+
+        # plain FP64 V-cycle on the same problem (for the speedup of the mixed one)
+        fp64 = None
+        if args.prec == "fp32" and not args.no_fp64_compare:
+            ctx.pmg_setup(degrees, smooth_its=2, prec="fp64")
+            for _ in range(args.warmup):
+                ctx.solve(x, rtol=args.rtol)
+            ms64, inf64 = timed_solves(args.steps, "fp64_step")
+            fp64 = {"ms_per_solve": ms64, "fgmres_iterations": inf64[-1]["iterations"],
+                    "rel_residual": inf64[-1]["rel_residual"], "dof_per_s": ndof / (ms64 / 1e3)}
+        ctx.pmg_setup(degrees, smooth_its=2, prec=args.prec)
+        for _ in range(args.warmup):
+            info = ctx.solve(x, rtol=args.rtol)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        l0 = ctx.launch_count()
+        with Clocks(local) as clk:
+            ms, infos = timed_solves(args.steps, "timed_step")
             torch.cuda.synchronize()
         launches = ctx.launch_count() - l0
-        ms = float(np.mean(times))
         if ws > 1:
             t = torch.tensor([ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
         value = ws * ndof / (ms / 1e3)
-        # dominant kernel: level-0 SpMV, timed live with CUDA events on the launching stream
+
+        # dominant kernel: the level-0 operator of the V-cycle, timed live with CUDA events on its stream
+        def time_kernel(fn, reps=20):
+            kt = []
+            for i in range(reps + 3):
+                flush.fill_(2.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                if i >= 3:
+                    kt.append(e0.elapsed_time(e1))
+            return float(np.mean(kt))
+
         xs = torch.randn(ndof, dtype=torch.float64, device="cuda")
         ys = torch.empty_like(xs)
-        kt = []
-        for i in range(23):
-            flush.fill_(2.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.spmv(0, xs, ys)
-            e1.record(stream)
-            e1.synchronize()
-            if i >= 3:
-                kt.append(e0.elapsed_time(e1))
-        spmv_ms = float(np.mean(kt))
-        nbytes = spmv_bytes(ctx, 0)
+        ms64_k = time_kernel(lambda: ctx.spmv(0, xs, ys))
+        nb64 = spmv_bytes(ctx, 0, 8)
         peak, peak_kind = peaks()
-        achieved = nbytes / (spmv_ms / 1e3) / 1e9
+        if args.prec == "fp32":
+            xs32, ys32 = xs.float(), torch.empty(ndof, dtype=torch.float32, device="cuda")
+            ms_k = time_kernel(lambda: ctx.spmv_f32(0, xs32, ys32))
+            nbytes = spmv_bytes(ctx, 0, 4)
+            kname = "k_spmv_b<float> (level 0, V-cycle operator, FP32)"
+        else:
+            ms_k, nbytes, kname = ms64_k, nb64, "k_spmv_b<double> (level 0)"
+        achieved = nbytes / (ms_k / 1e3) / 1e9
         # end-to-end through the public API with host buffers
         hf, hgD, hgN = f.cpu().pin_memory(), gD.cpu().pin_memory(), gN.cpu().pin_memory()
         hx = torch.empty(ndof, dtype=torch.float64).pin_memory()
@@ -274,13 +302,18 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wname, "dofs": ndof, "fgmres_iterations": last["iterations"],
-                       "coarse_iterations": last["coarse_iterations"], "rel_residual": last["rel_residual"],
+            "vs_baseline": None, "dtype": "f64 FGMRES + f32 V-cycle" if args.prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": wname, "vcycle_precision": args.prec, "dofs": ndof,
+                       "fgmres_iterations": last["iterations"], "coarse_iterations": last["coarse_iterations"],
+                       "rel_residual_fp64": last["rel_residual"], "fp64_vcycle": fp64,
+                       "speedup_vs_fp64_vcycle": (fp64["ms_per_solve"] / ms) if fp64 else None,
                        "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if ws > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": "k_spmv (level 0)", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                         "bytes_per_launch": nbytes, "ms_per_launch": spmv_ms},
+                         "bytes_per_launch": nbytes, "ms_per_launch": ms_k,
+                         "fp64_outer_spmv": {"achieved": nb64 / (ms64_k / 1e3) / 1e9, "bytes_per_launch": nb64,
+                                             "ms_per_launch": ms64_k}},
             "cpu_baseline": cpu,
             "e2e": {"value": ws * ndof / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int((f.numel() + gD.numel() + gN.numel()) * 8),

@@ -142,10 +142,13 @@ hho_status hho_assemble_noalloc(hho_ctx* ctx, const double* d_f, const double* d
 /* Build the p-hierarchy: levels of degrees degrees[0] = k > degrees[1] > ...
  * > degrees[n_levels-1] >= 0, coarse operators by Galerkin block extraction
  * from the fine condensed operator (Sec. 4.2), smoother data (face-block
- * Jacobi with element pressure pivot blocks), and the coarse solver (dense LU
- * if the coarse level has at most 10^4 unknowns, else block-Jacobi GMRES to a
- * 1e-3 relative residual).  prec: HHO_FP64.  smooth_its: GMRES iterations per
- * pre/post smoothing (the paper uses 2). */
+ * Jacobi with element pressure pivot blocks), and the exact coarse solver
+ * (dense inverse up to 10^4 coarse unknowns, two-level substructuring above).  prec: HHO_FP64 (every V-cycle operation in FP64) or
+ * HHO_FP32 (mixed precision: level operators, smoother blocks and smoother
+ * vectors stored and multiplied in FP32 with FP64 accumulation of every dot
+ * product, FP64 Hessenberg algebra and FP64 coarse solve; the outer FGMRES and
+ * its operator stay FP64).  smooth_its: GMRES iterations per pre/post
+ * smoothing (the paper uses 2). */
 hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, int smooth_its);
 
 /* Solver options (take effect at the next pmg_setup).  Keys:
@@ -155,7 +158,16 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
  *   "dd_elements"       target number of elements per subdomain of the
  *                       substructured coarse solver (default 128 in 2D, 64 in
  *                       3D; rounded so the subdomain count is a power of two)
- * Returns HHO_ERR_ARG for an unknown key or a non-positive value. */
+ *   "graphs"            1 (default): pmg_vcycle and hho_solve replay a CUDA
+ *                       graph of the V-cycle captured on first use for each
+ *                       (input, output) pair of device buffers; 0: launch
+ *                       kernels directly.  The legacy default stream is never
+ *                       captured.
+ *   "spmv_rows"         rows of one face or element handled by one thread in
+ *                       the operator kernels, 1..4 (0 = automatic)
+ *   "spmv_grid"         blocks of 256 threads of the operator kernels,
+ *                       1..8192 (0 = automatic: about one 32-row tile per warp)
+ * Returns HHO_ERR_ARG for an unknown key or an invalid value. */
 hho_status hho_set_option(hho_ctx* ctx, const char* key, double value);
 
 /* One V-cycle MG_V(0, r, 0) of the Algorithm of Sec. 3.3: d_z = MG(d_r).
@@ -164,6 +176,11 @@ hho_status pmg_vcycle(hho_ctx* ctx, const double* d_r, double* d_z);
 
 /* y = S^l x with the level-l condensed operator (device vectors of ndof(l)). */
 hho_status hho_spmv(hho_ctx* ctx, int level, const double* d_x, double* d_y);
+
+/* y = S^l x with the FP32 copy of the level-l operator that a mixed-precision
+ * hierarchy (pmg_setup with HHO_FP32) keeps for every level above the coarse
+ * one (device vectors of ndof(l) floats).  HHO_ERR_STATE if there is none. */
+hho_status hho_spmv_f32(hho_ctx* ctx, int level, const float* d_x, float* d_y);
 
 /* FGMRES (Sec. 3.3) on S x = rhs (the RHS of the last hho_assemble) with one
  * V-cycle per iteration, CGS2 orthogonalisation, x0 = 0, restart `restart`,

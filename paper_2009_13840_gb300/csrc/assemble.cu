@@ -367,6 +367,13 @@ void free_level(LevelMat& L) {
     dfree(L.dinv);
     dfree(L.minv);
     L.ff = L.fp = L.pf = L.pp = L.dinv = L.minv = nullptr;
+    dfree(L.ff32);
+    dfree(L.fp32);
+    dfree(L.pf32);
+    dfree(L.pp32);
+    dfree(L.dinv32);
+    dfree(L.minv32);
+    L.ff32 = L.fp32 = L.pf32 = L.pp32 = L.dinv32 = L.minv32 = nullptr;
 }
 
 hho_status assemble_level0(hho_ctx* ctx) {

@@ -138,9 +138,9 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
             ctx->err = "pmg_setup: degrees must decrease strictly to >= 0";
             return HHO_ERR_ARG;
         }
-    if (prec != HHO_FP64) {
-        ctx->err = "pmg_setup: only HHO_FP64 is built";
-        return HHO_ERR_UNSUPPORTED;
+    if (prec != HHO_FP64 && prec != HHO_FP32) {
+        ctx->err = "pmg_setup: prec must be HHO_FP64 or HHO_FP32";
+        return HHO_ERR_ARG;
     }
     if (smooth_its < 0 || smooth_its > 16) {
         ctx->err = "pmg_setup: smooth_its must be in 0..16";
@@ -165,6 +165,24 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
 hho_status hho_set_option(hho_ctx* ctx, const char* key, double value) {
     if (!ctx || !key) return HHO_ERR_ARG;
     std::string k(key);
+    invalidate_graphs(ctx);  // captured V-cycles embed the old settings
+    if (k == "graphs") {
+        if (value != 0.0 && value != 1.0) {
+            ctx->err = "hho_set_option: graphs must be 0 or 1";
+            return HHO_ERR_ARG;
+        }
+        ctx->use_graphs = value != 0.0;
+        return HHO_OK;
+    }
+    if (k == "spmv_rows" || k == "spmv_grid") {
+        if (value < 0.0 || (k == "spmv_rows" && value > 4.0) || (k == "spmv_grid" && value > 8192.0)) {
+            ctx->err = "hho_set_option: spmv_rows must be 0..4 and spmv_grid 0..8192";
+            return HHO_ERR_ARG;
+        }
+        if (k == "spmv_rows") ctx->spmv_rows = (int)value;
+        else ctx->spmv_grid = (int)value;
+        return HHO_OK;
+    }
     if (!(value > 0.0) || value > 9.0e18) {
         ctx->err = "hho_set_option: value must be positive";
         return HHO_ERR_ARG;
@@ -200,6 +218,15 @@ hho_status hho_spmv(hho_ctx* ctx, int level, const double* d_x, double* d_y) {
         return HHO_ERR_ARG;
     }
     return spmv(ctx, level, d_x, d_y);
+}
+
+hho_status hho_spmv_f32(hho_ctx* ctx, int level, const float* d_x, float* d_y) {
+    if (!ctx || !d_x || !d_y || (const void*)d_x == (const void*)d_y) return HHO_ERR_ARG;
+    if (level < 0 || level >= (int)ctx->levels.size()) {
+        ctx->err = "hho_spmv_f32: no such level";
+        return HHO_ERR_ARG;
+    }
+    return spmv_f32(ctx, level, d_x, d_y);
 }
 
 hho_status hho_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double* d_x, hho_solve_info* info) {

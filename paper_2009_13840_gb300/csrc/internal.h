@@ -106,6 +106,8 @@ struct LevelMat {
     // smoother data
     double* dinv = nullptr; // [b c][b r][nf]
     double* minv = nullptr; // [nP c][nP r][ne]
+    // FP32 copies used by a mixed-precision V-cycle (same layouts)
+    float *ff32 = nullptr, *fp32 = nullptr, *pf32 = nullptr, *pp32 = nullptr, *dinv32 = nullptr, *minv32 = nullptr;
 };
 
 struct Topo {
@@ -144,6 +146,9 @@ struct hho_ctx {
     int64_t launches = 0;                // kernels launched by the solver entry points
     int64_t coarse_dense_max = 10000;    // options
     int64_t dd_elements = 0;             // 0 = default per dimension
+    bool use_graphs = true;              // replay captured V-cycles
+    int spmv_rows = 0;                   // rows per thread of the operator kernels (0 = automatic)
+    int spmv_grid = 0;                   // blocks of the operator kernels (0 = automatic)
 };
 
 // ---- helpers shared across units ----
@@ -190,9 +195,11 @@ void free_level(hho::LevelMat& L);
 // solve.cu
 hho_status pmg_build(hho_ctx* ctx);
 hho_status spmv(hho_ctx* ctx, int l, const double* x, double* y);
+hho_status spmv_f32(hho_ctx* ctx, int l, const float* x, float* y);
 hho_status vcycle(hho_ctx* ctx, const double* r, double* z);
 hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, hho_solve_info* info);
 void free_workspace(hho_ctx* ctx);
+void invalidate_graphs(hho_ctx* ctx);
 // coarse.cu
 hho_status coarse_setup(hho_ctx* ctx);
 hho_status coarse_apply(hho_ctx* ctx, const double* d, double* c);

@@ -6,20 +6,35 @@
 //   restriction   per face and component keep the leading coefficients,
 //                 fused with the defect computation d = I(b - S w) (Sec. 3.1)
 //   prolongation  zero padding, added to the iterate (Sec. 3.1)
-//   coarse level  explicit inverse from a dense Gauss-Jordan factorisation
-//                 (at most 10^4 unknowns) with a rank-one fix of the constant
-//                 pressure kernel, else block-Jacobi GMRES to a 1e-3 relative
-//                 residual decrease (Sec. 5.2.2)
-//   outer solver  flexible GMRES, one V-cycle per iteration (Sec. 3.3)
+//   coarse level  exact solve in FP64 (coarse.cu)
+//   outer solver  flexible GMRES in FP64, one V-cycle per iteration (Sec. 3.3)
 //
-// Every Arnoldi step uses classical Gram-Schmidt applied twice (CGS2).  All
-// reductions are two-stage with a fixed grid, so results are bitwise
-// reproducible run to run.  Small Hessenberg algebra (Givens rotations,
-// back-substitution) runs in single-thread device kernels; the host reads only
-// the residual estimate of the outer and coarse iterations.
+// The V-cycle runs in FP64 or, for the mixed-precision option, with FP32
+// level operators, smoother blocks and smoother vectors (FP32 multiply-adds).
+// In the FP32 V-cycle a dot product is summed in FP32 inside a thread (a few
+// terms) and across the 32 lanes of a warp, and in FP64 from there on (warps,
+// blocks); the relative rounding error stays near (terms per thread + 5) FP32
+// ulps of sum |x_i y_i|, far below what the smoother needs, and the FP64 pipe
+// (about 1/64 of the FP32 rate on this part) stays off the streaming loops.
+// The Hessenberg algebra and the coarse solve are FP64, and the outer FGMRES
+// with its operator stays FP64.
+//
+// Arnoldi steps use classical Gram-Schmidt applied twice (CGS2).  Kernel
+// structure of one Arnoldi step (j):
+//   apply      v_j = w / ||w||, z_j = M^{-1} v_j          (smoother) or a V-cycle
+//   spmv+dot   w = S z_j,  t1 = V^T w
+//   upd+dot    w -= V t1,  t2 = V^T w
+//   upd+norm   w -= V t2,  ||w||^2, then the Hessenberg column, Givens rotation
+//              and residual estimate in the last block of the grid
+// Every dot product is a deterministic two-level reduction inside the kernel
+// that produces its operand: each block writes a partial sum and the last
+// block to finish adds the partials in index order, so results are bitwise
+// reproducible run to run.  The V-cycle is captured once per (input, output)
+// buffer pair into a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 
 #include "internal.h"
 
@@ -27,253 +42,49 @@ namespace hho {
 
 namespace {
 
-constexpr int RED_BLOCKS = 304;  // fixed grid of the two-stage reductions
-constexpr int RED_TPB = 256;
-constexpr int MDOT_MAX = 8;
+constexpr int GMAX = 8192;  // largest grid of any reduction kernel
+constexpr int RT = 256;     // threads per block of the reduction kernels
+constexpr int NVMAX = 8;    // dot products per kernel
 
 int grid1d(int64_t n, int tpb) {
     int64_t g = (n + tpb - 1) / tpb;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152LL * 64));
 }
 
-// ---------------------------------------------------------------------------
-// SpMV-type kernels (one thread per scalar row; 32 consecutive faces per warp)
-// mode 0: y = S x     mode 1: y = bv - S x
-// ---------------------------------------------------------------------------
-struct LevelView {
+// grid of the streaming vector kernels: about 4 elements per thread
+int vgrid(int64_t n) {
+    int64_t g = (n + 4LL * RT - 1) / (4LL * RT);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, GMAX));
+}
+
+template <typename T>
+struct LV {
     int64_t nf, ne;
-    int b, nP, S_max, N_max;
+    int b, nP;
     const int32_t *ff_col, *ff_nsl, *fp_col, *pf_col, *pf_nsl;
-    const double *ff, *fp, *pf, *pp, *dinv, *minv;
+    const T *ff, *fp, *pf, *pp, *dinv, *minv;
 };
 
-LevelView view(const LevelMat& L) {
-    LevelView v;
-    v.nf = L.nf;
-    v.ne = L.ne;
-    v.b = L.b;
-    v.nP = L.nP;
-    v.S_max = L.S_max;
-    v.N_max = L.N_max;
-    v.ff_col = L.ff_col;
-    v.ff_nsl = L.ff_nsl;
-    v.fp_col = L.fp_col;
-    v.pf_col = L.pf_col;
-    v.pf_nsl = L.pf_nsl;
-    v.ff = L.ff;
-    v.fp = L.fp;
-    v.pf = L.pf;
-    v.pp = L.pp;
-    v.dinv = L.dinv;
-    v.minv = L.minv;
-    return v;
+template <typename T>
+LV<T> view(const LevelMat& L);
+
+template <>
+LV<double> view<double>(const LevelMat& L) {
+    return LV<double>{L.nf, L.ne, L.b, L.nP, L.ff_col, L.ff_nsl, L.fp_col, L.pf_col, L.pf_nsl,
+                      L.ff, L.fp, L.pf, L.pp, L.dinv, L.minv};
 }
 
-__device__ __forceinline__ double face_row(const LevelView& L, int64_t F, int r, const double* __restrict__ x) {
-    const int b = L.b, nP = L.nP;
-    const int64_t nf = L.nf;
-    double acc = 0.0;
-    const int ns = L.ff_nsl[F];
-    for (int s = 0; s < ns; ++s) {
-        const int64_t G = L.ff_col[s * nf + F];
-        const double* xv = x + G * b;
-        const double* a = L.ff + ((int64_t)s * b * b + r) * nf + F;
-        for (int c = 0; c < b; ++c) acc += a[(int64_t)c * b * nf] * xv[c];
-    }
-    const double* xp = x + nf * b;
-    for (int p = 0; p < 2; ++p) {
-        const int T = L.fp_col[p * nf + F];
-        if (T < 0) continue;
-        const double* a = L.fp + ((int64_t)p * nP * b + r) * nf + F;
-        for (int c = 0; c < nP; ++c) acc += a[(int64_t)c * b * nf] * xp[(int64_t)T * nP + c];
-    }
-    return acc;
+template <>
+LV<float> view<float>(const LevelMat& L) {
+    return LV<float>{L.nf, L.ne, L.b, L.nP, L.ff_col, L.ff_nsl, L.fp_col, L.pf_col, L.pf_nsl,
+                     L.ff32, L.fp32, L.pf32, L.pp32, L.dinv32, L.minv32};
 }
 
-__device__ __forceinline__ double elem_row(const LevelView& L, int64_t T, int r, const double* __restrict__ x) {
-    const int b = L.b, nP = L.nP;
-    const int64_t ne = L.ne;
-    double acc = 0.0;
-    const int N = L.pf_nsl[T];
-    for (int f = 0; f < N; ++f) {
-        const int64_t G = L.pf_col[f * ne + T];
-        const double* a = L.pf + ((int64_t)f * b * nP + r) * ne + T;
-        for (int c = 0; c < b; ++c) acc += a[(int64_t)c * nP * ne] * x[G * b + c];
-    }
-    const double* xp = x + L.nf * b + T * nP;
-    const double* a = L.pp + (int64_t)r * ne + T;
-    for (int c = 0; c < nP; ++c) acc += a[(int64_t)c * nP * ne] * xp[c];
-    return acc;
-}
-
-__global__ void k_spmv(LevelView L, const double* __restrict__ x, const double* __restrict__ bv, double* __restrict__ y,
-                       int mode) {
-    const int64_t nfr = L.nf * L.b, ner = L.ne * L.nP;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < nfr) {
-            int r = (int)(i / L.nf);
-            int64_t F = i % L.nf;
-            double v = face_row(L, F, r, x);
-            int64_t o = F * L.b + r;
-            y[o] = mode ? bv[o] - v : v;
-        } else {
-            int64_t j = i - nfr;
-            int r = (int)(j / L.ne);
-            int64_t T = j % L.ne;
-            double v = elem_row(L, T, r, x);
-            int64_t o = nfr + T * L.nP + r;
-            y[o] = mode ? bv[o] - v : v;
-        }
-    }
-}
-
-// d (coarse layout) = I (bv - S x): only the rows kept by the restriction are formed.
-__global__ void k_residual_restrict(LevelView L, int nFf, int bc, int nFc, int nPc, const double* __restrict__ x,
-                                    const double* __restrict__ bv, double* __restrict__ d) {
-    const int64_t nfr = L.nf * bc, ner = L.ne * nPc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < nfr) {
-            int rc = (int)(i / L.nf);
-            int64_t F = i % L.nf;
-            int rf = (rc / nFc) * nFf + rc % nFc;
-            int64_t o = F * L.b + rf;
-            d[F * bc + rc] = bv[o] - face_row(L, F, rf, x);
-        } else {
-            int64_t j = i - nfr;
-            int r = (int)(j / L.ne);
-            int64_t T = j % L.ne;
-            int64_t o = L.nf * L.b + T * L.nP + r;
-            d[nfr + T * nPc + r] = bv[o] - elem_row(L, T, r, x);
-        }
-    }
-}
-
-// x (fine) += zero-padded xc (coarse)
-__global__ void k_prolong_add(int64_t nf, int64_t ne, int bf, int nFf, int nPf, int bc, int nFc, int nPc,
-                              const double* __restrict__ xc, double* __restrict__ x) {
-    const int64_t nfr = nf * bc, ner = ne * nPc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < nfr) {
-            int64_t F = i / bc;
-            int rc = (int)(i % bc);
-            int rf = (rc / nFc) * nFf + rc % nFc;
-            x[F * bf + rf] += xc[i];
-        } else {
-            int64_t j = i - nfr, T = j / nPc;
-            int r = (int)(j % nPc);
-            x[nf * bf + T * nPf + r] += xc[i];
-        }
-    }
-}
-
-// z = M^{-1} v (block Jacobi)
-__global__ void k_jacobi(LevelView L, const double* __restrict__ v, double* __restrict__ z) {
-    const int64_t nfr = L.nf * L.b, ner = L.ne * L.nP;
-    const int b = L.b, nP = L.nP;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < nfr) {
-            int r = (int)(i / L.nf);
-            int64_t F = i % L.nf;
-            const double* a = L.dinv + (int64_t)r * L.nf + F;
-            const double* vv = v + F * b;
-            double s = 0.0;
-            for (int c = 0; c < b; ++c) s += a[(int64_t)c * b * L.nf] * vv[c];
-            z[F * b + r] = s;
-        } else {
-            int64_t j = i - nfr;
-            int r = (int)(j / L.ne);
-            int64_t T = j % L.ne;
-            const double* a = L.minv + (int64_t)r * L.ne + T;
-            const double* vv = v + nfr + T * nP;
-            double s = 0.0;
-            for (int c = 0; c < nP; ++c) s += a[(int64_t)c * nP * L.ne] * vv[c];
-            z[nfr + T * nP + r] = s;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Deterministic reductions: dots of w with up to MDOT_MAX vectors V_i (stride ld)
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(RED_TPB) k_mdot_partial(int64_t n, const double* __restrict__ V, int64_t ld, int nv,
-                                                          const double* __restrict__ w, double* __restrict__ partial) {
-    double acc[MDOT_MAX];
-#pragma unroll
-    for (int v = 0; v < MDOT_MAX; ++v) acc[v] = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double wi = w[i];
-#pragma unroll
-        for (int v = 0; v < MDOT_MAX; ++v)
-            if (v < nv) acc[v] += V[v * ld + i] * wi;
-    }
-    __shared__ double sm[RED_TPB / 32][MDOT_MAX];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int v = 0; v < MDOT_MAX; ++v) {
-        double a = acc[v];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) sm[wid][v] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x < nv) {
-        double s = 0.0;
-        for (int i = 0; i < RED_TPB / 32; ++i) s += sm[i][threadIdx.x];
-        partial[threadIdx.x * RED_BLOCKS + blockIdx.x] = s;
-    }
-}
-
-__global__ void k_mdot_final(int nv, const double* __restrict__ partial, double* __restrict__ out) {
-    __shared__ double sm[RED_BLOCKS];
-    for (int v = 0; v < nv; ++v) {
-        for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) sm[i] = partial[v * RED_BLOCKS + i];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int i = 0; i < RED_BLOCKS; ++i) s += sm[i];
-            out[v] = s;
-        }
-        __syncthreads();
-    }
-}
-
-// out = a0 * out + sgn * sum_i coef[i] * V_i
-__global__ void k_combine(int64_t n, double* __restrict__ out, double a0, const double* __restrict__ V, int64_t ld,
-                          int nv, const double* __restrict__ coef, double sgn) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double s = (a0 == 0.0) ? 0.0 : a0 * out[i];
-        for (int v = 0; v < nv; ++v) s += sgn * coef[v] * V[v * ld + i];
-        out[i] = s;
-    }
-}
-
-// dst = src / *den  (zero if the denominator is zero)
-__global__ void k_scale(int64_t n, const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ den) {
-    double dv = *den;
-    double inv = (dv == 0.0) ? 0.0 : 1.0 / dv;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = src[i] * inv;
-}
-
-__global__ void k_copy(int64_t n, const double* __restrict__ src, double* __restrict__ dst) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = src[i];
-}
-
-__global__ void k_zero(int64_t n, double* __restrict__ dst) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = 0.0;
-}
-
-// ---------------------------------------------------------------------------
-// Small Hessenberg algebra (single thread).  Scalar area layout for restart m:
-//   [0] beta^2   [1] beta   [2] m_eff   [3] residual estimate   [4] breakdown
-//   [8 ..)       H (m+1) x m column-major
-//   then cs[m], sn[m], g[m+1], y[m], t1[m+1], t2[m+1], nrm2[1]
-// ---------------------------------------------------------------------------
+// Scalar area of one GMRES instance with restart m.
+//   [0] beta^2  [1] beta  [2] m_eff  [3] residual estimate  [4] breakdown  [5] norm of the pending w
+//   H (m+1) x m column-major, cs[m], sn[m], g[m+1], t1[m+1], t2[m+1], nrm
 struct GS {
-    int m;
-    int H, cs, sn, g, y, t1, t2, nrm;
-    int total;
+    int m, H, cs, sn, g, t1, t2, nrm, total;
 };
 GS gs_layout(int m) {
     GS s;
@@ -287,8 +98,6 @@ GS gs_layout(int m) {
     o += m;
     s.g = o;
     o += m + 1;
-    s.y = o;
-    o += m;
     s.t1 = o;
     o += m + 1;
     s.t2 = o;
@@ -299,65 +108,553 @@ GS gs_layout(int m) {
     return s;
 }
 
-__global__ void k_gs_start(double* sc, GS L) {
-    double b2 = sc[0];
-    double beta = sqrt(b2);
-    sc[1] = beta;
-    sc[2] = 0.0;
-    sc[3] = beta;
-    sc[4] = (beta == 0.0) ? 1.0 : 0.0;
-    for (int i = 0; i <= L.m; ++i) sc[L.g + i] = 0.0;
-    sc[L.g] = beta;
+enum Hook { HOOK_NONE = 0, HOOK_START = 1, HOOK_COLUMN = 2 };
+
+// Type of the per-thread and per-warp part of a dot product (see the header).
+template <typename T>
+struct AccT {
+    using type = double;
+};
+template <>
+struct AccT<float> {
+    using type = float;
+};
+
+// Scalar work done by one thread once the reductions of a kernel are final.
+__device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j) {
+    if (hook == HOOK_START) {
+        double beta = sqrt(sc[0]);
+        sc[1] = beta;
+        sc[2] = 0.0;
+        sc[3] = beta;
+        sc[4] = (beta == 0.0) ? 1.0 : 0.0;
+        sc[5] = beta;
+        for (int i = 0; i <= L.m; ++i) sc[L.g + i] = 0.0;
+        sc[L.g] = beta;
+    } else if (hook == HOOK_COLUMN) {
+        double* H = sc + L.H;
+        const int ld = L.m + 1;
+        if (sc[4] != 0.0) {  // after a breakdown the remaining columns are ignored
+            for (int i = 0; i <= L.m; ++i) H[j * ld + i] = 0.0;
+            sc[5] = 0.0;
+            return;
+        }
+        for (int i = 0; i <= j; ++i) H[j * ld + i] = sc[L.t1 + i] + sc[L.t2 + i];
+        double hn = sqrt(sc[L.nrm]);
+        H[j * ld + j + 1] = hn;
+        sc[5] = hn;
+        for (int i = 0; i < j; ++i) {
+            double c = sc[L.cs + i], s = sc[L.sn + i];
+            double a = H[j * ld + i], bb = H[j * ld + i + 1];
+            H[j * ld + i] = c * a + s * bb;
+            H[j * ld + i + 1] = -s * a + c * bb;
+        }
+        double a = H[j * ld + j], bb = H[j * ld + j + 1];
+        double r = hypot(a, bb);
+        double c = (r == 0.0) ? 1.0 : a / r, s = (r == 0.0) ? 0.0 : bb / r;
+        sc[L.cs + j] = c;
+        sc[L.sn + j] = s;
+        H[j * ld + j] = r;
+        H[j * ld + j + 1] = 0.0;
+        double gj = sc[L.g + j];
+        sc[L.g + j] = c * gj;
+        sc[L.g + j + 1] = -s * gj;
+        sc[3] = fabs(sc[L.g + j + 1]);
+        sc[2] = j + 1;
+        if (hn == 0.0) sc[4] = 1.0;
+    }
 }
 
-// Finish column j: H[:,j] = t1 + t2, H[j+1,j] = sqrt(nrm2); Givens update.
-__global__ void k_gs_column(double* sc, GS L, int j) {
-    double* H = sc + L.H;
-    const int ld = L.m + 1;
-    if (sc[4] != 0.0) {  // after a breakdown the remaining columns are ignored
-        for (int i = 0; i <= L.m; ++i) H[j * ld + i] = 0.0;
-        sc[L.nrm + 0] = 0.0;
-        return;
+// Block reduction of the accumulators acc[0..nv-1] and, when self is set, of
+// acc[NV-1] as output nv; partial sums per block; the last block adds the
+// partials in index order into out[0..nv+self-1] and runs the hook.  (Output
+// slots are mapped here, in shared memory, so that no register array is
+// indexed by a run-time value.)
+template <int NV, typename A>
+__device__ __forceinline__ void reduce_finish(A (&acc)[NV], int nv0, int self, double* __restrict__ partial,
+                                              unsigned* __restrict__ counter, double* __restrict__ out, int hook,
+                                              double* sc, GS L, int j) {
+    const int nv = nv0 + self;
+    __shared__ double sm[RT / 32][NV];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        A a = acc[v];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) sm[wid][v] = (double)a;
     }
-    for (int i = 0; i <= j; ++i) H[j * ld + i] = sc[L.t1 + i] + sc[L.t2 + i];
-    double hn = sqrt(sc[L.nrm]);
-    H[j * ld + j + 1] = hn;
-    sc[L.nrm] = hn;  // denominator for v_{j+1}
-    // apply previous rotations
-    for (int i = 0; i < j; ++i) {
-        double c = sc[L.cs + i], s = sc[L.sn + i];
-        double a = H[j * ld + i], bb = H[j * ld + i + 1];
-        H[j * ld + i] = c * a + s * bb;
-        H[j * ld + i + 1] = -s * a + c * bb;
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        const int src = ((int)threadIdx.x < nv0) ? (int)threadIdx.x : NV - 1;
+        double s = 0.0;
+        for (int w = 0; w < RT / 32; ++w) s += sm[w][src];
+        partial[threadIdx.x * GMAX + blockIdx.x] = s;
     }
-    double a = H[j * ld + j], bb = H[j * ld + j + 1];
-    double r = hypot(a, bb);
-    double c = (r == 0.0) ? 1.0 : a / r, s = (r == 0.0) ? 0.0 : bb / r;
-    sc[L.cs + j] = c;
-    sc[L.sn + j] = s;
-    H[j * ld + j] = r;
-    H[j * ld + j + 1] = 0.0;
-    double gj = sc[L.g + j];
-    sc[L.g + j] = c * gj;
-    sc[L.g + j + 1] = -s * gj;
-    sc[3] = fabs(sc[L.g + j + 1]);
-    sc[2] = j + 1;
-    if (hn == 0.0) sc[4] = 1.0;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // one warp per dot product: fixed per-lane strides, then a fixed shuffle tree
+    for (int v = wid; v < nv; v += RT / 32) {
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partial + v * GMAX + b);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[v] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        run_hook(hook, sc, L, j);
+        __threadfence();
+    }
 }
 
-// y = R^{-1} g over the first m_eff columns (zeros beyond).
-__global__ void k_gs_solve(double* sc, GS L) {
-    const double* H = sc + L.H;
-    const int ld = L.m + 1;
-    int me = (int)sc[2];
-    if (sc[1] == 0.0) me = 0;
-    for (int i = 0; i < L.m; ++i) sc[L.y + i] = 0.0;
-    for (int i = me - 1; i >= 0; --i) {
-        double s = sc[L.g + i];
-        for (int l = i + 1; l < me; ++l) s -= H[l * ld + i] * sc[L.y + l];
-        double d = H[i * ld + i];
-        sc[L.y + i] = (d == 0.0) ? 0.0 : s / d;
+// dacc[q] += V_q[o] * v for q < nv, dacc[NVMAX] += v * v: fully unrolled with
+// predicates so the accumulators stay in registers.
+template <typename T, typename A>
+__device__ __forceinline__ void accumulate_dots(A (&dacc)[NVMAX + 1], const T* __restrict__ V, int64_t ld,
+                                                int64_t o, int nv, int self, T v) {
+    const A dv = (A)v;
+#pragma unroll
+    for (int q = 0; q < NVMAX; ++q)
+        if (q < nv) dacc[q] += (A)V[q * ld + o] * dv;
+    if (self) dacc[NVMAX] += dv * dv;
+}
+
+// Finish the nv dots and the self product (output nv).
+template <typename A>
+__device__ __forceinline__ void finish_dots(A (&dacc)[NVMAX + 1], int nv, int self, double* partial,
+                                            unsigned* counter, double* out, int hook, double* sc, GS gsl, int j) {
+    reduce_finish<NVMAX + 1>(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
+}
+
+// ---------------------------------------------------------------------------
+// Operator rows.  A warp handles 32 consecutive faces (or elements) and R rows
+// of each, so every value load of the operator is one coalesced access and
+// each gathered x value serves R rows.  Accumulation is in the level type T.
+// ---------------------------------------------------------------------------
+template <int R, typename T>
+__device__ __forceinline__ void face_rows(const LV<T>& L, int64_t F, const int (&rows)[R], int nr,
+                                          const T* __restrict__ x, T (&acc)[R]) {
+    const int b = L.b, nP = L.nP;
+    const int64_t nf = L.nf;
+#pragma unroll
+    for (int i = 0; i < R; ++i) acc[i] = T(0);
+    const int ns = L.ff_nsl[F];
+    for (int s = 0; s < ns; ++s) {
+        const int64_t G = L.ff_col[s * nf + F];
+        const T* xv = x + G * b;
+        const T* a = L.ff + (int64_t)s * b * b * nf + F;
+#pragma unroll 4
+        for (int c = 0; c < b; ++c) {
+            const T xc = xv[c];
+            const T* ac = a + (int64_t)c * b * nf;
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (i < nr) acc[i] += __ldg(ac + (int64_t)rows[i] * nf) * xc;
+        }
     }
+    const T* xp = x + nf * b;
+    for (int p = 0; p < 2; ++p) {
+        const int Tl = L.fp_col[p * nf + F];
+        if (Tl < 0) continue;
+        const T* a = L.fp + (int64_t)p * nP * b * nf + F;
+        for (int c = 0; c < nP; ++c) {
+            const T xc = xp[(int64_t)Tl * nP + c];
+            const T* ac = a + (int64_t)c * b * nf;
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (i < nr) acc[i] += __ldg(ac + (int64_t)rows[i] * nf) * xc;
+        }
+    }
+}
+
+template <int R, typename T>
+__device__ __forceinline__ void elem_rows(const LV<T>& L, int64_t E, const int (&rows)[R], int nr,
+                                          const T* __restrict__ x, T (&acc)[R]) {
+    const int b = L.b, nP = L.nP;
+    const int64_t ne = L.ne;
+#pragma unroll
+    for (int i = 0; i < R; ++i) acc[i] = T(0);
+    const int N = L.pf_nsl[E];
+    for (int f = 0; f < N; ++f) {
+        const int64_t G = L.pf_col[f * ne + E];
+        const T* xv = x + G * b;
+        const T* a = L.pf + (int64_t)f * b * nP * ne + E;
+#pragma unroll 4
+        for (int c = 0; c < b; ++c) {
+            const T xc = xv[c];
+            const T* ac = a + (int64_t)c * nP * ne;
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (i < nr) acc[i] += __ldg(ac + (int64_t)rows[i] * ne) * xc;
+        }
+    }
+    const T* xp = x + L.nf * b + E * nP;
+    for (int c = 0; c < nP; ++c) {
+        const T xc = xp[c];
+        const T* ac = L.pp + (int64_t)c * nP * ne + E;
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            if (i < nr) acc[i] += __ldg(ac + (int64_t)rows[i] * ne) * xc;
+    }
+}
+
+// Work items of a level: (32-face tile, row group) then (32-element tile, row group).
+struct Items {
+    int64_t ftiles, etiles;
+    int fgroups, egroups;
+    __host__ __device__ int64_t total() const { return ftiles * fgroups + etiles * egroups; }
+};
+
+// y = S x (mode 0) or y = bv - S x (mode 1) on all rows; optional FP64 dots of y
+// with V_0..V_{nv-1} and with itself (self), finished by reduce_finish.
+template <int R, typename T>
+__global__ void __launch_bounds__(RT) k_spmv_dot(LV<T> L, Items it, const T* __restrict__ x, const T* __restrict__ bv,
+                                                  T* __restrict__ y, int mode, const T* __restrict__ V, int64_t ld,
+                                                  int nv, int self, double* __restrict__ partial,
+                                                  unsigned* __restrict__ counter, double* __restrict__ out, int hook,
+                                                  double* sc, GS gsl, int j) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    using A = typename AccT<T>::type;
+    A dacc[NVMAX + 1];
+#pragma unroll
+    for (int v = 0; v <= NVMAX; ++v) dacc[v] = A(0);
+    const int64_t nfi = it.ftiles * it.fgroups;
+    for (int64_t w = warp; w < it.total(); w += nwarps) {
+        const bool face = w < nfi;
+        const int64_t ww = face ? w : w - nfi;
+        const int groups = face ? it.fgroups : it.egroups;
+        const int64_t tile = ww / groups;
+        const int g = (int)(ww % groups);
+        const int64_t id = tile * 32 + lane;
+        const int nrow = face ? L.b : L.nP;
+        if (id >= (face ? L.nf : L.ne)) continue;
+        int rows[R];
+        int nr = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            rows[i] = g * R + i;
+            if (rows[i] < nrow) nr = i + 1;
+        }
+        T acc[R];
+        if (face) face_rows<R, T>(L, id, rows, nr, x, acc);
+        else elem_rows<R, T>(L, id, rows, nr, x, acc);
+        const int64_t base = face ? id * L.b : L.nf * L.b + id * L.nP;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (i >= nr) break;
+            const int64_t o = base + rows[i];
+            const T v = mode ? T(bv[o] - acc[i]) : acc[i];
+            y[o] = v;
+            accumulate_dots(dacc, V, ld, o, nv, self, v);
+        }
+    }
+    if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
+}
+
+// Same operator with the face block size B known at compile time: a thread
+// holds RF consecutive rows of one face (RF = B up to B = 12), the column loops
+// are fully unrolled and the B gathered x values of a neighbour face are loaded
+// once per slot.  Element rows: RP rows per thread.
+template <int B, int RF, int RP, typename T>
+__global__ void __launch_bounds__(RT) k_spmv_b(LV<T> L, Items it, const T* __restrict__ x, const T* __restrict__ bv,
+                                                T* __restrict__ y, int mode, const T* __restrict__ V, int64_t ld, int nv,
+                                                int self, double* __restrict__ partial, unsigned* __restrict__ counter,
+                                                double* __restrict__ out, int hook, double* sc, GS gsl, int j) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nf = L.nf, ne = L.ne;
+    const int nP = L.nP;
+    using A = typename AccT<T>::type;
+    A dacc[NVMAX + 1];
+#pragma unroll
+    for (int v = 0; v <= NVMAX; ++v) dacc[v] = A(0);
+    const int64_t nfi = it.ftiles * it.fgroups;
+    for (int64_t w = warp; w < it.total(); w += nwarps) {
+        if (w < nfi) {
+            const int64_t tile = w / it.fgroups;
+            const int r0 = (int)(w % it.fgroups) * RF;
+            const int64_t F = tile * 32 + lane;
+            if (F >= nf) continue;
+            T acc[RF];
+#pragma unroll
+            for (int i = 0; i < RF; ++i) acc[i] = T(0);
+            const int ns = L.ff_nsl[F];
+            for (int s = 0; s < ns; ++s) {
+                const int64_t G = L.ff_col[s * nf + F];
+                T xc[B];
+#pragma unroll
+                for (int c = 0; c < B; ++c) xc[c] = x[G * B + c];
+                const T* a = L.ff + ((int64_t)s * B * B + r0) * nf + F;
+#pragma unroll
+                for (int c = 0; c < B; ++c)
+#pragma unroll
+                    for (int i = 0; i < RF; ++i) acc[i] += __ldg(a + (int64_t)(c * B + i) * nf) * xc[c];
+            }
+            for (int p = 0; p < 2; ++p) {
+                const int Tl = L.fp_col[p * nf + F];
+                if (Tl < 0) continue;
+                const T* xp = x + nf * B + (int64_t)Tl * nP;
+                const T* a = L.fp + ((int64_t)p * nP * B + r0) * nf + F;
+                for (int c = 0; c < nP; ++c) {
+                    const T xc = xp[c];
+#pragma unroll
+                    for (int i = 0; i < RF; ++i) acc[i] += __ldg(a + (int64_t)(c * B + i) * nf) * xc;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < RF; ++i) {
+                const int64_t o = F * B + r0 + i;
+                const T v = mode ? T(bv[o] - acc[i]) : acc[i];
+                y[o] = v;
+                accumulate_dots(dacc, V, ld, o, nv, self, v);
+            }
+        } else {
+            const int64_t ww = w - nfi;
+            const int64_t tile = ww / it.egroups;
+            const int r0 = (int)(ww % it.egroups) * RP;
+            const int64_t E = tile * 32 + lane;
+            if (E >= ne) continue;
+            const int nr = min(RP, nP - r0);
+            T acc[RP];
+#pragma unroll
+            for (int i = 0; i < RP; ++i) acc[i] = T(0);
+            const int N = L.pf_nsl[E];
+            for (int f = 0; f < N; ++f) {
+                const int64_t G = L.pf_col[f * ne + E];
+                T xc[B];
+#pragma unroll
+                for (int c = 0; c < B; ++c) xc[c] = x[G * B + c];
+                const T* a = L.pf + ((int64_t)f * B * nP + r0) * ne + E;
+#pragma unroll
+                for (int c = 0; c < B; ++c)
+#pragma unroll
+                    for (int i = 0; i < RP; ++i)
+                        if (i < nr) acc[i] += __ldg(a + (int64_t)(c * nP + i) * ne) * xc[c];
+            }
+            const T* xp = x + nf * B + E * nP;
+            for (int c = 0; c < nP; ++c) {
+                const T xc = xp[c];
+                const T* a = L.pp + ((int64_t)c * nP + r0) * ne + E;
+#pragma unroll
+                for (int i = 0; i < RP; ++i)
+                    if (i < nr) acc[i] += __ldg(a + (int64_t)i * ne) * xc;
+            }
+#pragma unroll
+            for (int i = 0; i < RP; ++i) {
+                if (i >= nr) break;
+                const int64_t o = nf * B + E * nP + r0 + i;
+                const T v = mode ? T(bv[o] - acc[i]) : acc[i];
+                y[o] = v;
+                accumulate_dots(dacc, V, ld, o, nv, self, v);
+            }
+        }
+    }
+    if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
+}
+
+// d (coarse layout) = I (bv - S x): only the rows kept by the restriction are
+// formed; optionally ||d||^2 with the START hook of the coarse smoother.
+template <int R, typename T>
+__global__ void __launch_bounds__(RT) k_residual_restrict(LV<T> L, Items it, int nFf, int bc, int nFc, int nPc,
+                                                           const T* __restrict__ x, const T* __restrict__ bv,
+                                                           T* __restrict__ d, int do_norm, double* __restrict__ partial,
+                                                           unsigned* __restrict__ counter, double* __restrict__ out,
+                                                           double* sc, GS gsl) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    using A = typename AccT<T>::type;
+    A dacc[1] = {A(0)};
+    const int64_t nfi = it.ftiles * it.fgroups;
+    for (int64_t w = warp; w < it.total(); w += nwarps) {
+        const bool face = w < nfi;
+        const int64_t ww = face ? w : w - nfi;
+        const int groups = face ? it.fgroups : it.egroups;
+        const int64_t tile = ww / groups;
+        const int g = (int)(ww % groups);
+        const int64_t id = tile * 32 + lane;
+        const int nrow = face ? bc : nPc;
+        if (id >= (face ? L.nf : L.ne)) continue;
+        int rows[R];
+        int nr = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int rc = g * R + i;
+            rows[i] = face ? (rc / nFc) * nFf + rc % nFc : rc;
+            if (rc < nrow) nr = i + 1;
+        }
+        T acc[R];
+        if (face) face_rows<R, T>(L, id, rows, nr, x, acc);
+        else elem_rows<R, T>(L, id, rows, nr, x, acc);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (i >= nr) break;
+            const int rc = g * R + i;
+            const int64_t of = face ? id * L.b + rows[i] : L.nf * L.b + id * L.nP + rows[i];
+            const int64_t oc = face ? id * bc + rc : L.nf * bc + id * nPc + rc;
+            const T v = bv[of] - acc[i];
+            d[oc] = v;
+            dacc[0] += (A)v * (A)v;
+        }
+    }
+    if (do_norm) reduce_finish<1>(dacc, 1, 0, partial, counter, out, HOOK_START, sc, gsl, 0);
+}
+
+// v = w / den, z = M^{-1} v (block Jacobi): z is computed from w and scaled.
+template <typename T>
+__global__ void k_apply_jacobi(LV<T> L, const T* __restrict__ w, const double* __restrict__ den, T* __restrict__ v,
+                               T* __restrict__ z) {
+    const double dv = *den;
+    const T inv = (dv == 0.0) ? T(0) : T(1.0 / dv);
+    const int64_t nfr = L.nf * L.b, ner = L.ne * L.nP;
+    const int b = L.b, nP = L.nP;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < nfr) {
+            const int r = (int)(i / L.nf);
+            const int64_t F = i % L.nf;
+            const T* a = L.dinv + (int64_t)r * L.nf + F;
+            const T* wv = w + F * b;
+            T s = T(0);
+            for (int c = 0; c < b; ++c) s += a[(int64_t)c * b * L.nf] * wv[c];
+            z[F * b + r] = s * inv;
+            v[F * b + r] = wv[r] * inv;
+        } else {
+            const int64_t jj = i - nfr;
+            const int r = (int)(jj / L.ne);
+            const int64_t E = jj % L.ne;
+            const T* a = L.minv + (int64_t)r * L.ne + E;
+            const T* wv = w + nfr + E * nP;
+            T s = T(0);
+            for (int c = 0; c < nP; ++c) s += a[(int64_t)c * nP * L.ne] * wv[c];
+            z[nfr + E * nP + r] = s * inv;
+            v[nfr + E * nP + r] = wv[r] * inv;
+        }
+    }
+}
+
+// v = w / den (FGMRES basis vector)
+__global__ void k_scale(int64_t n, const double* __restrict__ w, const double* __restrict__ den, double* __restrict__ v) {
+    const double dv = *den;
+    const double inv = (dv == 0.0) ? 0.0 : 1.0 / dv;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = w[i] * inv;
+}
+
+// w += sgn * sum_{q<ncomb} coef[q] V_q, then FP64 dots of the new w with Vd_0..Vd_{nv-1} and itself.
+template <typename T>
+__global__ void __launch_bounds__(RT) k_update_dot(int64_t n, T* __restrict__ w, const T* __restrict__ V, int64_t ld,
+                                                    int ncomb, const double* __restrict__ coef, double sgn,
+                                                    const T* __restrict__ Vd, int nv, int self,
+                                                    double* __restrict__ partial, unsigned* __restrict__ counter,
+                                                    double* __restrict__ out, int hook, double* sc, GS gsl, int j) {
+    __shared__ T s_coef[64];
+    for (int q = threadIdx.x; q < ncomb && q < 64; q += blockDim.x) s_coef[q] = T(sgn * coef[q]);
+    __syncthreads();
+    using A = typename AccT<T>::type;
+    A dacc[NVMAX + 1];
+#pragma unroll
+    for (int v = 0; v <= NVMAX; ++v) dacc[v] = A(0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T s = w[i];
+        for (int q = 0; q < ncomb; ++q) s += s_coef[q] * V[q * ld + i];
+        if (ncomb > 0) w[i] = s;
+        accumulate_dots(dacc, Vd, ld, i, nv, self, s);
+    }
+    if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
+}
+
+// x = a0 x + Z y with y = R^{-1} g solved redundantly by every block (m <= 64).
+template <typename T>
+__global__ void k_update_x(int64_t n, T* __restrict__ x, double a0, const T* __restrict__ Z, int64_t ld,
+                           const double* __restrict__ sc, GS L) {
+    __shared__ double y[64];
+    if (threadIdx.x == 0) {
+        const double* H = sc + L.H;
+        const int ld2 = L.m + 1;
+        int me = (int)sc[2];
+        if (sc[1] == 0.0) me = 0;
+        for (int i = 0; i < L.m; ++i) y[i] = 0.0;
+        for (int i = me - 1; i >= 0; --i) {
+            double s = sc[L.g + i];
+            for (int l = i + 1; l < me; ++l) s -= H[l * ld2 + i] * y[l];
+            const double dd = H[i * ld2 + i];
+            y[i] = (dd == 0.0) ? 0.0 : s / dd;
+        }
+    }
+    __syncthreads();
+    using A = typename AccT<T>::type;
+    __shared__ A ya[64];
+    if (threadIdx.x < 64) ya[threadIdx.x] = (threadIdx.x < L.m) ? (A)y[threadIdx.x] : A(0);
+    __syncthreads();
+    const int me = (sc[1] == 0.0) ? 0 : (int)sc[2];
+    const A a0a = (A)a0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        A s = (a0 == 0.0) ? A(0) : a0a * (A)x[i];
+        for (int q = 0; q < me; ++q) s += ya[q] * (A)Z[q * ld + i];
+        x[i] = T(s);
+    }
+}
+
+// x += zero-padded xc (prolongation)
+template <typename T>
+__global__ void k_prolong_add(int64_t nf, int64_t ne, int bf, int nFf, int nPf, int bc, int nFc, int nPc,
+                              const T* __restrict__ xc, T* __restrict__ x) {
+    const int64_t nfr = nf * bc, ner = ne * nPc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < nfr) {
+            const int64_t F = i / bc;
+            const int rc = (int)(i % bc);
+            x[F * bf + (rc / nFc) * nFf + rc % nFc] += xc[i];
+        } else {
+            const int64_t jj = i - nfr, E = jj / nPc;
+            x[nf * bf + E * nPf + (int)(jj % nPc)] += xc[i];
+        }
+    }
+}
+
+template <typename S, typename D>
+__global__ void k_convert(int64_t n, const S* __restrict__ src, D* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = D(src[i]);
+}
+
+template <typename T>
+__global__ void k_zero(int64_t n, T* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = T(0);
+}
+
+// x -= (n.x) n, the dot product already in *dot
+__global__ void k_null_project(int64_t n, double* __restrict__ x, const double* __restrict__ nv,
+                               const double* __restrict__ dot) {
+    const double a = *dot;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] -= a * nv[i];
+}
+
+int rows_per_thread(int nrow) {
+    if (nrow % 4 == 0) return 4;
+    if (nrow % 3 == 0) return 3;
+    if (nrow % 2 == 0) return 2;
+    return nrow >= 4 ? 4 : nrow;
+}
+
+Items items_for(const LevelMat& L, int R, int frows, int erows) {
+    Items it;
+    it.ftiles = (L.nf + 31) / 32;
+    it.etiles = (L.ne + 31) / 32;
+    it.fgroups = (frows + R - 1) / R;
+    it.egroups = (erows + R - 1) / R;
+    return it;
 }
 
 }  // namespace
@@ -366,129 +663,241 @@ __global__ void k_gs_solve(double* sc, GS L) {
 // Workspace
 // ---------------------------------------------------------------------------
 struct LevelWork {
-    double *bv = nullptr, *x = nullptr, *r = nullptr, *V = nullptr, *Z = nullptr, *w = nullptr, *sc = nullptr;
+    // smoother vectors in the V-cycle type (double or float)
+    void *bv = nullptr, *x = nullptr, *w = nullptr, *V = nullptr, *Z = nullptr;
+    double* sc = nullptr;
+    double *cd = nullptr, *cc = nullptr;  // FP64 coarse right-hand side and solution (mixed precision)
 };
 
 struct Workspace {
     std::vector<LevelWork> lv;
     double* partial = nullptr;
+    unsigned* counter = nullptr;
     // FGMRES
     int restart = 0;
-    double *fV = nullptr, *fZ = nullptr, *fw = nullptr, *fr = nullptr, *fsc = nullptr;
+    double *fV = nullptr, *fZ = nullptr, *fw = nullptr, *fb = nullptr, *fsc = nullptr;
     double* h_sc = nullptr;  // pinned host scalars
+    // captured V-cycles
+    std::map<std::pair<const double*, double*>, cudaGraphExec_t> graphs;
+    std::map<std::pair<const double*, double*>, int64_t> graph_launches;
 };
+
+static void free_graphs(Workspace* W) {
+    for (auto& g : W->graphs) cudaGraphExecDestroy(g.second);
+    W->graphs.clear();
+    W->graph_launches.clear();
+}
+
+void invalidate_graphs(hho_ctx* ctx) {
+    if (ctx->ws) free_graphs(ctx->ws);
+}
 
 void free_workspace(hho_ctx* ctx) {
     Workspace* W = ctx->ws;
     if (!W) return;
+    free_graphs(W);
     for (auto& l : W->lv) {
         dfree(l.bv);
         dfree(l.x);
-        dfree(l.r);
+        dfree(l.w);
         dfree(l.V);
         dfree(l.Z);
-        dfree(l.w);
         dfree(l.sc);
+        dfree(l.cd);
+        dfree(l.cc);
     }
     dfree(W->partial);
+    dfree(W->counter);
     dfree(W->fV);
     dfree(W->fZ);
     dfree(W->fw);
-    dfree(W->fr);
+    dfree(W->fb);
     dfree(W->fsc);
     if (W->h_sc) cudaFreeHost(W->h_sc);
     delete W;
     ctx->ws = nullptr;
 }
 
-static hho_status mdot(hho_ctx* ctx, int64_t n, const double* V, int64_t ld, int nv, const double* w, double* out) {
-    Workspace* W = ctx->ws;
-    for (int v0 = 0; v0 < nv; v0 += MDOT_MAX) {
-        int cnt = std::min(MDOT_MAX, nv - v0);
-        k_mdot_partial<<<RED_BLOCKS, RED_TPB, 0, ctx->stream>>>(n, V + v0 * ld, ld, cnt, w, W->partial);
-        ++ctx->launches;
-        k_mdot_final<<<1, 256, 0, ctx->stream>>>(cnt, W->partial, out + v0);
-        ++ctx->launches;
+// ---- launch helpers (each counts its kernel) ----
+static int op_rows(const hho_ctx* ctx, int nrow) {
+    return ctx->spmv_rows > 0 ? ctx->spmv_rows : rows_per_thread(nrow);
+}
+
+static int op_grid(const hho_ctx* ctx, const Items& it) {
+    if (ctx->spmv_grid > 0) return ctx->spmv_grid;
+    const int64_t g = (it.total() + (RT / 32) - 1) / (RT / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, GMAX));
+}
+
+// rows of a face held by one thread in k_spmv_b: small blocks whole, larger
+// ones split in two or three row groups so that enough warps are in flight
+constexpr int face_rows_for(int B) {
+    return B <= 4 ? B : (B % 2 == 0 && B <= 12 ? B / 2 : (B % 3 == 0 ? (B / 3 <= 10 ? B / 3 : B / 6) : B));
+}
+
+template <int B, typename T>
+static bool launch_spmv_b_B(hho_ctx* ctx, const LevelMat& L, const T* x, const T* bv, T* y, int mode, const T* V,
+                            int64_t ld, int nv, int self, double* partial, unsigned* counter, double* out, int hook,
+                            double* sc, GS gsl, int j) {
+    constexpr int RF = face_rows_for(B);
+    const int RP = L.nP == 1 ? 1 : 4;
+    Items it;
+    it.ftiles = (L.nf + 31) / 32;
+    it.etiles = (L.ne + 31) / 32;
+    it.fgroups = B / RF;
+    it.egroups = (L.nP + RP - 1) / RP;
+    const int g = op_grid(ctx, it);
+    const LV<T> lv = view<T>(L);
+    if (RP == 1)
+        k_spmv_b<B, RF, 1, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter, out,
+                                                         hook, sc, gsl, j);
+    else
+        k_spmv_b<B, RF, 4, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter, out,
+                                                         hook, sc, gsl, j);
+    return true;
+}
+
+template <typename T>
+static bool launch_spmv_b(hho_ctx* ctx, const LevelMat& L, const T* x, const T* bv, T* y, int mode, const T* V,
+                          int64_t ld, int nv, int self, double* partial, unsigned* counter, double* out, int hook,
+                          double* sc, GS gsl, int j) {
+    if (ctx->spmv_rows > 0) return false;  // explicit row grouping requested: generic kernel
+#define HHO_B_CASE(BB)                                                                                             \
+    case BB:                                                                                                       \
+        return launch_spmv_b_B<BB, T>(ctx, L, x, bv, y, mode, V, ld, nv, self, partial, counter, out, hook, sc, gsl, j);
+    switch (L.b) {
+        HHO_B_CASE(2)
+        HHO_B_CASE(3)
+        HHO_B_CASE(4)
+        HHO_B_CASE(6)
+        HHO_B_CASE(8)
+        HHO_B_CASE(9)
+        HHO_B_CASE(10)
+        HHO_B_CASE(12)
+        HHO_B_CASE(18)
+        HHO_B_CASE(30)
+        default:
+            return false;
     }
-    HHO_CUDA(cudaGetLastError());
-    return HHO_OK;
+#undef HHO_B_CASE
+}
+
+template <typename T>
+static void launch_spmv_dot(hho_ctx* ctx, int l, const T* x, const T* bv, T* y, int mode, const T* V, int64_t ld,
+                            int nv, int self, double* out, int hook, double* sc, GS gsl, int j) {
+    const LevelMat& L = ctx->levels[l];
+    {
+        double* partial = ctx->ws ? ctx->ws->partial : nullptr;
+        unsigned* counter = ctx->ws ? ctx->ws->counter : nullptr;
+        if (launch_spmv_b<T>(ctx, L, x, bv, y, mode, V, ld, nv, self, partial, counter, out, hook, sc, gsl, j)) {
+            ++ctx->launches;
+            return;
+        }
+    }
+    const int R = op_rows(ctx, std::max(L.b, L.nP));
+    Items it = items_for(L, R, L.b, L.nP);
+    double* partial = ctx->ws ? ctx->ws->partial : nullptr;
+    unsigned* counter = ctx->ws ? ctx->ws->counter : nullptr;
+    const int g = op_grid(ctx, it);
+    const LV<T> lv = view<T>(L);
+    switch (R) {
+        case 1:
+            k_spmv_dot<1, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter, out,
+                                                        hook, sc, gsl, j);
+            break;
+        case 2:
+            k_spmv_dot<2, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter, out,
+                                                        hook, sc, gsl, j);
+            break;
+        case 3:
+            k_spmv_dot<3, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter, out,
+                                                        hook, sc, gsl, j);
+            break;
+        default:
+            k_spmv_dot<4, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter, out,
+                                                        hook, sc, gsl, j);
+    }
+    ++ctx->launches;
 }
 
 hho_status spmv(hho_ctx* ctx, int l, const double* x, double* y) {
-    const LevelMat& L = ctx->levels[l];
-    k_spmv<<<grid1d(L.n, 256), 256, 0, ctx->stream>>>(view(L), x, nullptr, y, 0);
-    ++ctx->launches;
+    launch_spmv_dot<double>(ctx, l, x, nullptr, y, 0, nullptr, 0, 0, 0, nullptr, HOOK_NONE, nullptr, gs_layout(1), 0);
     HHO_CUDA(cudaGetLastError());
     return HHO_OK;
 }
 
-static hho_status residual(hho_ctx* ctx, int l, const double* x, const double* bv, double* r) {
+hho_status spmv_f32(hho_ctx* ctx, int l, const float* x, float* y) {
     const LevelMat& L = ctx->levels[l];
-    k_spmv<<<grid1d(L.n, 256), 256, 0, ctx->stream>>>(view(L), x, bv, r, 1);
-    ++ctx->launches;
+    if (!L.ff32) {
+        ctx->err = "hho_spmv_f32: no FP32 copy of this level (pmg_setup with HHO_FP32 keeps one below the coarse level)";
+        return HHO_ERR_STATE;
+    }
+    launch_spmv_dot<float>(ctx, l, x, nullptr, y, 0, nullptr, 0, 0, 0, nullptr, HOOK_NONE, nullptr, gs_layout(1), 0);
     HHO_CUDA(cudaGetLastError());
     return HHO_OK;
 }
 
-static hho_status jacobi(hho_ctx* ctx, int l, const double* v, double* z) {
-    const LevelMat& L = ctx->levels[l];
-    k_jacobi<<<grid1d(L.n, 256), 256, 0, ctx->stream>>>(view(L), v, z);
+template <typename T>
+static void launch_update_dot(hho_ctx* ctx, int64_t n, T* w, const T* V, int64_t ld, int ncomb, const double* coef,
+                              double sgn, const T* Vd, int nv, int self, double* out, int hook, double* sc, GS gsl,
+                              int j) {
+    Workspace* W = ctx->ws;
+    k_update_dot<T><<<vgrid(n), RT, 0, ctx->stream>>>(n, w, V, ld, ncomb, coef, sgn, Vd, nv, self, W->partial,
+                                                      W->counter, out, hook, sc, gsl, j);
     ++ctx->launches;
-    HHO_CUDA(cudaGetLastError());
-    return HHO_OK;
 }
 
-// One Arnoldi step j with CGS2: w = A z_j is given in w; V holds v_0..v_j.
-static hho_status arnoldi_finish(hho_ctx* ctx, int64_t n, double* V, double* w, double* sc, const GS& G, int j) {
-    HHO_TRY(mdot(ctx, n, V, n, j + 1, w, sc + G.t1));
-    k_combine<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, w, 1.0, V, n, j + 1, sc + G.t1, -1.0);
-    ++ctx->launches;
-    HHO_TRY(mdot(ctx, n, V, n, j + 1, w, sc + G.t2));
-    k_combine<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, w, 1.0, V, n, j + 1, sc + G.t2, -1.0);
-    ++ctx->launches;
-    HHO_TRY(mdot(ctx, n, w, n, 1, w, sc + G.nrm));
-    k_gs_column<<<1, 1, 0, ctx->stream>>>(sc, G, j);
-    ++ctx->launches;
-    k_scale<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, w, V + (int64_t)(j + 1) * n, sc + G.nrm);
-    ++ctx->launches;
-    HHO_CUDA(cudaGetLastError());
-    return HHO_OK;
+// dots of w with V_0..V_{nv-1} in chunks of NVMAX (no hook)
+static void dots(hho_ctx* ctx, int64_t n, const double* V, int64_t ld, int nv, double* w, double* out, double* sc,
+                 GS gsl, int j) {
+    for (int v0 = 0; v0 < nv; v0 += NVMAX) {
+        const int cnt = std::min(NVMAX, nv - v0);
+        launch_update_dot<double>(ctx, n, w, nullptr, ld, 0, nullptr, 0.0, V + v0 * ld, cnt, 0, out + v0, HOOK_NONE, sc,
+                                  gsl, j);
+    }
 }
 
 // m iterations of right-preconditioned GMRES on level l: x <- x + Z y (x = Z y when x_zero).
-static hho_status smooth(hho_ctx* ctx, int l, const double* bv, double* x, bool x_zero) {
+// beta_ready: ||bv||^2 is already in sc[0] with the START hook run (by the restriction kernel).
+template <typename T>
+static hho_status smooth(hho_ctx* ctx, int l, const T* bv, T* x, bool x_zero, bool beta_ready) {
     const LevelMat& L = ctx->levels[l];
     LevelWork& lw = ctx->ws->lv[l];
     const int m = ctx->smooth_its;
     const int64_t n = L.n;
     if (m == 0) {
         if (x_zero) {
-            k_zero<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x);
+            k_zero<T><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x);
             ++ctx->launches;
         }
         return HHO_OK;
     }
     GS G = gs_layout(m);
     double* sc = lw.sc;
+    T* w = static_cast<T*>(lw.w);
+    T* V = static_cast<T*>(lw.V);
+    T* Z = static_cast<T*>(lw.Z);
+    const T* w0;
     if (x_zero) {
-        k_copy<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, bv, lw.r);
-        ++ctx->launches;
+        if (!beta_ready)
+            launch_update_dot<T>(ctx, n, const_cast<T*>(bv), nullptr, n, 0, nullptr, 0.0, bv, 1, 0, sc + 0, HOOK_START,
+                                 sc, G, 0);
+        w0 = bv;
     } else {
-        HHO_TRY(residual(ctx, l, x, bv, lw.r));
+        launch_spmv_dot<T>(ctx, l, x, bv, w, 1, nullptr, n, 0, 1, sc + 0, HOOK_START, sc, G, 0);
+        w0 = w;
     }
-    HHO_TRY(mdot(ctx, n, lw.r, n, 1, lw.r, sc + 0));
-    k_gs_start<<<1, 1, 0, ctx->stream>>>(sc, G);
-    ++ctx->launches;
-    k_scale<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, lw.r, lw.V, sc + 1);
-    ++ctx->launches;
+    const LV<T> lv = view<T>(L);
     for (int j = 0; j < m; ++j) {
-        HHO_TRY(jacobi(ctx, l, lw.V + (int64_t)j * n, lw.Z + (int64_t)j * n));
-        HHO_TRY(spmv(ctx, l, lw.Z + (int64_t)j * n, lw.w));
-        HHO_TRY(arnoldi_finish(ctx, n, lw.V, lw.w, sc, G, j));
+        T* vj = V + (int64_t)j * n;
+        T* zj = Z + (int64_t)j * n;
+        k_apply_jacobi<T><<<grid1d(n, 256), 256, 0, ctx->stream>>>(lv, j == 0 ? w0 : w, sc + 5, vj, zj);
+        ++ctx->launches;
+        launch_spmv_dot<T>(ctx, l, zj, nullptr, w, 0, V, n, j + 1, 0, sc + G.t1, HOOK_NONE, sc, G, j);
+        launch_update_dot<T>(ctx, n, w, V, n, j + 1, sc + G.t1, -1.0, V, j + 1, 0, sc + G.t2, HOOK_NONE, sc, G, j);
+        launch_update_dot<T>(ctx, n, w, V, n, j + 1, sc + G.t2, -1.0, nullptr, 0, 1, sc + G.nrm, HOOK_COLUMN, sc, G, j);
     }
-    k_gs_solve<<<1, 1, 0, ctx->stream>>>(sc, G);
-    ++ctx->launches;
-    k_combine<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x, x_zero ? 0.0 : 1.0, lw.Z, n, m, sc + G.y, 1.0);
+    k_update_x<T><<<vgrid(n), RT, 0, ctx->stream>>>(n, x, x_zero ? 0.0 : 1.0, Z, n, sc, G);
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());
     return HHO_OK;
@@ -500,57 +909,135 @@ static hho_status host_read(hho_ctx* ctx, const double* dsrc, double* hdst, int 
     return HHO_OK;
 }
 
-static hho_status coarse_solve(hho_ctx* ctx, int l, const double* d, double* c) {
-    (void)l;
+template <int R, typename T>
+static void restrict_R(hho_ctx* ctx, const LevelMat& F, const LevelMat& C, Items it, const T* x, const T* bv, T* d,
+                       int do_norm, double* sc, GS G) {
+    Workspace* W = ctx->ws;
+    k_residual_restrict<R, T><<<op_grid(ctx, it), RT, 0, ctx->stream>>>(view<T>(F), it, F.nF, C.b, C.nF, C.nP, x, bv,
+                                                                        d, do_norm, W->partial, W->counter, sc, sc, G);
+}
+
+template <typename T>
+static hho_status coarse_level(hho_ctx* ctx, int l, const T* d, T* c);
+
+template <>
+hho_status coarse_level<double>(hho_ctx* ctx, int, const double* d, double* c) {
     return coarse_apply(ctx, d, c);
 }
 
-// MG_V(l, b, w) with the iterate held in lv[l].x (zero initial guess when x_zero).
-static hho_status vcycle_level(hho_ctx* ctx, int l, const double* bv, double* x, bool x_zero) {
+template <>
+hho_status coarse_level<float>(hho_ctx* ctx, int l, const float* d, float* c) {
+    LevelWork& lw = ctx->ws->lv[l];
+    const int64_t n = ctx->levels[l].n;
+    k_convert<float, double><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, d, lw.cd);
+    HHO_TRY(coarse_apply(ctx, lw.cd, lw.cc));
+    k_convert<double, float><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, lw.cc, c);
+    ctx->launches += 2;
+    HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
+}
+
+// MG_V(l, b, w): iterate in x (zero initial guess when x_zero).
+template <typename T>
+static hho_status vcycle_level(hho_ctx* ctx, int l, const T* bv, T* x, bool x_zero, bool beta_ready) {
     const int Lc = (int)ctx->levels.size() - 1;
     const LevelMat& F = ctx->levels[l];
     const LevelMat& C = ctx->levels[l + 1];
     LevelWork& cw = ctx->ws->lv[l + 1];
-    HHO_TRY(smooth(ctx, l, bv, x, x_zero));
-    k_residual_restrict<<<grid1d(C.n, 256), 256, 0, ctx->stream>>>(view(F), F.nF, C.b, C.nF, C.nP, x, bv, cw.bv);
+    T* cbv = static_cast<T*>(cw.bv);
+    T* cx = static_cast<T*>(cw.x);
+    HHO_TRY(smooth<T>(ctx, l, bv, x, x_zero, beta_ready));
+    const bool coarse_next = (l + 1 == Lc);
+    const int Rc = op_rows(ctx, std::max(C.b, C.nP));
+    Items it = items_for(F, Rc, C.b, C.nP);
+    GS Gc = gs_layout(std::max(ctx->smooth_its, 1));
+    const int do_norm = (!coarse_next && ctx->smooth_its > 0) ? 1 : 0;
+    switch (Rc) {
+        case 1: restrict_R<1, T>(ctx, F, C, it, x, bv, cbv, do_norm, cw.sc, Gc); break;
+        case 2: restrict_R<2, T>(ctx, F, C, it, x, bv, cbv, do_norm, cw.sc, Gc); break;
+        case 3: restrict_R<3, T>(ctx, F, C, it, x, bv, cbv, do_norm, cw.sc, Gc); break;
+        default: restrict_R<4, T>(ctx, F, C, it, x, bv, cbv, do_norm, cw.sc, Gc);
+    }
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());
-    if (l + 1 == Lc) HHO_TRY(coarse_solve(ctx, l + 1, cw.bv, cw.x));
-    else HHO_TRY(vcycle_level(ctx, l + 1, cw.bv, cw.x, true));
-    k_prolong_add<<<grid1d(C.n, 256), 256, 0, ctx->stream>>>(F.nf, F.ne, F.b, F.nF, F.nP, C.b, C.nF, C.nP, cw.x, x);
+    if (coarse_next) HHO_TRY(coarse_level<T>(ctx, l + 1, cbv, cx));
+    else HHO_TRY(vcycle_level<T>(ctx, l + 1, cbv, cx, true, do_norm != 0));
+    k_prolong_add<T><<<grid1d(C.n, 256), 256, 0, ctx->stream>>>(F.nf, F.ne, F.b, F.nF, F.nP, C.b, C.nF, C.nP, cx, x);
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());
-    HHO_TRY(smooth(ctx, l, bv, x, false));
+    HHO_TRY(smooth<T>(ctx, l, bv, x, false, false));
     return HHO_OK;
 }
 
-hho_status vcycle(hho_ctx* ctx, const double* r, double* z) {
-    if (ctx->levels.size() == 1) return coarse_solve(ctx, 0, r, z);
-    return vcycle_level(ctx, 0, r, z, true);
+static hho_status vcycle_direct(hho_ctx* ctx, const double* r, double* z) {
+    if (ctx->levels.size() == 1) return coarse_apply(ctx, r, z);
+    if (ctx->prec == HHO_FP64) return vcycle_level<double>(ctx, 0, r, z, true, false);
+    // mixed precision: FP32 copy of r in, FP32 iterate converted out
+    LevelWork& lw = ctx->ws->lv[0];
+    const int64_t n = ctx->levels[0].n;
+    float* rb = static_cast<float*>(lw.bv);
+    float* xz = static_cast<float*>(lw.x);
+    k_convert<double, float><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, r, rb);
+    ++ctx->launches;
+    HHO_TRY(vcycle_level<float>(ctx, 0, rb, xz, true, false));
+    k_convert<float, double><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, xz, z);
+    ++ctx->launches;
+    HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
 }
 
-__global__ void k_null_project(int64_t n, double* __restrict__ x, const double* __restrict__ nv, const double* __restrict__ dot) {
-    double a = *dot;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] -= a * nv[i];
+// V-cycle through a CUDA graph captured once per (r, z) pair; direct launches on
+// the legacy default stream, which cannot be captured.
+hho_status vcycle(hho_ctx* ctx, const double* r, double* z) {
+    Workspace* W = ctx->ws;
+    if (ctx->stream == nullptr || !ctx->use_graphs) return vcycle_direct(ctx, r, z);
+    auto key = std::make_pair(r, z);
+    auto itg = W->graphs.find(key);
+    if (itg == W->graphs.end()) {
+        if (W->graphs.size() >= 128) free_graphs(W);
+        const int64_t before = ctx->launches;
+        const int64_t coarse_before = ctx->coarse_its_total;
+        HHO_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        hho_status st = vcycle_direct(ctx, r, z);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(ctx->stream, &graph);
+        if (st != HHO_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        HHO_CUDA(ee);
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        HHO_CUDA(ie);
+        W->graphs[key] = exec;
+        W->graph_launches[key] = ctx->launches - before;
+        ctx->launches = before;
+        ctx->coarse_its_total = coarse_before;
+        itg = W->graphs.find(key);
+    }
+    HHO_CUDA(cudaGraphLaunch(itg->second, ctx->stream));
+    ctx->launches += W->graph_launches[key];
+    ctx->coarse_its_total += 1;
+    return HHO_OK;
 }
 
 static hho_status project_null(hho_ctx* ctx, int64_t n, double* x, const double* nv, double* tmp) {
-    HHO_TRY(mdot(ctx, n, nv, n, 1, x, tmp));
+    GS g = gs_layout(1);
+    launch_update_dot<double>(ctx, n, x, nullptr, n, 0, nullptr, 0.0, nv, 1, 0, tmp, HOOK_NONE, nullptr, g, 0);
     k_null_project<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x, nv, tmp);
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());
     return HHO_OK;
 }
 
-static std::vector<double> null_vector_host(hho_ctx* ctx, const LevelMat& L) {
-    std::vector<double> meas(L.ne), v(L.n, 0.0);
-    cudaMemcpy(meas.data(), ctx->disc.emeas, L.ne * sizeof(double), cudaMemcpyDeviceToHost);
-    double s = 0.0;
-    for (int64_t T = 0; T < L.ne; ++T) s += meas[T];
-    double inv = 1.0 / std::sqrt(s);
-    for (int64_t T = 0; T < L.ne; ++T) v[L.nf * L.b + T * L.nP] = std::sqrt(meas[T]) * inv;
-    return v;
+static hho_status make_fp32_copy(hho_ctx* ctx, const double* src, float** dst, size_t n) {
+    dfree(*dst);
+    *dst = nullptr;
+    HHO_TRY(dalloc(ctx, dst, n));
+    k_convert<double, float><<<grid1d((int64_t)n, 256), 256, 0, ctx->stream>>>((int64_t)n, src, *dst);
+    HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
 }
 
 hho_status pmg_build(hho_ctx* ctx) {
@@ -561,27 +1048,49 @@ hho_status pmg_build(hho_ctx* ctx) {
     W->lv.resize(nl);
     const int m = std::max(ctx->smooth_its, 1);
     GS G = gs_layout(m);
+    const bool mixed = ctx->prec == HHO_FP32;
+    const size_t es = mixed ? sizeof(float) : sizeof(double);
     for (int l = 0; l < nl; ++l) {
-        const int64_t n = ctx->levels[l].n;
+        LevelMat& L = ctx->levels[l];
+        const int64_t n = L.n;
         LevelWork& w = W->lv[l];
-        HHO_TRY(dalloc(ctx, &w.bv, n));
-        HHO_TRY(dalloc(ctx, &w.x, n));
-        HHO_TRY(dalloc(ctx, &w.r, n));
-        HHO_TRY(dalloc(ctx, &w.V, (size_t)(m + 1) * n));
-        HHO_TRY(dalloc(ctx, &w.Z, (size_t)m * n));
-        HHO_TRY(dalloc(ctx, &w.w, n));
+        HHO_TRY(device_alloc(ctx, &w.bv, n * es));
+        HHO_TRY(device_alloc(ctx, &w.x, n * es));
+        HHO_TRY(device_alloc(ctx, &w.w, n * es));
+        HHO_TRY(device_alloc(ctx, &w.V, (size_t)(m + 1) * n * es));
+        HHO_TRY(device_alloc(ctx, &w.Z, (size_t)m * n * es));
         HHO_TRY(dalloc(ctx, &w.sc, G.total));
+        HHO_CUDA(cudaMemset(w.sc, 0, G.total * sizeof(double)));
+        if (mixed && l < nl - 1) {
+            HHO_TRY(make_fp32_copy(ctx, L.ff, &L.ff32, (size_t)L.S_max * L.b * L.b * L.nf));
+            HHO_TRY(make_fp32_copy(ctx, L.fp, &L.fp32, (size_t)2 * L.nP * L.b * L.nf));
+            HHO_TRY(make_fp32_copy(ctx, L.pf, &L.pf32, (size_t)L.N_max * L.b * L.nP * L.ne));
+            HHO_TRY(make_fp32_copy(ctx, L.pp, &L.pp32, (size_t)L.nP * L.nP * L.ne));
+            HHO_TRY(make_fp32_copy(ctx, L.dinv, &L.dinv32, (size_t)L.b * L.b * L.nf));
+            HHO_TRY(make_fp32_copy(ctx, L.minv, &L.minv32, (size_t)L.nP * L.nP * L.ne));
+        }
+        if (mixed && l == nl - 1 && nl > 1) {
+            HHO_TRY(dalloc(ctx, &w.cd, n));
+            HHO_TRY(dalloc(ctx, &w.cc, n));
+        }
     }
-    HHO_TRY(dalloc(ctx, &W->partial, (size_t)MDOT_MAX * RED_BLOCKS));
+    HHO_TRY(dalloc(ctx, &W->partial, (size_t)(NVMAX + 1) * GMAX));
+    HHO_TRY(dalloc(ctx, &W->counter, 16));
+    HHO_CUDA(cudaMemset(W->counter, 0, 16 * sizeof(unsigned)));
     HHO_CUDA(cudaMallocHost(&W->h_sc, 64 * sizeof(double)));
     bool neumann = false;
     for (auto b : ctx->disc.h_fbc) neumann |= (b == 2);
     ctx->has_null = !neumann;
-    // level-0 null vector
     dfree(ctx->null_vec0);
     ctx->null_vec0 = nullptr;
     if (ctx->has_null) {
-        auto v = null_vector_host(ctx, ctx->levels[0]);
+        const LevelMat& L = ctx->levels[0];
+        std::vector<double> meas(L.ne), v(L.n, 0.0);
+        HHO_CUDA(cudaMemcpy(meas.data(), ctx->disc.emeas, L.ne * sizeof(double), cudaMemcpyDeviceToHost));
+        double s = 0.0;
+        for (int64_t T = 0; T < L.ne; ++T) s += meas[T];
+        const double inv = 1.0 / std::sqrt(s);
+        for (int64_t T = 0; T < L.ne; ++T) v[L.nf * L.b + T * L.nP] = std::sqrt(meas[T]) * inv;
         HHO_TRY(dalloc(ctx, &ctx->null_vec0, v.size()));
         HHO_CUDA(cudaMemcpy(ctx->null_vec0, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
@@ -593,85 +1102,104 @@ hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, 
     Workspace* W = ctx->ws;
     const LevelMat& L0 = ctx->levels[0];
     const int64_t n = L0.n;
-    if (restart < 1 || restart > 200 || maxit < 0 || !(rtol > 0.0)) {
-        ctx->err = "hho_solve: invalid restart, maxit or rtol";
+    if (restart < 1 || restart > 64 || maxit < 0 || !(rtol > 0.0)) {
+        ctx->err = "hho_solve: invalid restart (1..64), maxit or rtol";
         return HHO_ERR_ARG;
     }
     if (W->restart != restart) {
         dfree(W->fV);
         dfree(W->fZ);
         dfree(W->fw);
-        dfree(W->fr);
+        dfree(W->fb);
         dfree(W->fsc);
         HHO_TRY(dalloc(ctx, &W->fV, (size_t)(restart + 1) * n));
         HHO_TRY(dalloc(ctx, &W->fZ, (size_t)restart * n));
         HHO_TRY(dalloc(ctx, &W->fw, n));
-        HHO_TRY(dalloc(ctx, &W->fr, n));
+        HHO_TRY(dalloc(ctx, &W->fb, n));
         HHO_TRY(dalloc(ctx, &W->fsc, gs_layout(restart).total + 8));
+        HHO_CUDA(cudaMemset(W->fsc, 0, (gs_layout(restart).total + 8) * sizeof(double)));
         W->restart = restart;
     }
     GS G = gs_layout(restart);
     double* sc = W->fsc;
+    double* tmp = sc + G.total;
     double* hs = W->h_sc;
-    double* bvec = W->fr;
+    double* bvec = W->fb;
     cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, ctx->stream);
+    HHO_CUDA(cudaEventCreate(&e0));
+    HHO_CUDA(cudaEventCreate(&e1));
+    HHO_CUDA(cudaEventRecord(e0, ctx->stream));
     ctx->coarse_its_total = 0;
-    // b (projected on the complement of the constant-pressure kernel when it exists)
-    k_copy<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, ctx->rhs, bvec);
+    k_convert<double, double><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, ctx->rhs, bvec);
     ++ctx->launches;
-    if (ctx->has_null) HHO_TRY(project_null(ctx, n, bvec, ctx->null_vec0, sc + G.total));
-    k_zero<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x);
+    if (ctx->has_null) HHO_TRY(project_null(ctx, n, bvec, ctx->null_vec0, tmp));
+    k_zero<double><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x);
     ++ctx->launches;
-    HHO_TRY(mdot(ctx, n, bvec, n, 1, bvec, sc + 0));
-    HHO_TRY(host_read(ctx, sc, hs, 1));
-    const double bnorm = std::sqrt(hs[0]);
+    // ||b||, which is also beta of the first restart cycle (r = b)
+    launch_update_dot<double>(ctx, n, bvec, nullptr, n, 0, nullptr, 0.0, bvec, 1, 0, sc + 0, HOOK_START, sc, G, 0);
+    HHO_TRY(host_read(ctx, sc + 1, hs, 1));
+    const double bnorm = hs[0];
     int it = 0;
     double relres = 0.0;
     hho_status st = HHO_OK;
     if (bnorm > 0.0) {
-        k_copy<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, bvec, W->fw);
-        ++ctx->launches;
         bool conv = false;
+        const double* r = bvec;
+        double beta = bnorm;
         while (it < maxit) {
-            // r = b - S x is in fw
-            HHO_TRY(mdot(ctx, n, W->fw, n, 1, W->fw, sc + 0));
-            k_gs_start<<<1, 1, 0, ctx->stream>>>(sc, G);
-            ++ctx->launches;
-            HHO_TRY(host_read(ctx, sc + 1, hs, 1));
-            if (hs[0] <= rtol * bnorm) {
+            if (beta <= rtol * bnorm) {
                 conv = true;
                 break;
             }
-            k_scale<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, W->fw, W->fV, sc + 1);
+            k_scale<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, r, sc + 5, W->fV);
             ++ctx->launches;
-            int j = 0;
-            for (; j < restart; ++j) {
-                HHO_TRY(vcycle(ctx, W->fV + (int64_t)j * n, W->fZ + (int64_t)j * n));
-                HHO_TRY(spmv(ctx, 0, W->fZ + (int64_t)j * n, W->fw));
-                HHO_TRY(arnoldi_finish(ctx, n, W->fV, W->fw, sc, G, j));
+            for (int j = 0; j < restart; ++j) {
+                double* vj = W->fV + (int64_t)j * n;
+                double* zj = W->fZ + (int64_t)j * n;
+                HHO_TRY(vcycle(ctx, vj, zj));
+                const int nv = j + 1;
+                const int c0 = std::min(nv, NVMAX);
+                // w = S z_j, t1 = V^T w
+                launch_spmv_dot<double>(ctx, 0, zj, nullptr, W->fw, 0, W->fV, n, c0, 0, sc + G.t1, HOOK_NONE, sc, G, j);
+                if (nv > c0) dots(ctx, n, W->fV + (int64_t)c0 * n, n, nv - c0, W->fw, sc + G.t1 + c0, sc, G, j);
+                // w -= V t1, t2 = V^T w
+                launch_update_dot<double>(ctx, n, W->fw, W->fV, n, nv, sc + G.t1, -1.0, W->fV, c0, 0, sc + G.t2,
+                                          HOOK_NONE, sc, G, j);
+                if (nv > c0) dots(ctx, n, W->fV + (int64_t)c0 * n, n, nv - c0, W->fw, sc + G.t2 + c0, sc, G, j);
+                // w -= V t2, ||w||^2, Hessenberg column and Givens rotation
+                launch_update_dot<double>(ctx, n, W->fw, W->fV, n, nv, sc + G.t2, -1.0, nullptr, 0, 1, sc + G.nrm,
+                                          HOOK_COLUMN, sc, G, j);
                 ++it;
                 HHO_TRY(host_read(ctx, sc + 3, hs, 2));
-                if (hs[0] <= rtol * bnorm || hs[1] != 0.0 || it >= maxit) break;
+                const bool stop = hs[0] <= rtol * bnorm || hs[1] != 0.0 || it >= maxit;
+                if (stop || j + 1 == restart) break;
+                k_scale<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, W->fw, sc + 5, W->fV + (int64_t)(j + 1) * n);
+                ++ctx->launches;
             }
-            k_gs_solve<<<1, 1, 0, ctx->stream>>>(sc, G);
+            // x += Z y over the columns of this cycle
+            k_update_x<double><<<vgrid(n), RT, 0, ctx->stream>>>(n, x, 1.0, W->fZ, n, sc, G);
             ++ctx->launches;
-            k_combine<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x, 1.0, W->fZ, n, std::min(j + 1, restart), sc + G.y,
-                                                              1.0);
-            ++ctx->launches;
-            HHO_TRY(residual(ctx, 0, x, bvec, W->fw));
+            // true residual, its norm and the START state of the next cycle
+            launch_spmv_dot<double>(ctx, 0, x, bvec, W->fw, 1, nullptr, n, 0, 1, sc + 0, HOOK_START, sc, G, 0);
+            HHO_TRY(host_read(ctx, sc + 1, hs, 1));
+            beta = hs[0];
+            r = W->fw;
+            if (beta <= rtol * bnorm) {
+                conv = true;
+                break;
+            }
         }
-        if (ctx->has_null) HHO_TRY(project_null(ctx, n, x, ctx->null_vec0, sc + G.total));
-        HHO_TRY(residual(ctx, 0, x, bvec, W->fw));
-        HHO_TRY(mdot(ctx, n, W->fw, n, 1, W->fw, sc + 0));
-        HHO_TRY(host_read(ctx, sc, hs, 1));
-        relres = std::sqrt(hs[0]) / bnorm;
+        if (ctx->has_null) {
+            HHO_TRY(project_null(ctx, n, x, ctx->null_vec0, tmp));
+            launch_spmv_dot<double>(ctx, 0, x, bvec, W->fw, 1, nullptr, n, 0, 1, sc + 0, HOOK_START, sc, G, 0);
+            HHO_TRY(host_read(ctx, sc + 1, hs, 1));
+            beta = hs[0];
+        }
+        relres = beta / bnorm;
         if (!conv && relres > rtol) st = HHO_ERR_NOT_CONVERGED;
     }
-    cudaEventRecord(e1, ctx->stream);
-    cudaEventSynchronize(e1);
+    HHO_CUDA(cudaEventRecord(e1, ctx->stream));
+    HHO_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);

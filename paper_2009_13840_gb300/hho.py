@@ -24,7 +24,7 @@ COND = {"v": 0, "vp": 1}
 NODES = {"elem": 0, "face": 1}
 
 # every entry point declared in include/hho.h
-SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "hho_assemble_noalloc", "pmg_setup", "pmg_vcycle", "hho_spmv",
+SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "hho_assemble_noalloc", "pmg_setup", "pmg_vcycle", "hho_spmv", "hho_spmv_f32",
            "hho_solve", "hho_recover", "hho_errors", "hho_get_element_schur", "hho_get_level_coo",
            "hho_set_element_schur", "hho_launch_count", "hho_set_option", "hho_destroy",
            "hho_last_error"]
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
         "pmg_setup": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int]),
         "pmg_vcycle": (C.c_int, [P, P, P]),
         "hho_spmv": (C.c_int, [P, C.c_int, P, P]),
+        "hho_spmv_f32": (C.c_int, [P, C.c_int, P, P]),
         "hho_solve": (C.c_int, [P, C.c_double, C.c_int, C.c_int, P, C.POINTER(SolveInfo)]),
         "hho_recover": (C.c_int, [P, P, P]),
         "hho_errors": (C.c_int, [P, P, P, P, P, C.POINTER(C.c_double)]),
@@ -183,7 +184,8 @@ class Context:
     def assemble_noalloc(self, f, gD, gN, rhs_out=None):
         self._check(self.lib.hho_assemble_noalloc(self.h, _ptr(f), _ptr(gD), _ptr(gN), _ptr(rhs_out)))
 
-    def pmg_setup(self, degrees, smooth_its: int = 2, prec: int = 0):
+    def pmg_setup(self, degrees, smooth_its: int = 2, prec="fp64"):
+        prec = {"fp64": 0, "fp32": 1, 0: 0, 1: 1}[prec]
         arr = (C.c_int * len(degrees))(*degrees)
         self._check(self.lib.pmg_setup(self.h, len(degrees), arr, prec, smooth_its))
         self.degrees = list(degrees)
@@ -193,6 +195,9 @@ class Context:
 
     def spmv(self, level, x, y):
         self._check(self.lib.hho_spmv(self.h, level, _ptr(x), _ptr(y)))
+
+    def spmv_f32(self, level, x, y):
+        self._check(self.lib.hho_spmv_f32(self.h, level, _ptr(x), _ptr(y)))
 
     def solve(self, x, rtol=1e-8, maxit=1000, restart=50, raise_on_fail=True):
         info = SolveInfo()

@@ -232,3 +232,45 @@ def test_substructured_coarse_solver(hho_mod, name, mk, cond):
     res = np.linalg.norm(pmg.levels[0].S @ zz - b) / np.linalg.norm(b)
     assert res < 1e-10, res
     ctx.close()
+
+
+@pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("cond", ["vp", "v"])
+def test_mixed_precision_vcycle_and_solve(hho_mod, name, mk, cond):
+    """FP32 V-cycle inside FP64 FGMRES: FP64 true residual 1e-8 and the error
+    against the oracle's direct solution; the FP32 V-cycle stays within FP32
+    rounding of the FP64 V-cycle."""
+    mesh = mk()
+    k = 3
+    fld = fields.TrigStokes2D()
+    h, rhs_o = _oracle(mesh, k, cond, fld)
+    xd = h.direct_solve(rhs_o)
+    ctx = hho_mod.Context(mesh, k, cond)
+    ctx.assemble(*hho_mod.data_arrays(ctx, fld))
+    n = ctx.ndof(0)
+    rng = np.random.default_rng(4)
+    b = torch.from_numpy(rng.standard_normal(n)).cuda()
+    z64 = torch.empty(n, dtype=torch.float64, device="cuda")
+    z32 = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.pmg_setup([3, 2, 1, 0], prec="fp64")
+    ctx.vcycle(b, z64)
+    x64 = torch.empty(n, dtype=torch.float64, device="cuda")
+    i64 = ctx.solve(x64, rtol=1e-8)
+    ctx.pmg_setup([3, 2, 1, 0], prec="fp32")
+    ctx.vcycle(b, z32)
+    rel = (torch.linalg.norm(z32 - z64) / torch.linalg.norm(z64)).item()
+    assert rel < 1e-4, rel
+    # FP32 level operator against the FP64 one
+    xf = torch.from_numpy(rng.standard_normal(n)).cuda()
+    y64 = torch.empty(n, dtype=torch.float64, device="cuda")
+    y32 = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx.spmv(0, xf, y64)
+    ctx.spmv_f32(0, xf.float(), y32)
+    assert (torch.linalg.norm(y32.double() - y64) / torch.linalg.norm(y64)).item() < 1e-5
+    x32 = torch.empty(n, dtype=torch.float64, device="cuda")
+    i32 = ctx.solve(x32, rtol=1e-8)
+    assert i32["rel_residual"] <= 1e-8
+    assert i32["iterations"] <= 1.1 * i64["iterations"] + 3, (i32, i64)
+    err = np.linalg.norm(x32.cpu().numpy() - xd) / np.linalg.norm(xd)
+    assert err < 1e-6, err
+    ctx.close()
