@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of the headline")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--coarse-fp32", type=int, default=1, choices=[0, 1],
+                    help="FP32 coarse solve inside the FP32 V-cycle (velocity-only condensation default)")
     return ap.parse_args()
 
 
@@ -223,6 +225,7 @@ def run_ours(args):
             ms64, inf64 = timed_solves(args.steps, "fp64_step")
             fp64 = {"ms_per_solve": ms64, "fgmres_iterations": inf64[-1]["iterations"],
                     "rel_residual": inf64[-1]["rel_residual"], "dof_per_s": ndof / (ms64 / 1e3)}
+        ctx.set_option("coarse_fp32", args.coarse_fp32 if args.prec == "fp32" else 0)
         ctx.pmg_setup(degrees, smooth_its=2, prec=args.prec)
         for _ in range(args.warmup):
             info = ctx.solve(x, rtol=args.rtol)
@@ -304,7 +307,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 FGMRES + f32 V-cycle" if args.prec == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": wname, "vcycle_precision": args.prec, "dofs": ndof,
+            "config": {"workload": wname, "vcycle_precision": args.prec,
+                       "coarse_precision": "fp32" if (args.prec == "fp32" and args.coarse_fp32) else "fp64",
+                       "dofs": ndof,
                        "fgmres_iterations": last["iterations"], "coarse_iterations": last["coarse_iterations"],
                        "rel_residual_fp64": last["rel_residual"], "fp64_vcycle": fp64,
                        "speedup_vs_fp64_vcycle": (fp64["ms_per_solve"] / ms) if fp64 else None,

@@ -151,7 +151,8 @@ hho_status hho_assemble_noalloc(hho_ctx* ctx, const double* d_f, const double* d
  * smoothing (the paper uses 2). */
 hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, int smooth_its);
 
-/* Solver options (take effect at the next pmg_setup).  Keys:
+/* Solver options.  "coarse_dense_max", "dd_elements" and "coarse_fp32" take
+ * effect at the next pmg_setup.  Keys:
  *   "coarse_dense_max"  largest coarse level solved by the dense inverse
  *                       (default 10000 unknowns); larger coarse levels use
  *                       the substructured direct solver
@@ -163,11 +164,23 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
  *                       (input, output) pair of device buffers; 0: launch
  *                       kernels directly.  The legacy default stream is never
  *                       captured.
- *   "spmv_rows"         rows of one face or element handled by one thread in
- *                       the operator kernels, 1..4 (0 = automatic)
+ *   "spmv_rows"         0 (default): operator kernels specialised for the
+ *                       face block size (2, 3, 4, 6, 8, 9, 10, 12, 18, 30
+ *                       unknowns), generic kernel for other sizes; 1..4: the
+ *                       generic kernel with that many rows of a face or
+ *                       element per thread
  *   "spmv_grid"         blocks of 256 threads of the operator kernels,
  *                       1..8192 (0 = automatic: about one 32-row tile per warp)
- * Returns HHO_ERR_ARG for an unknown key or an invalid value. */
+ *   "coarse_fp32"       with HHO_FP32: 1 keeps FP32 copies of the coarse
+ *                       solver's inverse blocks and runs the coarse solve in
+ *                       FP32 (FP32 multiply-adds, no FP64 round trip);
+ *                       0 (default): FP64 coarse solve.  The FP32 coarse
+ *                       solve can cost FGMRES iterations when the coarse
+ *                       operator is badly conditioned (velocity-pressure
+ *                       condensation).  Copies are made at pmg_setup;
+ *                       setting 0 afterwards switches back at once.
+ * "graphs", "spmv_rows", "spmv_grid" and a later "coarse_fp32" = 0 act at the
+ * next V-cycle.  Returns HHO_ERR_ARG for an unknown key or an invalid value. */
 hho_status hho_set_option(hho_ctx* ctx, const char* key, double value);
 
 /* One V-cycle MG_V(0, r, 0) of the Algorithm of Sec. 3.3: d_z = MG(d_r).

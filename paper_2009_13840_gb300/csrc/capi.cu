@@ -174,6 +174,14 @@ hho_status hho_set_option(hho_ctx* ctx, const char* key, double value) {
         ctx->use_graphs = value != 0.0;
         return HHO_OK;
     }
+    if (k == "coarse_fp32") {
+        if (value != 0.0 && value != 1.0) {
+            ctx->err = "hho_set_option: coarse_fp32 must be 0 or 1";
+            return HHO_ERR_ARG;
+        }
+        ctx->coarse_fp32 = value != 0.0 ? 1 : 0;
+        return HHO_OK;
+    }
     if (k == "spmv_rows" || k == "spmv_grid") {
         if (value < 0.0 || (k == "spmv_rows" && value > 4.0) || (k == "spmv_grid" && value > 8192.0)) {
             ctx->err = "hho_set_option: spmv_rows must be 0..4 and spmv_grid 0..8192";

@@ -155,13 +155,24 @@ __global__ void k_gj_elim(double* __restrict__ A, double* __restrict__ Ai, int64
     }
 }
 
-// y = A x (row-major dense), one warp per row
-__global__ void k_gemv(const double* __restrict__ A, int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+// y = A x (row-major dense), one warp per row; four independent partial sums
+// per lane keep four loads of the row in flight
+template <typename T>
+__global__ void k_gemv(const T* __restrict__ A, int64_t n, const T* __restrict__ x, T* __restrict__ y) {
     int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     for (int64_t r = w; r < n; r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        double s = 0.0;
-        for (int64_t c = lane; c < n; c += 32) s += A[r * n + c] * x[c];
+        const T* a = A + r * n;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        int64_t c = lane;
+        for (; c + 96 < n; c += 128) {
+            s0 += __ldg(a + c) * x[c];
+            s1 += __ldg(a + c + 32) * x[c + 32];
+            s2 += __ldg(a + c + 64) * x[c + 64];
+            s3 += __ldg(a + c + 96) * x[c + 96];
+        }
+        for (; c < n; c += 32) s0 += __ldg(a + c) * x[c];
+        T s = (s0 + s1) + (s2 + s3);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) y[r] = s;
     }
@@ -266,43 +277,51 @@ __global__ void k_mean_abs_diag_level(int64_t nf, int64_t ne, int b, int nP, con
 }
 
 // dI = d[interior unknowns]
-__global__ void k_dd_gather(int64_t nIt, const int32_t* __restrict__ flat_glob, const double* __restrict__ d,
-                            double* __restrict__ dI) {
+template <typename T>
+__global__ void k_dd_gather(int64_t nIt, const int32_t* __restrict__ flat_glob, const T* __restrict__ d,
+                            T* __restrict__ dI) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nIt; i += (int64_t)gridDim.x * blockDim.x)
         dI[i] = d[flat_glob[i]];
 }
 
 // yI = A_II^{-1} dI per subdomain (thread per interior unknown)
+template <typename T>
 __global__ void k_dd_yI(int64_t nIt, const int32_t* __restrict__ flat_sub, const int64_t* __restrict__ offI,
-                        const int32_t* __restrict__ nI, const int64_t* __restrict__ offA, const double* __restrict__ AinvT,
-                        const double* __restrict__ dI, double* __restrict__ yI) {
+                        const int32_t* __restrict__ nI, const int64_t* __restrict__ offA, const T* __restrict__ AinvT,
+                        const T* __restrict__ dI, T* __restrict__ yI) {
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nIt; f += (int64_t)gridDim.x * blockDim.x) {
         int s = flat_sub[f];
         int64_t o = offI[s];
         int n = nI[s], i = (int)(f - o);
-        const double* A = AinvT + offA[s] + i;
-        const double* x = dI + o;
-        double acc = 0.0;
-        for (int j = 0; j < n; ++j) acc += A[(int64_t)j * n] * x[j];
-        yI[f] = acc;
+        const T* A = AinvT + offA[s] + i;
+        const T* x = dI + o;
+        T a0 = T(0), a1 = T(0);
+        int j = 0;
+        for (; j + 1 < n; j += 2) {
+            a0 += __ldg(A + (int64_t)j * n) * x[j];
+            a1 += __ldg(A + (int64_t)(j + 1) * n) * x[j + 1];
+        }
+        if (j < n) a0 += __ldg(A + (int64_t)j * n) * x[j];
+        yI[f] = a0 + a1;
     }
 }
 
 // rG[g] = d[gam_glob[g]] - sum over its subdomains of (A_GI yI)[j], warp per g, fixed order
+template <typename T>
 __global__ void k_dd_rG(int64_t nG, const int32_t* __restrict__ gam_glob, const int32_t* __restrict__ g_ptr,
                         const int32_t* __restrict__ g_s, const int32_t* __restrict__ g_j, const int32_t* __restrict__ nI,
                         const int64_t* __restrict__ offI, const int64_t* __restrict__ offAG,
-                        const double* __restrict__ AGI, const double* __restrict__ yI, const double* __restrict__ d,
-                        double* __restrict__ rG) {
+                        const T* __restrict__ AGI, const T* __restrict__ yI, const T* __restrict__ d,
+                        T* __restrict__ rG) {
     int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     for (int64_t g = w; g < nG; g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        double v = d[gam_glob[g]];
+        T v = d[gam_glob[g]];
         for (int c = g_ptr[g]; c < g_ptr[g + 1]; ++c) {
             int s = g_s[c], j = g_j[c], n = nI[s];
-            const double* a = AGI + offAG[s] + (int64_t)j * n;
-            const double* y = yI + offI[s];
-            double acc = 0.0;
+            const T* a = AGI + offAG[s] + (int64_t)j * n;
+            const T* y = yI + offI[s];
+            T acc = T(0);
             for (int i = lane; i < n; i += 32) acc += a[i] * y[i];
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             v -= acc;
@@ -312,33 +331,36 @@ __global__ void k_dd_rG(int64_t nG, const int32_t* __restrict__ gam_glob, const 
 }
 
 // c[interior] = yI - X cG_s
+template <typename T>
 __global__ void k_dd_cI(int64_t nIt, const int32_t* __restrict__ flat_sub, const int32_t* __restrict__ flat_glob,
                         const int64_t* __restrict__ offI, const int32_t* __restrict__ nI, const int32_t* __restrict__ nGs,
                         const int64_t* __restrict__ offX, const int64_t* __restrict__ offGam,
-                        const int32_t* __restrict__ gam_list, const double* __restrict__ XT,
-                        const double* __restrict__ yI, const double* __restrict__ cG, double* __restrict__ c) {
+                        const int32_t* __restrict__ gam_list, const T* __restrict__ XT,
+                        const T* __restrict__ yI, const T* __restrict__ cG, T* __restrict__ c) {
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nIt; f += (int64_t)gridDim.x * blockDim.x) {
         int s = flat_sub[f];
         int n = nI[s], i = (int)(f - offI[s]), m = nGs[s];
-        const double* X = XT + offX[s] + i;
+        const T* X = XT + offX[s] + i;
         const int32_t* gam = gam_list + offGam[s];
-        double acc = yI[f];
+        T acc = yI[f];
         for (int j = 0; j < m; ++j) acc -= X[(int64_t)j * n] * cG[gam[j]];
         c[flat_glob[f]] = acc;
     }
 }
 
-__global__ void k_dd_scatter_G(int64_t nG, const int32_t* __restrict__ gam_glob, const double* __restrict__ cG,
-                               double* __restrict__ c) {
+template <typename T>
+__global__ void k_dd_scatter_G(int64_t nG, const int32_t* __restrict__ gam_glob, const T* __restrict__ cG,
+                               T* __restrict__ c) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nG; g += (int64_t)gridDim.x * blockDim.x)
         c[gam_glob[g]] = cG[g];
 }
 
-__global__ void k_null_dot(int64_t n, const double* __restrict__ nv, const double* __restrict__ x, double* __restrict__ out) {
+template <typename T>
+__global__ void k_null_dot(int64_t n, const double* __restrict__ nv, const T* __restrict__ x, double* __restrict__ out) {
     // single block, fixed order tree
     __shared__ double sm[256];
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += nv[i] * x[i];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += nv[i] * (double)x[i];
     sm[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -348,10 +370,16 @@ __global__ void k_null_dot(int64_t n, const double* __restrict__ nv, const doubl
     if (threadIdx.x == 0) *out = sm[0];
 }
 
-__global__ void k_null_sub(int64_t n, const double* __restrict__ nv, const double* __restrict__ dot, double* __restrict__ x) {
-    double a = *dot;
+template <typename T>
+__global__ void k_null_sub(int64_t n, const double* __restrict__ nv, const double* __restrict__ dot, T* __restrict__ x) {
+    const double a = *dot;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] -= a * nv[i];
+        x[i] = T((double)x[i] - a * nv[i]);
+}
+
+__global__ void k_to_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
 }
 
 }  // namespace
@@ -371,6 +399,10 @@ struct CoarseSolver {
     int64_t *offI = nullptr, *offA = nullptr, *offX = nullptr, *offAG = nullptr, *offGam = nullptr,
             *elem_loc_off = nullptr;
     double *AinvT = nullptr, *XT = nullptr, *AGI = nullptr, *dI = nullptr, *yI = nullptr, *rG = nullptr, *cG = nullptr;
+    // FP32 copies of the solve operators and work vectors (mixed-precision V-cycle)
+    int64_t nAinv = 0, nAinvT = 0, nXT = 0, nAGI = 0;
+    float *Ainv32 = nullptr, *AinvT32 = nullptr, *XT32 = nullptr, *AGI32 = nullptr, *dI32 = nullptr, *yI32 = nullptr,
+          *rG32 = nullptr, *cG32 = nullptr;
 };
 
 void coarse_free(hho_ctx* ctx) {
@@ -378,7 +410,8 @@ void coarse_free(hho_ctx* ctx) {
     if (!C) return;
     void* ps[] = {C->Ainv, C->nullv, C->scal, C->sub_elem_ptr, C->sub_elem, C->nI, C->nGs, C->flat_sub, C->flat_glob,
                   C->gam_list, C->gam_glob, C->g_ptr, C->g_s, C->g_j, C->elem_loc, C->offI, C->offA, C->offX,
-                  C->offAG, C->offGam, C->elem_loc_off, C->AinvT, C->XT, C->AGI, C->dI, C->yI, C->rG, C->cG};
+                  C->offAG, C->offGam, C->elem_loc_off, C->AinvT, C->XT, C->AGI, C->dI, C->yI, C->rG, C->cG,
+                  C->Ainv32, C->AinvT32, C->XT32, C->AGI32, C->dI32, C->yI32, C->rG32, C->cG32};
     for (void* p : ps) dfree(p);
     delete C;
     ctx->coarse = nullptr;
@@ -654,6 +687,10 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
     HHO_TRY(dalloc(ctx, &scratch, std::max<int64_t>(tW, 1)));
     HHO_TRY(dalloc(ctx, &G, (size_t)nG * nG));
     HHO_TRY(dalloc(ctx, &C->Ainv, (size_t)nG * nG));
+    C->nAinv = nG * nG;
+    C->nAinvT = tA;
+    C->nXT = tX;
+    C->nAGI = tAG;
     HHO_CUDA(cudaMemsetAsync(G, 0, (size_t)nG * nG * sizeof(double), ctx->stream));
     // pin of the pressure kernel (all-Dirichlet problems)
     int pin_s = -1;
@@ -710,7 +747,38 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
     return st;
 }
 
+static hho_status copy_f32(hho_ctx* ctx, const double* src, int64_t n, float** dst) {
+    if (!src || n <= 0) return HHO_OK;
+    HHO_TRY(dalloc(ctx, dst, (size_t)n));
+    k_to_f32<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, src, *dst);
+    HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
+}
+
+static hho_status coarse_build(hho_ctx* ctx);
+
 hho_status coarse_setup(hho_ctx* ctx) {
+    HHO_TRY(coarse_build(ctx));
+    CoarseSolver* C = ctx->coarse;
+    if (ctx->prec == HHO_FP32 && ctx->coarse_fp32 && ctx->levels.size() > 1) {
+        HHO_TRY(copy_f32(ctx, C->Ainv, C->nAinv, &C->Ainv32));
+        if (C->kind == 1) {
+            HHO_TRY(copy_f32(ctx, C->AinvT, C->nAinvT, &C->AinvT32));
+            HHO_TRY(copy_f32(ctx, C->XT, C->nXT, &C->XT32));
+            HHO_TRY(copy_f32(ctx, C->AGI, C->nAGI, &C->AGI32));
+            HHO_TRY(dalloc(ctx, &C->dI32, (size_t)std::max<int64_t>(C->nIt, 1)));
+            HHO_TRY(dalloc(ctx, &C->yI32, (size_t)std::max<int64_t>(C->nIt, 1)));
+            HHO_TRY(dalloc(ctx, &C->rG32, (size_t)C->nG));
+            HHO_TRY(dalloc(ctx, &C->cG32, (size_t)C->nG));
+        }
+        HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return HHO_OK;
+}
+
+bool coarse_has_f32(const hho_ctx* ctx) { return ctx->coarse && ctx->coarse->Ainv32; }
+
+static hho_status coarse_build(hho_ctx* ctx) {
     coarse_free(ctx);
     CoarseSolver* C = new CoarseSolver();
     ctx->coarse = C;
@@ -732,6 +800,7 @@ hho_status coarse_setup(hho_ctx* ctx) {
         double* A = nullptr;
         HHO_TRY(dalloc(ctx, &A, (size_t)n * n));
         HHO_TRY(dalloc(ctx, &C->Ainv, (size_t)n * n));
+        C->nAinv = n * n;
         HHO_CUDA(cudaMemsetAsync(A, 0, (size_t)n * n * sizeof(double), ctx->stream));
         k_dense_from_level<<<grid1d(n, 128), 128, 0, ctx->stream>>>(L.nf, L.ne, L.b, L.nP, L.ff_col, L.ff_nsl, L.fp_col,
                                                                      L.pf_col, L.pf_nsl, L.ff, L.fp, L.pf, L.pp, A, n);
@@ -748,32 +817,48 @@ hho_status coarse_setup(hho_ctx* ctx) {
     return build_dd(ctx, C);
 }
 
-hho_status coarse_apply(hho_ctx* ctx, const double* d, double* c) {
-    CoarseSolver* C = ctx->coarse;
+template <typename T>
+static hho_status coarse_apply_t(hho_ctx* ctx, CoarseSolver* C, const T* Ainv, const T* AinvT, const T* XT,
+                                 const T* AGI, T* dI, T* yI, T* rG, T* cG, const T* d, T* c) {
     if (C->kind == 0) {
-        k_gemv<<<grid1d(C->n * 32, 256), 256, 0, ctx->stream>>>(C->Ainv, C->n, d, c);
+        k_gemv<T><<<grid1d(C->n * 32, 256), 256, 0, ctx->stream>>>(Ainv, C->n, d, c);
         ++ctx->launches;
     } else {
-        k_dd_gather<<<grid1d(C->nIt, 256), 256, 0, ctx->stream>>>(C->nIt, C->flat_glob, d, C->dI);
-        k_dd_yI<<<grid1d(C->nIt, 128), 128, 0, ctx->stream>>>(C->nIt, C->flat_sub, C->offI, C->nI, C->offA, C->AinvT,
-                                                              C->dI, C->yI);
-        k_dd_rG<<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(C->nG, C->gam_glob, C->g_ptr, C->g_s, C->g_j, C->nI,
-                                                                  C->offI, C->offAG, C->AGI, C->yI, d, C->rG);
-        k_gemv<<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(C->Ainv, C->nG, C->rG, C->cG);
-        k_dd_cI<<<grid1d(C->nIt, 128), 128, 0, ctx->stream>>>(C->nIt, C->flat_sub, C->flat_glob, C->offI, C->nI,
-                                                              C->nGs, C->offX, C->offGam, C->gam_list, C->XT, C->yI,
-                                                              C->cG, c);
-        k_dd_scatter_G<<<grid1d(C->nG, 256), 256, 0, ctx->stream>>>(C->nG, C->gam_glob, C->cG, c);
+        k_dd_gather<T><<<grid1d(C->nIt, 256), 256, 0, ctx->stream>>>(C->nIt, C->flat_glob, d, dI);
+        k_dd_yI<T><<<grid1d(C->nIt, 128), 128, 0, ctx->stream>>>(C->nIt, C->flat_sub, C->offI, C->nI, C->offA, AinvT,
+                                                                 dI, yI);
+        k_dd_rG<T><<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(C->nG, C->gam_glob, C->g_ptr, C->g_s, C->g_j,
+                                                                     C->nI, C->offI, C->offAG, AGI, yI, d, rG);
+        k_gemv<T><<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(Ainv, C->nG, rG, cG);
+        k_dd_cI<T><<<grid1d(C->nIt, 128), 128, 0, ctx->stream>>>(C->nIt, C->flat_sub, C->flat_glob, C->offI, C->nI,
+                                                                 C->nGs, C->offX, C->offGam, C->gam_list, XT, yI, cG,
+                                                                 c);
+        k_dd_scatter_G<T><<<grid1d(C->nG, 256), 256, 0, ctx->stream>>>(C->nG, C->gam_glob, cG, c);
         ctx->launches += 6;
         if (C->nullv) {
-            k_null_dot<<<1, 256, 0, ctx->stream>>>(C->n, C->nullv, c, C->scal + 1);
-            k_null_sub<<<grid1d(C->n, 256), 256, 0, ctx->stream>>>(C->n, C->nullv, C->scal + 1, c);
+            k_null_dot<T><<<1, 256, 0, ctx->stream>>>(C->n, C->nullv, c, C->scal + 1);
+            k_null_sub<T><<<grid1d(C->n, 256), 256, 0, ctx->stream>>>(C->n, C->nullv, C->scal + 1, c);
             ctx->launches += 2;
         }
     }
     HHO_CUDA(cudaGetLastError());
     ctx->coarse_its_total += 1;
     return HHO_OK;
+}
+
+hho_status coarse_apply(hho_ctx* ctx, const double* d, double* c) {
+    CoarseSolver* C = ctx->coarse;
+    return coarse_apply_t<double>(ctx, C, C->Ainv, C->AinvT, C->XT, C->AGI, C->dI, C->yI, C->rG, C->cG, d, c);
+}
+
+hho_status coarse_apply_f32(hho_ctx* ctx, const float* d, float* c) {
+    CoarseSolver* C = ctx->coarse;
+    if (!C->Ainv32) {
+        ctx->err = "coarse solve: no FP32 copy of the coarse operators";
+        return HHO_ERR_STATE;
+    }
+    return coarse_apply_t<float>(ctx, C, C->Ainv32, C->AinvT32, C->XT32, C->AGI32, C->dI32, C->yI32, C->rG32,
+                                 C->cG32, d, c);
 }
 
 }  // namespace hho

@@ -146,6 +146,7 @@ struct hho_ctx {
     int64_t launches = 0;                // kernels launched by the solver entry points
     int64_t coarse_dense_max = 10000;    // options
     int64_t dd_elements = 0;             // 0 = default per dimension
+    int coarse_fp32 = 0;                 // mixed precision: FP32 coarse solve operators
     bool use_graphs = true;              // replay captured V-cycles
     int spmv_rows = 0;                   // rows per thread of the operator kernels (0 = automatic)
     int spmv_grid = 0;                   // blocks of the operator kernels (0 = automatic)
@@ -203,5 +204,8 @@ void invalidate_graphs(hho_ctx* ctx);
 // coarse.cu
 hho_status coarse_setup(hho_ctx* ctx);
 hho_status coarse_apply(hho_ctx* ctx, const double* d, double* c);
+// FP32 coarse solve (FP32 copies of the solve operators; only when they exist)
+bool coarse_has_f32(const hho_ctx* ctx);
+hho_status coarse_apply_f32(hho_ctx* ctx, const float* d, float* c);
 void coarse_free(hho_ctx* ctx);
 }  // namespace hho

@@ -120,77 +120,121 @@ struct AccT<float> {
     using type = float;
 };
 
-// Scalar work done by one thread once the reductions of a kernel are final.
-__device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j) {
-    if (hook == HOOK_START) {
-        double beta = sqrt(sc[0]);
-        sc[1] = beta;
-        sc[2] = 0.0;
-        sc[3] = beta;
-        sc[4] = (beta == 0.0) ? 1.0 : 0.0;
-        sc[5] = beta;
-        for (int i = 0; i <= L.m; ++i) sc[L.g + i] = 0.0;
-        sc[L.g] = beta;
-    } else if (hook == HOOK_COLUMN) {
-        double* H = sc + L.H;
-        const int ld = L.m + 1;
-        if (sc[4] != 0.0) {  // after a breakdown the remaining columns are ignored
-            for (int i = 0; i <= L.m; ++i) H[j * ld + i] = 0.0;
-            sc[5] = 0.0;
-            return;
-        }
-        for (int i = 0; i <= j; ++i) H[j * ld + i] = sc[L.t1 + i] + sc[L.t2 + i];
-        double hn = sqrt(sc[L.nrm]);
-        H[j * ld + j + 1] = hn;
-        sc[5] = hn;
-        for (int i = 0; i < j; ++i) {
-            double c = sc[L.cs + i], s = sc[L.sn + i];
-            double a = H[j * ld + i], bb = H[j * ld + i + 1];
-            H[j * ld + i] = c * a + s * bb;
-            H[j * ld + i + 1] = -s * a + c * bb;
-        }
-        double a = H[j * ld + j], bb = H[j * ld + j + 1];
-        double r = hypot(a, bb);
-        double c = (r == 0.0) ? 1.0 : a / r, s = (r == 0.0) ? 0.0 : bb / r;
-        sc[L.cs + j] = c;
-        sc[L.sn + j] = s;
-        H[j * ld + j] = r;
-        H[j * ld + j + 1] = 0.0;
-        double gj = sc[L.g + j];
-        sc[L.g + j] = c * gj;
-        sc[L.g + j + 1] = -s * gj;
-        sc[3] = fabs(sc[L.g + j + 1]);
-        sc[2] = j + 1;
-        if (hn == 0.0) sc[4] = 1.0;
+constexpr int MMAX = 64;  // largest GMRES restart
+
+// 1 / *den (0 when *den is 0) computed once per block: divisions, FP64 ones in
+// particular, are costly per thread.  Call from all threads of the block.
+template <typename T>
+__device__ __forceinline__ T block_inverse(const double* __restrict__ den) {
+    __shared__ T s_inv;
+    if (threadIdx.x == 0) {
+        const T dv = (T)*den;
+        s_inv = (dv == T(0)) ? T(0) : T(1) / dv;
     }
+    __syncthreads();
+    return s_inv;
 }
 
-// Block reduction of the accumulators acc[0..nv-1] and, when self is set, of
-// acc[NV-1] as output nv; partial sums per block; the last block adds the
-// partials in index order into out[0..nv+self-1] and runs the hook.  (Output
-// slots are mapped here, in shared memory, so that no register array is
-// indexed by a run-time value.)
+// Scalar work once the reductions of a kernel are final, run by the whole last
+// block: the operands are first staged in shared memory by all threads in one
+// round of loads, then one thread does the short serial recurrence there, in
+// the arithmetic type A of the kernel (FP32 for the FP32 V-cycle: FP64
+// arithmetic is scarce on this part, and storage stays FP64).
+//   START   fresh = ||r||^2: beta, residual estimate, g = beta e_1
+//   COLUMN  fresh = ||w||^2 after the second projection: Hessenberg column j
+//           (t1 + t2, ||w||), the earlier Givens rotations applied to it, the
+//           new rotation, and the updated residual estimate |g_{j+1}|
+template <typename A>
+__device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j, A fresh) {
+    __shared__ A s_h[MMAX + 2], s_cs[MMAX], s_sn[MMAX], s_misc[2];
+    if (hook == HOOK_START) {
+        const A beta = sqrt(fresh);
+        for (int i = threadIdx.x; i <= L.m; i += blockDim.x) sc[L.g + i] = (i == 0) ? (double)beta : 0.0;
+        if (threadIdx.x == 0) {
+            sc[1] = beta;
+            sc[2] = 0.0;
+            sc[3] = beta;
+            sc[4] = (beta == A(0)) ? 1.0 : 0.0;
+            sc[5] = beta;
+        }
+        return;
+    }
+    if (hook != HOOK_COLUMN) return;
+    const int ld = L.m + 1;
+    double* H = sc + L.H;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        s_h[i] = (A)sc[L.t1 + i] + (A)sc[L.t2 + i];
+        if (i < j) {
+            s_cs[i] = (A)sc[L.cs + i];
+            s_sn[i] = (A)sc[L.sn + i];
+        }
+    }
+    if (threadIdx.x == 0) {
+        s_misc[0] = (A)sc[4];
+        s_misc[1] = (A)sc[L.g + j];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (s_misc[0] != A(0)) {  // after a breakdown the remaining columns are ignored
+        for (int i = 0; i <= L.m; ++i) H[j * ld + i] = 0.0;
+        sc[5] = 0.0;
+        return;
+    }
+    const A hn = sqrt(fresh);
+    s_h[j + 1] = hn;
+    sc[5] = hn;
+    for (int i = 0; i < j; ++i) {
+        const A c = s_cs[i], s = s_sn[i];
+        const A a = s_h[i], bb = s_h[i + 1];
+        s_h[i] = c * a + s * bb;
+        s_h[i + 1] = -s * a + c * bb;
+    }
+    const A a = s_h[j], bb = s_h[j + 1];
+    const A r = hypot(a, bb);
+    const A c = (r == A(0)) ? A(1) : a / r, s = (r == A(0)) ? A(0) : bb / r;
+    s_h[j] = r;
+    s_h[j + 1] = A(0);
+    for (int i = 0; i <= j + 1; ++i) H[j * ld + i] = s_h[i];
+    sc[L.cs + j] = c;
+    sc[L.sn + j] = s;
+    const A gj = s_misc[1];
+    sc[L.g + j] = c * gj;
+    sc[L.g + j + 1] = -s * gj;
+    sc[3] = fabs(s * gj);
+    sc[2] = j + 1;
+    if (hn == A(0)) sc[4] = 1.0;
+}
+
+// Block reduction of the accumulators acc[0..nv0-1] and, when self is set, of
+// acc[NV-1] as output nv0; partial sums per block; the last block adds the
+// partials in a fixed order into out[0..nv0+self-1] and runs the hook.  All
+// arithmetic is in A (partials are stored as FP64).  Output slots are mapped
+// in shared memory, so that no register array is indexed by a run-time value,
+// and warps shuffle only the slots in use.
 template <int NV, typename A>
 __device__ __forceinline__ void reduce_finish(A (&acc)[NV], int nv0, int self, double* __restrict__ partial,
                                               unsigned* __restrict__ counter, double* __restrict__ out, int hook,
                                               double* sc, GS L, int j) {
     const int nv = nv0 + self;
-    __shared__ double sm[RT / 32][NV];
+    __shared__ A sm[RT / 32][NV];
     __shared__ bool s_last;
+    __shared__ A s_fresh;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        A a = acc[v];
+        if (v < nv0 || (self && v == NV - 1)) {
+            A a = acc[v];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) sm[wid][v] = (double)a;
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) sm[wid][v] = a;
+        }
     }
     __syncthreads();
     if (threadIdx.x < nv) {
         const int src = ((int)threadIdx.x < nv0) ? (int)threadIdx.x : NV - 1;
-        double s = 0.0;
+        A s = A(0);
         for (int w = 0; w < RT / 32; ++w) s += sm[w][src];
-        partial[threadIdx.x * GMAX + blockIdx.x] = s;
+        partial[threadIdx.x * GMAX + blockIdx.x] = (double)s;
     }
     __threadfence();
     __syncthreads();
@@ -198,19 +242,35 @@ __device__ __forceinline__ void reduce_finish(A (&acc)[NV], int nv0, int self, d
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // one warp per dot product: fixed per-lane strides, then a fixed shuffle tree
-    for (int v = wid; v < nv; v += RT / 32) {
-        double s = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partial + v * GMAX + b);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) out[v] = s;
+    // thread t adds the partials of blocks t, t + RT, ...; then a fixed shuffle
+    // tree per warp and the warps in index order
+    A ps[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ps[v] = A(0);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += RT) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            if (v < nv) ps[v] += (A)__ldcg(partial + v * GMAX + b);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        if (v < nv) {
+            A a = ps[v];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) sm[wid][v] = a;
+        }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        *counter = 0u;
-        run_hook(hook, sc, L, j);
-        __threadfence();
+    if (threadIdx.x < nv) {
+        A s = A(0);
+        for (int w = 0; w < RT / 32; ++w) s += sm[w][threadIdx.x];
+        out[threadIdx.x] = (double)s;
+        if (threadIdx.x == 0) s_fresh = s;
     }
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    run_hook<A>(hook, sc, L, j, s_fresh);
 }
 
 // dacc[q] += V_q[o] * v for q < nv, dacc[NVMAX] += v * v: fully unrolled with
@@ -373,6 +433,7 @@ __global__ void __launch_bounds__(RT) k_spmv_b(LV<T> L, Items it, const T* __res
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nf = L.nf, ne = L.ne;
     const int nP = L.nP;
+    constexpr int CU = B <= 12 ? B : 2;  // column unrolling
     using A = typename AccT<T>::type;
     A dacc[NVMAX + 1];
 #pragma unroll
@@ -389,15 +450,14 @@ __global__ void __launch_bounds__(RT) k_spmv_b(LV<T> L, Items it, const T* __res
             for (int i = 0; i < RF; ++i) acc[i] = T(0);
             const int ns = L.ff_nsl[F];
             for (int s = 0; s < ns; ++s) {
-                const int64_t G = L.ff_col[s * nf + F];
-                T xc[B];
-#pragma unroll
-                for (int c = 0; c < B; ++c) xc[c] = x[G * B + c];
+                const T* xv = x + (int64_t)L.ff_col[s * nf + F] * B;
                 const T* a = L.ff + ((int64_t)s * B * B + r0) * nf + F;
+#pragma unroll(CU)
+                for (int c = 0; c < B; ++c) {
+                    const T xc = xv[c];
 #pragma unroll
-                for (int c = 0; c < B; ++c)
-#pragma unroll
-                    for (int i = 0; i < RF; ++i) acc[i] += __ldg(a + (int64_t)(c * B + i) * nf) * xc[c];
+                    for (int i = 0; i < RF; ++i) acc[i] += __ldg(a + (int64_t)(c * B + i) * nf) * xc;
+                }
             }
             for (int p = 0; p < 2; ++p) {
                 const int Tl = L.fp_col[p * nf + F];
@@ -423,34 +483,30 @@ __global__ void __launch_bounds__(RT) k_spmv_b(LV<T> L, Items it, const T* __res
             const int r0 = (int)(ww % it.egroups) * RP;
             const int64_t E = tile * 32 + lane;
             if (E >= ne) continue;
-            const int nr = min(RP, nP - r0);
             T acc[RP];
 #pragma unroll
             for (int i = 0; i < RP; ++i) acc[i] = T(0);
             const int N = L.pf_nsl[E];
             for (int f = 0; f < N; ++f) {
-                const int64_t G = L.pf_col[f * ne + E];
-                T xc[B];
-#pragma unroll
-                for (int c = 0; c < B; ++c) xc[c] = x[G * B + c];
+                const T* xv = x + (int64_t)L.pf_col[f * ne + E] * B;
                 const T* a = L.pf + ((int64_t)f * B * nP + r0) * ne + E;
+#pragma unroll 2
+                for (int c = 0; c < B; ++c) {
+                    const T xc = xv[c];
 #pragma unroll
-                for (int c = 0; c < B; ++c)
-#pragma unroll
-                    for (int i = 0; i < RP; ++i)
-                        if (i < nr) acc[i] += __ldg(a + (int64_t)(c * nP + i) * ne) * xc[c];
+                    for (int i = 0; i < RP; ++i) acc[i] += __ldg(a + (int64_t)(c * nP + i) * ne) * xc;
+                }
             }
             const T* xp = x + nf * B + E * nP;
+#pragma unroll 2
             for (int c = 0; c < nP; ++c) {
                 const T xc = xp[c];
                 const T* a = L.pp + ((int64_t)c * nP + r0) * ne + E;
 #pragma unroll
-                for (int i = 0; i < RP; ++i)
-                    if (i < nr) acc[i] += __ldg(a + (int64_t)i * ne) * xc;
+                for (int i = 0; i < RP; ++i) acc[i] += __ldg(a + (int64_t)i * ne) * xc;
             }
 #pragma unroll
             for (int i = 0; i < RP; ++i) {
-                if (i >= nr) break;
                 const int64_t o = nf * B + E * nP + r0 + i;
                 const T v = mode ? T(bv[o] - acc[i]) : acc[i];
                 y[o] = v;
@@ -513,8 +569,7 @@ __global__ void __launch_bounds__(RT) k_residual_restrict(LV<T> L, Items it, int
 template <typename T>
 __global__ void k_apply_jacobi(LV<T> L, const T* __restrict__ w, const double* __restrict__ den, T* __restrict__ v,
                                T* __restrict__ z) {
-    const double dv = *den;
-    const T inv = (dv == 0.0) ? T(0) : T(1.0 / dv);
+    const T inv = block_inverse<T>(den);
     const int64_t nfr = L.nf * L.b, ner = L.ne * L.nP;
     const int b = L.b, nP = L.nP;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
@@ -541,10 +596,72 @@ __global__ void k_apply_jacobi(LV<T> L, const T* __restrict__ w, const double* _
     }
 }
 
+// Same operation with the face block size B known at compile time: a thread
+// holds RF rows of one face (its B values of w loaded once) or RP rows of one
+// element; the block values are read coalesced across the 32 faces (elements)
+// of a warp.  Work items as in k_spmv_b.
+template <int B, int RF, int RP, typename T>
+__global__ void __launch_bounds__(RT) k_jacobi_b(LV<T> L, Items it, const T* __restrict__ w,
+                                                  const double* __restrict__ den, T* __restrict__ v,
+                                                  T* __restrict__ z) {
+    const T inv = block_inverse<T>(den);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nf = L.nf, ne = L.ne;
+    const int nP = L.nP;
+    constexpr int CU = B <= 12 ? B : 2;  // column unrolling
+    const int64_t nfi = it.ftiles * it.fgroups;
+    for (int64_t wi = warp; wi < it.total(); wi += nwarps) {
+        if (wi < nfi) {
+            const int64_t F = (wi / it.fgroups) * 32 + lane;
+            const int r0 = (int)(wi % it.fgroups) * RF;
+            if (F >= nf) continue;
+            const T* wv = w + F * B;
+            T acc[RF];
+#pragma unroll
+            for (int i = 0; i < RF; ++i) acc[i] = T(0);
+            const T* a = L.dinv + (int64_t)r0 * nf + F;
+#pragma unroll(CU)
+            for (int c = 0; c < B; ++c) {
+                const T wc = wv[c];
+#pragma unroll
+                for (int i = 0; i < RF; ++i) acc[i] += __ldg(a + (int64_t)(c * B + i) * nf) * wc;
+            }
+#pragma unroll
+            for (int i = 0; i < RF; ++i) {
+                z[F * B + r0 + i] = acc[i] * inv;
+                v[F * B + r0 + i] = w[F * B + r0 + i] * inv;
+            }
+        } else {
+            const int64_t ww = wi - nfi;
+            const int64_t E = (ww / it.egroups) * 32 + lane;
+            const int r0 = (int)(ww % it.egroups) * RP;
+            if (E >= ne) continue;
+            const T* wv = w + nf * B + E * nP;
+            T acc[RP];
+#pragma unroll
+            for (int i = 0; i < RP; ++i) acc[i] = T(0);
+            const T* a = L.minv + (int64_t)r0 * ne + E;
+#pragma unroll 2
+            for (int c = 0; c < nP; ++c) {
+                const T wc = wv[c];
+#pragma unroll
+                for (int i = 0; i < RP; ++i) acc[i] += __ldg(a + (int64_t)(c * nP + i) * ne) * wc;
+            }
+#pragma unroll
+            for (int i = 0; i < RP; ++i) {
+                const int64_t o = nf * B + E * nP + r0 + i;
+                z[o] = acc[i] * inv;
+                v[o] = wv[r0 + i] * inv;
+            }
+        }
+    }
+}
+
 // v = w / den (FGMRES basis vector)
 __global__ void k_scale(int64_t n, const double* __restrict__ w, const double* __restrict__ den, double* __restrict__ v) {
-    const double dv = *den;
-    const double inv = (dv == 0.0) ? 0.0 : 1.0 / dv;
+    const double inv = block_inverse<double>(den);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         v[i] = w[i] * inv;
 }
@@ -572,30 +689,33 @@ __global__ void __launch_bounds__(RT) k_update_dot(int64_t n, T* __restrict__ w,
     if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
 }
 
-// x = a0 x + Z y with y = R^{-1} g solved redundantly by every block (m <= 64).
+// x = a0 x + Z y with y = R^{-1} g solved redundantly by every block (m <= 64):
+// the triangle of H and g are staged in shared memory by all threads, then one
+// thread back-substitutes there.  Dynamic shared memory: xupd_smem(m) bytes.
 template <typename T>
 __global__ void k_update_x(int64_t n, T* __restrict__ x, double a0, const T* __restrict__ Z, int64_t ld,
                            const double* __restrict__ sc, GS L) {
-    __shared__ double y[64];
+    extern __shared__ double s_dyn[];
+    using A = typename AccT<T>::type;
+    __shared__ A ya[MMAX];
+    const int ld2 = L.m + 1;
+    double* Hs = s_dyn;
+    double* y = s_dyn + ld2 * L.m;
+    const int me = (sc[1] == 0.0) ? 0 : (int)sc[2];
+    for (int i = threadIdx.x; i < ld2 * me; i += blockDim.x) Hs[i] = sc[L.H + i];
+    for (int i = threadIdx.x; i < me; i += blockDim.x) y[i] = sc[L.g + i];
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const double* H = sc + L.H;
-        const int ld2 = L.m + 1;
-        int me = (int)sc[2];
-        if (sc[1] == 0.0) me = 0;
-        for (int i = 0; i < L.m; ++i) y[i] = 0.0;
         for (int i = me - 1; i >= 0; --i) {
-            double s = sc[L.g + i];
-            for (int l = i + 1; l < me; ++l) s -= H[l * ld2 + i] * y[l];
-            const double dd = H[i * ld2 + i];
+            double s = y[i];
+            for (int l = i + 1; l < me; ++l) s -= Hs[l * ld2 + i] * y[l];
+            const double dd = Hs[i * ld2 + i];
             y[i] = (dd == 0.0) ? 0.0 : s / dd;
         }
     }
     __syncthreads();
-    using A = typename AccT<T>::type;
-    __shared__ A ya[64];
-    if (threadIdx.x < 64) ya[threadIdx.x] = (threadIdx.x < L.m) ? (A)y[threadIdx.x] : A(0);
+    if (threadIdx.x < MMAX) ya[threadIdx.x] = ((int)threadIdx.x < me) ? (A)y[threadIdx.x] : A(0);
     __syncthreads();
-    const int me = (sc[1] == 0.0) ? 0 : (int)sc[2];
     const A a0a = (A)a0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         A s = (a0 == 0.0) ? A(0) : a0a * (A)x[i];
@@ -603,6 +723,8 @@ __global__ void k_update_x(int64_t n, T* __restrict__ x, double a0, const T* __r
         x[i] = T(s);
     }
 }
+
+size_t xupd_smem(int m) { return (size_t)((m + 1) * m + m) * sizeof(double); }
 
 // x += zero-padded xc (prolongation)
 template <typename T>
@@ -735,26 +857,75 @@ constexpr int face_rows_for(int B) {
     return B <= 4 ? B : (B % 2 == 0 && B <= 12 ? B / 2 : (B % 3 == 0 ? (B / 3 <= 10 ? B / 3 : B / 6) : B));
 }
 
+// rows of an element held by one thread: a divisor of the pressure block size
+// that the degree behind B gives under velocity-only condensation
+// (2D: B = 2(k+1), nP = (k+1)(k+2)/2; 3D: B = 3(k+1)(k+2)/2,
+// nP = (k+1)(k+2)(k+3)/6); a level whose nP it does not divide (one pressure
+// per element under velocity-pressure condensation) uses RP = 1
+constexpr int elem_rows_for(int B) {
+    return B == 4 ? 3 : B == 6 ? 3 : B == 8 ? 5 : B == 10 ? 5 : B == 12 ? 7 : B == 9 ? 4 : B == 18 ? 5 : B == 30 ? 5 : 1;
+}
+
+template <int B>
+static Items items_b(const LevelMat& L, int RP) {
+    Items it;
+    it.ftiles = (L.nf + 31) / 32;
+    it.etiles = (L.ne + 31) / 32;
+    it.fgroups = B / face_rows_for(B);
+    it.egroups = (L.nP + RP - 1) / RP;
+    return it;
+}
+
 template <int B, typename T>
 static bool launch_spmv_b_B(hho_ctx* ctx, const LevelMat& L, const T* x, const T* bv, T* y, int mode, const T* V,
                             int64_t ld, int nv, int self, double* partial, unsigned* counter, double* out, int hook,
                             double* sc, GS gsl, int j) {
     constexpr int RF = face_rows_for(B);
-    const int RP = L.nP == 1 ? 1 : 4;
-    Items it;
-    it.ftiles = (L.nf + 31) / 32;
-    it.etiles = (L.ne + 31) / 32;
-    it.fgroups = B / RF;
-    it.egroups = (L.nP + RP - 1) / RP;
+    constexpr int RPB = elem_rows_for(B);
+    const int RP = (L.nP % RPB == 0) ? RPB : 1;  // element row groups are always full
+    const Items it = items_b<B>(L, RP);
     const int g = op_grid(ctx, it);
     const LV<T> lv = view<T>(L);
     if (RP == 1)
         k_spmv_b<B, RF, 1, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter, out,
                                                          hook, sc, gsl, j);
     else
-        k_spmv_b<B, RF, 4, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter, out,
-                                                         hook, sc, gsl, j);
+        k_spmv_b<B, RF, RPB, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter,
+                                                           out, hook, sc, gsl, j);
     return true;
+}
+
+template <int B, typename T>
+static void launch_jacobi_b_B(hho_ctx* ctx, const LevelMat& L, const T* w, const double* den, T* v, T* z) {
+    constexpr int RF = face_rows_for(B);
+    constexpr int RPB = elem_rows_for(B);
+    const int RP = (L.nP % RPB == 0) ? RPB : 1;  // element row groups are always full
+    const Items it = items_b<B>(L, RP);
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>((it.total() + RT / 32 - 1) / (RT / 32), GMAX));
+    const LV<T> lv = view<T>(L);
+    if (RP == 1) k_jacobi_b<B, RF, 1, T><<<(int)g, RT, 0, ctx->stream>>>(lv, it, w, den, v, z);
+    else k_jacobi_b<B, RF, RPB, T><<<(int)g, RT, 0, ctx->stream>>>(lv, it, w, den, v, z);
+}
+
+// v = w / den, z = M^{-1} v: the compile-time block size kernel where B is one
+// of the instantiated sizes, else the generic one
+template <typename T>
+static void launch_jacobi(hho_ctx* ctx, const LevelMat& L, const T* w, const double* den, T* v, T* z) {
+    switch (L.b) {
+        case 2: launch_jacobi_b_B<2, T>(ctx, L, w, den, v, z); break;
+        case 3: launch_jacobi_b_B<3, T>(ctx, L, w, den, v, z); break;
+        case 4: launch_jacobi_b_B<4, T>(ctx, L, w, den, v, z); break;
+        case 6: launch_jacobi_b_B<6, T>(ctx, L, w, den, v, z); break;
+        case 8: launch_jacobi_b_B<8, T>(ctx, L, w, den, v, z); break;
+        case 9: launch_jacobi_b_B<9, T>(ctx, L, w, den, v, z); break;
+        case 10: launch_jacobi_b_B<10, T>(ctx, L, w, den, v, z); break;
+        case 12: launch_jacobi_b_B<12, T>(ctx, L, w, den, v, z); break;
+        case 18: launch_jacobi_b_B<18, T>(ctx, L, w, den, v, z); break;
+        case 30: launch_jacobi_b_B<30, T>(ctx, L, w, den, v, z); break;
+        default:
+            k_apply_jacobi<T><<<grid1d(L.n, 256), 256, 0, ctx->stream>>>(view<T>(L), w, den, v, z);
+    }
+    ++ctx->launches;
 }
 
 template <typename T>
@@ -887,17 +1058,15 @@ static hho_status smooth(hho_ctx* ctx, int l, const T* bv, T* x, bool x_zero, bo
         launch_spmv_dot<T>(ctx, l, x, bv, w, 1, nullptr, n, 0, 1, sc + 0, HOOK_START, sc, G, 0);
         w0 = w;
     }
-    const LV<T> lv = view<T>(L);
     for (int j = 0; j < m; ++j) {
         T* vj = V + (int64_t)j * n;
         T* zj = Z + (int64_t)j * n;
-        k_apply_jacobi<T><<<grid1d(n, 256), 256, 0, ctx->stream>>>(lv, j == 0 ? w0 : w, sc + 5, vj, zj);
-        ++ctx->launches;
+        launch_jacobi<T>(ctx, L, j == 0 ? w0 : w, sc + 5, vj, zj);
         launch_spmv_dot<T>(ctx, l, zj, nullptr, w, 0, V, n, j + 1, 0, sc + G.t1, HOOK_NONE, sc, G, j);
         launch_update_dot<T>(ctx, n, w, V, n, j + 1, sc + G.t1, -1.0, V, j + 1, 0, sc + G.t2, HOOK_NONE, sc, G, j);
         launch_update_dot<T>(ctx, n, w, V, n, j + 1, sc + G.t2, -1.0, nullptr, 0, 1, sc + G.nrm, HOOK_COLUMN, sc, G, j);
     }
-    k_update_x<T><<<vgrid(n), RT, 0, ctx->stream>>>(n, x, x_zero ? 0.0 : 1.0, Z, n, sc, G);
+    k_update_x<T><<<vgrid(n), RT, xupd_smem(G.m), ctx->stream>>>(n, x, x_zero ? 0.0 : 1.0, Z, n, sc, G);
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());
     return HHO_OK;
@@ -927,6 +1096,7 @@ hho_status coarse_level<double>(hho_ctx* ctx, int, const double* d, double* c) {
 
 template <>
 hho_status coarse_level<float>(hho_ctx* ctx, int l, const float* d, float* c) {
+    if (ctx->coarse_fp32 && coarse_has_f32(ctx)) return coarse_apply_f32(ctx, d, c);
     LevelWork& lw = ctx->ws->lv[l];
     const int64_t n = ctx->levels[l].n;
     k_convert<float, double><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, d, lw.cd);
@@ -1177,7 +1347,7 @@ hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, 
                 ++ctx->launches;
             }
             // x += Z y over the columns of this cycle
-            k_update_x<double><<<vgrid(n), RT, 0, ctx->stream>>>(n, x, 1.0, W->fZ, n, sc, G);
+            k_update_x<double><<<vgrid(n), RT, xupd_smem(G.m), ctx->stream>>>(n, x, 1.0, W->fZ, n, sc, G);
             ++ctx->launches;
             // true residual, its norm and the START state of the next cycle
             launch_spmv_dot<double>(ctx, 0, x, bvec, W->fw, 1, nullptr, n, 0, 1, sc + 0, HOOK_START, sc, G, 0);
