@@ -20,12 +20,18 @@
 // with its operator stays FP64.
 //
 // Arnoldi steps use classical Gram-Schmidt applied twice (CGS2).  Kernel
-// structure of one Arnoldi step (j):
-//   apply      v_j = w / ||w||, z_j = M^{-1} v_j          (smoother) or a V-cycle
+// structure of one Arnoldi step (j) of the outer FGMRES:
+//   apply      v_j = w / ||w||, z_j = MG(v_j)  (a V-cycle)
 //   spmv+dot   w = S z_j,  t1 = V^T w
 //   upd+dot    w -= V t1,  t2 = V^T w
 //   upd+norm   w -= V t2,  ||w||^2, then the Hessenberg column, Givens rotation
 //              and residual estimate in the last block of the grid
+// and of the smoother, one kernel shorter:
+//   apply      w'' = w' - V t2 (second pass of step j-1), v_j = w'' / ||w''||,
+//              z_j = M^{-1} v_j  (block Jacobi)
+//   spmv+dot   w = S z_j,  t1 = V^T w
+//   upd+dot    w' = w - V t1,  t2 = V^T w',  ||w'||^2, then the Hessenberg
+//              column with ||w''||^2 = ||w'||^2 - ||t2||^2
 // Every dot product is a deterministic two-level reduction inside the kernel
 // that produces its operand: each block writes a partial sum and the last
 // block to finish adds the partials in index order, so results are bitwise
@@ -45,6 +51,7 @@ namespace {
 constexpr int GMAX = 8192;  // largest grid of any reduction kernel
 constexpr int RT = 256;     // threads per block of the reduction kernels
 constexpr int NVMAX = 8;    // dot products per kernel
+constexpr int MMAX = 64;    // largest GMRES restart
 
 int grid1d(int64_t n, int tpb) {
     int64_t g = (n + tpb - 1) / tpb;
@@ -108,7 +115,7 @@ GS gs_layout(int m) {
     return s;
 }
 
-enum Hook { HOOK_NONE = 0, HOOK_START = 1, HOOK_COLUMN = 2 };
+enum Hook { HOOK_NONE = 0, HOOK_START = 1, HOOK_COLUMN = 2, HOOK_COLUMN_PY = 3 };
 
 // Type of the per-thread and per-warp part of a dot product (see the header).
 template <typename T>
@@ -120,7 +127,6 @@ struct AccT<float> {
     using type = float;
 };
 
-constexpr int MMAX = 64;  // largest GMRES restart
 
 // 1 / *den (0 when *den is 0) computed once per block: divisions, FP64 ones in
 // particular, are costly per thread.  Call from all threads of the block.
@@ -135,6 +141,26 @@ __device__ __forceinline__ T block_inverse(const double* __restrict__ den) {
     return s_inv;
 }
 
+// Coefficients of a pending second Gram-Schmidt pass (FP64 storage) staged in
+// shared memory in the level type.  Call from all threads of the block.
+template <typename T>
+__device__ __forceinline__ const T* stage_pending(const double* __restrict__ pc, int npend) {
+    __shared__ T s_pc[MMAX];
+    for (int q = threadIdx.x; q < npend; q += blockDim.x) s_pc[q] = (T)pc[q];
+    __syncthreads();
+    return s_pc;
+}
+
+// w''[o] = w'[o] - sum_{q < npend} pc_q Vp_q[o]: the second pass of the last
+// Arnoldi step, applied where w'' is consumed
+template <typename T>
+__device__ __forceinline__ T pending(const T* __restrict__ w, const T* __restrict__ Vp, int64_t ld, int npend,
+                                     const T* s_pc, int64_t o) {
+    T u = w[o];
+    for (int q = 0; q < npend; ++q) u -= s_pc[q] * Vp[q * ld + o];
+    return u;
+}
+
 // Scalar work once the reductions of a kernel are final, run by the whole last
 // block: the operands are first staged in shared memory by all threads in one
 // round of loads, then one thread does the short serial recurrence there, in
@@ -144,6 +170,10 @@ __device__ __forceinline__ T block_inverse(const double* __restrict__ den) {
 //   COLUMN  fresh = ||w||^2 after the second projection: Hessenberg column j
 //           (t1 + t2, ||w||), the earlier Givens rotations applied to it, the
 //           new rotation, and the updated residual estimate |g_{j+1}|
+//   COLUMN_PY  the same with fresh = ||w'||^2 before the second projection
+//           w'' = w' - V t2 (t2 = V^T w'), which is left to the consumer of
+//           w'': ||w''||^2 = ||w'||^2 - ||t2||^2 for orthonormal V (the
+//           correction t2 is small against w', so the difference is benign)
 template <typename A>
 __device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j, A fresh) {
     __shared__ A s_h[MMAX + 2], s_cs[MMAX], s_sn[MMAX], s_misc[2];
@@ -159,11 +189,14 @@ __device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j, A fr
         }
         return;
     }
-    if (hook != HOOK_COLUMN) return;
+    if (hook != HOOK_COLUMN && hook != HOOK_COLUMN_PY) return;
     const int ld = L.m + 1;
     double* H = sc + L.H;
+    __shared__ A s_t2sq[MMAX + 1];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        s_h[i] = (A)sc[L.t1 + i] + (A)sc[L.t2 + i];
+        const A t2 = (A)sc[L.t2 + i];
+        s_h[i] = (A)sc[L.t1 + i] + t2;
+        s_t2sq[i] = t2 * t2;
         if (i < j) {
             s_cs[i] = (A)sc[L.cs + i];
             s_sn[i] = (A)sc[L.sn + i];
@@ -180,7 +213,12 @@ __device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j, A fr
         sc[5] = 0.0;
         return;
     }
-    const A hn = sqrt(fresh);
+    A hn2 = fresh;
+    if (hook == HOOK_COLUMN_PY) {
+        for (int i = 0; i <= j; ++i) hn2 -= s_t2sq[i];
+        hn2 = hn2 > A(0) ? hn2 : A(0);
+    }
+    const A hn = sqrt(hn2);
     s_h[j + 1] = hn;
     sc[5] = hn;
     for (int i = 0; i < j; ++i) {
@@ -207,7 +245,8 @@ __device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j, A fr
 
 // Block reduction of the accumulators acc[0..nv0-1] and, when self is set, of
 // acc[NV-1] as output nv0; partial sums per block; the last block adds the
-// partials in a fixed order into out[0..nv0+self-1] and runs the hook.  All
+// partials in a fixed order into out[0..nv0+self-1] and runs the hook on the
+// self output (on output 0 without one).  All
 // arithmetic is in A (partials are stored as FP64).  Output slots are mapped
 // in shared memory, so that no register array is indexed by a run-time value,
 // and warps shuffle only the slots in use.
@@ -266,7 +305,7 @@ __device__ __forceinline__ void reduce_finish(A (&acc)[NV], int nv0, int self, d
         A s = A(0);
         for (int w = 0; w < RT / 32; ++w) s += sm[w][threadIdx.x];
         out[threadIdx.x] = (double)s;
-        if (threadIdx.x == 0) s_fresh = s;
+        if ((int)threadIdx.x == (self ? nv0 : 0)) s_fresh = s;
     }
     if (threadIdx.x == 0) *counter = 0u;
     __syncthreads();
@@ -568,8 +607,10 @@ __global__ void __launch_bounds__(RT) k_residual_restrict(LV<T> L, Items it, int
 // v = w / den, z = M^{-1} v (block Jacobi): z is computed from w and scaled.
 template <typename T>
 __global__ void k_apply_jacobi(LV<T> L, const T* __restrict__ w, const double* __restrict__ den, T* __restrict__ v,
-                               T* __restrict__ z) {
+                               T* __restrict__ z, const T* __restrict__ Vp, int64_t ld, int npend,
+                               const double* __restrict__ pc) {
     const T inv = block_inverse<T>(den);
+    const T* s_pc = stage_pending<T>(pc, npend);
     const int64_t nfr = L.nf * L.b, ner = L.ne * L.nP;
     const int b = L.b, nP = L.nP;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
@@ -577,21 +618,20 @@ __global__ void k_apply_jacobi(LV<T> L, const T* __restrict__ w, const double* _
             const int r = (int)(i / L.nf);
             const int64_t F = i % L.nf;
             const T* a = L.dinv + (int64_t)r * L.nf + F;
-            const T* wv = w + F * b;
             T s = T(0);
-            for (int c = 0; c < b; ++c) s += a[(int64_t)c * b * L.nf] * wv[c];
+            for (int c = 0; c < b; ++c) s += a[(int64_t)c * b * L.nf] * pending(w, Vp, ld, npend, s_pc, F * b + c);
             z[F * b + r] = s * inv;
-            v[F * b + r] = wv[r] * inv;
+            v[F * b + r] = pending(w, Vp, ld, npend, s_pc, F * b + r) * inv;
         } else {
             const int64_t jj = i - nfr;
             const int r = (int)(jj / L.ne);
             const int64_t E = jj % L.ne;
             const T* a = L.minv + (int64_t)r * L.ne + E;
-            const T* wv = w + nfr + E * nP;
+            const int64_t ob = nfr + E * nP;
             T s = T(0);
-            for (int c = 0; c < nP; ++c) s += a[(int64_t)c * nP * L.ne] * wv[c];
-            z[nfr + E * nP + r] = s * inv;
-            v[nfr + E * nP + r] = wv[r] * inv;
+            for (int c = 0; c < nP; ++c) s += a[(int64_t)c * nP * L.ne] * pending(w, Vp, ld, npend, s_pc, ob + c);
+            z[ob + r] = s * inv;
+            v[ob + r] = pending(w, Vp, ld, npend, s_pc, ob + r) * inv;
         }
     }
 }
@@ -603,8 +643,10 @@ __global__ void k_apply_jacobi(LV<T> L, const T* __restrict__ w, const double* _
 template <int B, int RF, int RP, typename T>
 __global__ void __launch_bounds__(RT) k_jacobi_b(LV<T> L, Items it, const T* __restrict__ w,
                                                   const double* __restrict__ den, T* __restrict__ v,
-                                                  T* __restrict__ z) {
+                                                  T* __restrict__ z, const T* __restrict__ Vp, int64_t ld,
+                                                  int npend, const double* __restrict__ pc) {
     const T inv = block_inverse<T>(den);
+    const T* s_pc = stage_pending<T>(pc, npend);
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -617,43 +659,42 @@ __global__ void __launch_bounds__(RT) k_jacobi_b(LV<T> L, Items it, const T* __r
             const int64_t F = (wi / it.fgroups) * 32 + lane;
             const int r0 = (int)(wi % it.fgroups) * RF;
             if (F >= nf) continue;
-            const T* wv = w + F * B;
             T acc[RF];
 #pragma unroll
             for (int i = 0; i < RF; ++i) acc[i] = T(0);
             const T* a = L.dinv + (int64_t)r0 * nf + F;
 #pragma unroll(CU)
             for (int c = 0; c < B; ++c) {
-                const T wc = wv[c];
+                const T wc = pending(w, Vp, ld, npend, s_pc, F * B + c);
 #pragma unroll
                 for (int i = 0; i < RF; ++i) acc[i] += __ldg(a + (int64_t)(c * B + i) * nf) * wc;
             }
 #pragma unroll
             for (int i = 0; i < RF; ++i) {
                 z[F * B + r0 + i] = acc[i] * inv;
-                v[F * B + r0 + i] = w[F * B + r0 + i] * inv;
+                v[F * B + r0 + i] = pending(w, Vp, ld, npend, s_pc, F * B + r0 + i) * inv;
             }
         } else {
             const int64_t ww = wi - nfi;
             const int64_t E = (ww / it.egroups) * 32 + lane;
             const int r0 = (int)(ww % it.egroups) * RP;
             if (E >= ne) continue;
-            const T* wv = w + nf * B + E * nP;
+            const int64_t ob = nf * B + E * nP;
             T acc[RP];
 #pragma unroll
             for (int i = 0; i < RP; ++i) acc[i] = T(0);
             const T* a = L.minv + (int64_t)r0 * ne + E;
 #pragma unroll 2
             for (int c = 0; c < nP; ++c) {
-                const T wc = wv[c];
+                const T wc = pending(w, Vp, ld, npend, s_pc, ob + c);
 #pragma unroll
                 for (int i = 0; i < RP; ++i) acc[i] += __ldg(a + (int64_t)(c * nP + i) * ne) * wc;
             }
 #pragma unroll
             for (int i = 0; i < RP; ++i) {
-                const int64_t o = nf * B + E * nP + r0 + i;
+                const int64_t o = ob + r0 + i;
                 z[o] = acc[i] * inv;
-                v[o] = wv[r0 + i] * inv;
+                v[o] = pending(w, Vp, ld, npend, s_pc, o) * inv;
             }
         }
     }
@@ -896,34 +937,38 @@ static bool launch_spmv_b_B(hho_ctx* ctx, const LevelMat& L, const T* x, const T
 }
 
 template <int B, typename T>
-static void launch_jacobi_b_B(hho_ctx* ctx, const LevelMat& L, const T* w, const double* den, T* v, T* z) {
+static void launch_jacobi_b_B(hho_ctx* ctx, const LevelMat& L, const T* w, const double* den, T* v, T* z,
+                              const T* Vp, int64_t ld, int npend, const double* pc) {
     constexpr int RF = face_rows_for(B);
     constexpr int RPB = elem_rows_for(B);
     const int RP = (L.nP % RPB == 0) ? RPB : 1;  // element row groups are always full
     const Items it = items_b<B>(L, RP);
     const int64_t g = std::max<int64_t>(1, std::min<int64_t>((it.total() + RT / 32 - 1) / (RT / 32), GMAX));
     const LV<T> lv = view<T>(L);
-    if (RP == 1) k_jacobi_b<B, RF, 1, T><<<(int)g, RT, 0, ctx->stream>>>(lv, it, w, den, v, z);
-    else k_jacobi_b<B, RF, RPB, T><<<(int)g, RT, 0, ctx->stream>>>(lv, it, w, den, v, z);
+    if (RP == 1) k_jacobi_b<B, RF, 1, T><<<(int)g, RT, 0, ctx->stream>>>(lv, it, w, den, v, z, Vp, ld, npend, pc);
+    else k_jacobi_b<B, RF, RPB, T><<<(int)g, RT, 0, ctx->stream>>>(lv, it, w, den, v, z, Vp, ld, npend, pc);
 }
 
-// v = w / den, z = M^{-1} v: the compile-time block size kernel where B is one
-// of the instantiated sizes, else the generic one
+// v = w / den, z = M^{-1} v, with w = w' - sum_{q < npend} pc_q Vp_q when a
+// second Gram-Schmidt pass is pending: the compile-time block size kernel where
+// B is one of the instantiated sizes, else the generic one
 template <typename T>
-static void launch_jacobi(hho_ctx* ctx, const LevelMat& L, const T* w, const double* den, T* v, T* z) {
+static void launch_jacobi(hho_ctx* ctx, const LevelMat& L, const T* w, const double* den, T* v, T* z, const T* Vp,
+                          int64_t ld, int npend, const double* pc) {
     switch (L.b) {
-        case 2: launch_jacobi_b_B<2, T>(ctx, L, w, den, v, z); break;
-        case 3: launch_jacobi_b_B<3, T>(ctx, L, w, den, v, z); break;
-        case 4: launch_jacobi_b_B<4, T>(ctx, L, w, den, v, z); break;
-        case 6: launch_jacobi_b_B<6, T>(ctx, L, w, den, v, z); break;
-        case 8: launch_jacobi_b_B<8, T>(ctx, L, w, den, v, z); break;
-        case 9: launch_jacobi_b_B<9, T>(ctx, L, w, den, v, z); break;
-        case 10: launch_jacobi_b_B<10, T>(ctx, L, w, den, v, z); break;
-        case 12: launch_jacobi_b_B<12, T>(ctx, L, w, den, v, z); break;
-        case 18: launch_jacobi_b_B<18, T>(ctx, L, w, den, v, z); break;
-        case 30: launch_jacobi_b_B<30, T>(ctx, L, w, den, v, z); break;
+        case 2: launch_jacobi_b_B<2, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 3: launch_jacobi_b_B<3, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 4: launch_jacobi_b_B<4, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 6: launch_jacobi_b_B<6, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 8: launch_jacobi_b_B<8, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 9: launch_jacobi_b_B<9, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 10: launch_jacobi_b_B<10, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 12: launch_jacobi_b_B<12, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 18: launch_jacobi_b_B<18, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 30: launch_jacobi_b_B<30, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
         default:
-            k_apply_jacobi<T><<<grid1d(L.n, 256), 256, 0, ctx->stream>>>(view<T>(L), w, den, v, z);
+            k_apply_jacobi<T><<<grid1d(L.n, 256), 256, 0, ctx->stream>>>(view<T>(L), w, den, v, z, Vp, ld, npend,
+                                                                         pc);
     }
     ++ctx->launches;
 }
@@ -1061,10 +1106,12 @@ static hho_status smooth(hho_ctx* ctx, int l, const T* bv, T* x, bool x_zero, bo
     for (int j = 0; j < m; ++j) {
         T* vj = V + (int64_t)j * n;
         T* zj = Z + (int64_t)j * n;
-        launch_jacobi<T>(ctx, L, j == 0 ? w0 : w, sc + 5, vj, zj);
+        // the second pass of step j-1 (w'' = w' - V t2) is applied inside the Jacobi kernel
+        launch_jacobi<T>(ctx, L, j == 0 ? w0 : w, sc + 5, vj, zj, V, n, j, sc + G.t2);
         launch_spmv_dot<T>(ctx, l, zj, nullptr, w, 0, V, n, j + 1, 0, sc + G.t1, HOOK_NONE, sc, G, j);
-        launch_update_dot<T>(ctx, n, w, V, n, j + 1, sc + G.t1, -1.0, V, j + 1, 0, sc + G.t2, HOOK_NONE, sc, G, j);
-        launch_update_dot<T>(ctx, n, w, V, n, j + 1, sc + G.t2, -1.0, nullptr, 0, 1, sc + G.nrm, HOOK_COLUMN, sc, G, j);
+        // w' = w - V t1, t2 = V^T w', ||w'||^2; Hessenberg column with ||w''||^2 = ||w'||^2 - ||t2||^2
+        launch_update_dot<T>(ctx, n, w, V, n, j + 1, sc + G.t1, -1.0, V, j + 1, 1, sc + G.t2, HOOK_COLUMN_PY, sc, G,
+                             j);
     }
     k_update_x<T><<<vgrid(n), RT, xupd_smem(G.m), ctx->stream>>>(n, x, x_zero ? 0.0 : 1.0, Z, n, sc, G);
     ++ctx->launches;
