@@ -458,6 +458,14 @@ __global__ void __launch_bounds__(RT) k_spmv_dot(LV<T> L, Items it, const T* __r
     if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
 }
 
+// Row selection of the restriction d = I(bv - S x) (mode 2 of k_spmv_b): of a
+// fine face block (components of nFf unknowns each) the first nFc of every
+// component are kept, of a fine element pressure block the first nPc; d is
+// written in the coarse layout (face blocks of bc, then element blocks of nPc).
+struct Restr {
+    int nFf, nFc, bc, nPc;
+};
+
 // Same operator with the face block size B known at compile time: a thread
 // holds RF consecutive rows of one face (RF = B up to B = 12), the column loops
 // are fully unrolled and the B gathered x values of a neighbour face are loaded
@@ -466,7 +474,8 @@ template <int B, int RF, int RP, typename T>
 __global__ void __launch_bounds__(RT) k_spmv_b(LV<T> L, Items it, const T* __restrict__ x, const T* __restrict__ bv,
                                                 T* __restrict__ y, int mode, const T* __restrict__ V, int64_t ld, int nv,
                                                 int self, double* __restrict__ partial, unsigned* __restrict__ counter,
-                                                double* __restrict__ out, int hook, double* sc, GS gsl, int j) {
+                                                double* __restrict__ out, int hook, double* sc, GS gsl, int j,
+                                                Restr rs) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -513,8 +522,16 @@ __global__ void __launch_bounds__(RT) k_spmv_b(LV<T> L, Items it, const T* __res
             for (int i = 0; i < RF; ++i) {
                 const int64_t o = F * B + r0 + i;
                 const T v = mode ? T(bv[o] - acc[i]) : acc[i];
-                y[o] = v;
-                accumulate_dots(dacc, V, ld, o, nv, self, v);
+                if (mode == 2) {
+                    const int r = r0 + i, comp = r / rs.nFf, rr = r - comp * rs.nFf;
+                    if (rr < rs.nFc) {
+                        y[F * rs.bc + comp * rs.nFc + rr] = v;
+                        if (self) dacc[NVMAX] += (A)v * (A)v;
+                    }
+                } else {
+                    y[o] = v;
+                    accumulate_dots(dacc, V, ld, o, nv, self, v);
+                }
             }
         } else {
             const int64_t ww = w - nfi;
@@ -548,8 +565,15 @@ __global__ void __launch_bounds__(RT) k_spmv_b(LV<T> L, Items it, const T* __res
             for (int i = 0; i < RP; ++i) {
                 const int64_t o = nf * B + E * nP + r0 + i;
                 const T v = mode ? T(bv[o] - acc[i]) : acc[i];
-                y[o] = v;
-                accumulate_dots(dacc, V, ld, o, nv, self, v);
+                if (mode == 2) {
+                    if (r0 + i < rs.nPc) {
+                        y[nf * rs.bc + E * rs.nPc + r0 + i] = v;
+                        if (self) dacc[NVMAX] += (A)v * (A)v;
+                    }
+                } else {
+                    y[o] = v;
+                    accumulate_dots(dacc, V, ld, o, nv, self, v);
+                }
             }
         }
     }
@@ -920,7 +944,7 @@ static Items items_b(const LevelMat& L, int RP) {
 template <int B, typename T>
 static bool launch_spmv_b_B(hho_ctx* ctx, const LevelMat& L, const T* x, const T* bv, T* y, int mode, const T* V,
                             int64_t ld, int nv, int self, double* partial, unsigned* counter, double* out, int hook,
-                            double* sc, GS gsl, int j) {
+                            double* sc, GS gsl, int j, Restr rs) {
     constexpr int RF = face_rows_for(B);
     constexpr int RPB = elem_rows_for(B);
     const int RP = (L.nP % RPB == 0) ? RPB : 1;  // element row groups are always full
@@ -929,10 +953,10 @@ static bool launch_spmv_b_B(hho_ctx* ctx, const LevelMat& L, const T* x, const T
     const LV<T> lv = view<T>(L);
     if (RP == 1)
         k_spmv_b<B, RF, 1, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter, out,
-                                                         hook, sc, gsl, j);
+                                                         hook, sc, gsl, j, rs);
     else
         k_spmv_b<B, RF, RPB, T><<<g, RT, 0, ctx->stream>>>(lv, it, x, bv, y, mode, V, ld, nv, self, partial, counter,
-                                                           out, hook, sc, gsl, j);
+                                                           out, hook, sc, gsl, j, rs);
     return true;
 }
 
@@ -976,11 +1000,12 @@ static void launch_jacobi(hho_ctx* ctx, const LevelMat& L, const T* w, const dou
 template <typename T>
 static bool launch_spmv_b(hho_ctx* ctx, const LevelMat& L, const T* x, const T* bv, T* y, int mode, const T* V,
                           int64_t ld, int nv, int self, double* partial, unsigned* counter, double* out, int hook,
-                          double* sc, GS gsl, int j) {
+                          double* sc, GS gsl, int j, Restr rs = Restr{0, 0, 0, 0}) {
     if (ctx->spmv_rows > 0) return false;  // explicit row grouping requested: generic kernel
 #define HHO_B_CASE(BB)                                                                                             \
     case BB:                                                                                                       \
-        return launch_spmv_b_B<BB, T>(ctx, L, x, bv, y, mode, V, ld, nv, self, partial, counter, out, hook, sc, gsl, j);
+        return launch_spmv_b_B<BB, T>(ctx, L, x, bv, y, mode, V, ld, nv, self, partial, counter, out, hook, sc, gsl, j, \
+                                      rs);
     switch (L.b) {
         HHO_B_CASE(2)
         HHO_B_CASE(3)
@@ -1169,7 +1194,11 @@ static hho_status vcycle_level(hho_ctx* ctx, int l, const T* bv, T* x, bool x_ze
     Items it = items_for(F, Rc, C.b, C.nP);
     GS Gc = gs_layout(std::max(ctx->smooth_its, 1));
     const int do_norm = (!coarse_next && ctx->smooth_its > 0) ? 1 : 0;
-    switch (Rc) {
+    const Restr rs{F.nF, C.nF, C.b, C.nP};
+    if (launch_spmv_b<T>(ctx, F, x, bv, cbv, 2, nullptr, 0, 0, do_norm, ctx->ws->partial, ctx->ws->counter, cw.sc,
+                         do_norm ? HOOK_START : HOOK_NONE, cw.sc, Gc, 0, rs)) {
+        // fused into the operator kernel specialised on the fine block size
+    } else switch (Rc) {
         case 1: restrict_R<1, T>(ctx, F, C, it, x, bv, cbv, do_norm, cw.sc, Gc); break;
         case 2: restrict_R<2, T>(ctx, F, C, it, x, bv, cbv, do_norm, cw.sc, Gc); break;
         case 3: restrict_R<3, T>(ctx, F, C, it, x, bv, cbv, do_norm, cw.sc, Gc); break;
