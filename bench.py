@@ -8,12 +8,14 @@ assembled operator and RHS resident in HBM): 128 x 128 squares split into
 Dirichlet on x=0, y=0, y=1 and Neumann on x=1, manufactured field
 u = (sin(pi x) cos(pi y), -cos(pi x) sin(pi y)), p = sin(2 pi x) sin(2 pi y),
 k = 3, v-cond static condensation, p-levels 3-2-1-0.  The headline solve uses
-the mixed-precision V-cycle (FP32 level operators and smoother vectors with
-FP64 dot products and an FP64 coarse solve) inside FP64 FGMRES; the plain
-FP64 V-cycle is timed on the same problem for the speedup.
+the mixed-precision V-cycle (FP32 level operators, smoother vectors, dot
+products and coarse solve; FP64 only for stored scalars) inside FP64 FGMRES;
+the plain FP64 V-cycle is timed on the same problem for the speedup.
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
-bounded sample of the same workload family instead.
+bounded sample of the same workload family instead.  ``--probe-spmv`` only
+runs three FP32 and one FP64 level-0 operator launches on the workload (the
+small command for ncu captures of the roofline kernel) and prints nothing.
 """
 from __future__ import annotations
 
@@ -32,6 +34,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FGMRES+p-MG time & DOFs/s to 1e-8 rel. residual; V-cycle GB/s vs HBM peak"
 UNIT = "DOF/s"
+# DRAM bytes (read + write) of one FP32 level-0 operator launch on the default
+# workload, from the ncu capture summarised in
+# profiles/k_spmv_b_level0_tri128_k3_vcond.md (kernel unchanged since)
+SPMV_F32_TRAFFIC = {("tri", 128, 3, "v"): 144323072 + 3200512}
 
 
 def parse():
@@ -48,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of the headline")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--probe-spmv", action="store_true", help="three FP32 and one FP64 level-0 operator launches")
     ap.add_argument("--coarse-fp32", type=int, default=1, choices=[0, 1],
                     help="FP32 coarse solve inside the FP32 V-cycle (velocity-only condensation default)")
     return ap.parse_args()
@@ -197,6 +204,17 @@ def run_ours(args):
         ctx.assemble(f, gD, gN)
         degrees = list(range(args.k, -1, -1))
         ndof = ctx.ndof(0)
+        if args.probe_spmv:
+            ctx.pmg_setup(degrees, smooth_its=2, prec="fp32")
+            xp = torch.randn(ndof, dtype=torch.float64, device="cuda")
+            yp = torch.empty_like(xp)
+            xf, yf = xp.float(), torch.empty(ndof, dtype=torch.float32, device="cuda")
+            for _ in range(3):
+                ctx.spmv_f32(0, xf, yf)
+            ctx.spmv(0, xp, yp)
+            torch.cuda.synchronize()
+            ctx.close()
+            return
         x = torch.empty(ndof, dtype=torch.float64, device="cuda")
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -315,7 +333,9 @@ def run_ours(args):
                        "speedup_vs_fp64_vcycle": (fp64["ms_per_solve"] / ms) if fp64 else None,
                        "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": (SPMV_F32_TRAFFIC.get(("tri", args.n, args.k, args.cond))
+                                     if args.prec == "fp32" else None),
                          "bytes_per_launch": nbytes, "ms_per_launch": ms_k,
                          "fp64_outer_spmv": {"achieved": nb64 / (ms64_k / 1e3) / 1e9, "bytes_per_launch": nb64,
                                              "ms_per_launch": ms64_k}},
