@@ -201,6 +201,39 @@ hho_status hho_spmv_f32(hho_ctx* ctx, int level, const float* d_x, float* d_y);
  * be NULL.  Returns HHO_ERR_NOT_CONVERGED if maxit is reached. */
 hho_status hho_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double* d_x, hho_solve_info* info);
 
+/* Batches of independent problems (no counterpart in the paper).  Declares the
+ * context's mesh a disjoint union of n_prob (1..65535) problems: problem p owns faces
+ * [face_off[p], face_off[p+1]) and elements [elem_off[p], elem_off[p+1])
+ * (host arrays of n_prob + 1, copied; face_off[0] = elem_off[0] = 0, last
+ * entries the face and element counts; no face may touch an element of
+ * another problem: HHO_ERR_MESH).  Call between hho_setup and pmg_setup
+ * (HHO_ERR_STATE afterwards, and pmg_setup must then be called again).
+ * Every level operator is block diagonal, so one launch of each V-cycle kernel
+ * serves all problems; a problem without Neumann face gets its own constant-
+ * pressure kernel treatment (projection, coarse pin). */
+hho_status hho_set_batch(hho_ctx* ctx, int n_prob, const int64_t* face_off, const int64_t* elem_off);
+
+/* One FGMRES per problem of a declared batch (Sec. 3.3: one V-cycle per
+ * iteration, CGS2, x0 = 0), all advanced in lockstep with per-problem
+ * (segmented) dot products, each stopping at ||rhs_p - S_p x_p|| <=
+ * rtol ||rhs_p||; a converged problem is frozen while the others go on.  The
+ * V-cycle is the union's (its smoother's Krylov coefficients are shared by the
+ * batch, which flexible GMRES admits).  d_x: device, ndof(0).  h_iters
+ * (host, n_prob, may be NULL): iteration at which each problem converged;
+ * h_relres (host, n_prob, may be NULL): each problem's final true relative
+ * residual.  info: batch totals (iterations of the lockstep loop, the largest
+ * relative residual, wall time).  HHO_ERR_NOT_CONVERGED if some problem is
+ * above rtol after maxit iterations. */
+hho_status hho_solve_batch(hho_ctx* ctx, double rtol, int maxit, int restart, double* d_x, int32_t* h_iters,
+                           double* h_relres, hho_solve_info* info);
+
+/* Autotuner (after pmg_setup): times `reps` V-cycles for every candidate of
+ * "spmv_rows" (0, 2, 4) x "spmv_grid" (automatic, 1216, 2432) and, for a
+ * declared batch, `reps` segmented update kernels for tile sizes 1024 ..
+ * 8192 unknowns, and keeps the fastest.  h_choice (host, 3 doubles, may be
+ * NULL) receives {spmv_rows, spmv_grid, tile_rows}.  reps in 1..1000. */
+hho_status hho_autotune(hho_ctx* ctx, int reps, double* h_choice);
+
 /* Back-substitution of the eliminated unknowns (Eq. ST.1 / ST.2): for every
  * element the full local vector [U_T | U_F1 .. U_FN | P_T] (velocity
  * component-major, orthonormal element/face bases) from the condensed

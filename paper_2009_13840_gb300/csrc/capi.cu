@@ -96,7 +96,39 @@ hho_status hho_setup(const hho_mesh* mesh, int k, int cond, void* stream, hho_ct
     HHO_TRY(build_topology(ctx));
     HHO_TRY(assemble_level0(ctx));
     HHO_TRY(dalloc(ctx, &ctx->rhs, (size_t)ctx->levels[0].n));
+    // one problem until a batch is declared
+    Problems& pr = ctx->probs;
+    pr.P = 1;
+    pr.face_off = {0, ctx->disc.nf};
+    pr.elem_off = {0, ctx->disc.ne};
+    pr.elem_prob.assign(ctx->disc.ne, 0);
+    pr.declared = false;
     return HHO_OK;
+}
+
+hho_status hho_set_batch(hho_ctx* ctx, int n_prob, const int64_t* face_off, const int64_t* elem_off) {
+    if (!ctx || !face_off || !elem_off) return HHO_ERR_ARG;
+    HHO_TRY(batch_set(ctx, n_prob, face_off, elem_off));
+    return HHO_OK;
+}
+
+hho_status hho_solve_batch(hho_ctx* ctx, double rtol, int maxit, int restart, double* d_x, int32_t* h_iters,
+                           double* h_relres, hho_solve_info* info) {
+    if (!ctx || !d_x) return HHO_ERR_ARG;
+    if (!ctx->have_pmg || !ctx->have_rhs) {
+        ctx->err = "hho_solve_batch: call hho_assemble and pmg_setup first";
+        return HHO_ERR_STATE;
+    }
+    return batch_solve(ctx, rtol, maxit, restart, d_x, h_iters, h_relres, info);
+}
+
+hho_status hho_autotune(hho_ctx* ctx, int reps, double* h_choice) {
+    if (!ctx || reps < 1 || reps > 1000) return HHO_ERR_ARG;
+    if (!ctx->have_pmg) {
+        ctx->err = "hho_autotune: call pmg_setup first";
+        return HHO_ERR_STATE;
+    }
+    return autotune(ctx, reps, h_choice);
 }
 
 hho_status hho_ndof(const hho_ctx* ctx, int level, int64_t* ndof) {
@@ -306,8 +338,11 @@ hho_status hho_destroy(hho_ctx* ctx) {
     Topo& T = ctx->topo;
     void* pt[] = {T.ff_col, T.ff_nsl, T.fp_col, T.pf_col, T.pf_nsl, T.asm_T, T.asm_lf, T.asm_lg};
     for (void* p : pt) dfree(p);
+    batch_free(ctx);
     dfree(ctx->rhs);
     dfree(ctx->null_vec0);
+    dfree(ctx->null_w);
+    dfree(ctx->d_elem_off);
     dfree(ctx->d_flag);
     delete ctx;
     return HHO_OK;

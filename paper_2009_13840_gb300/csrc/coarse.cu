@@ -82,12 +82,22 @@ __global__ void k_mean_abs_diag_dense(const double* __restrict__ A, int64_t n, d
     }
 }
 
-__global__ void k_rank1(double* __restrict__ A, int64_t n, const double* __restrict__ nv, const double* __restrict__ alpha) {
+// A += alpha sum_p n_p n_p^T: nv holds every problem's unit kernel vector
+// (disjoint supports), rprob the problem of each row
+__global__ void k_rank1(double* __restrict__ A, int64_t n, const double* __restrict__ nv,
+                        const int32_t* __restrict__ rprob, const double* __restrict__ alpha) {
     double a = *alpha;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t r = i / n, c = i % n;
-        if (nv[r] != 0.0 && nv[c] != 0.0) A[i] += a * nv[r] * nv[c];
+        if (nv[r] != 0.0 && nv[c] != 0.0 && rprob[r] == rprob[c]) A[i] += a * nv[r] * nv[c];
     }
+}
+
+// G[g][g] += alpha for the pinned kept pressures (one per problem with a kernel;
+// pins are positions in the block storage of the interface matrix)
+__global__ void k_pin(double* __restrict__ G, const int64_t* __restrict__ pins, int npins,
+                      const double* __restrict__ alpha) {
+    for (int i = threadIdx.x; i < npins; i += blockDim.x) G[pins[i]] += *alpha;
 }
 
 __global__ void k_eye(double* __restrict__ A, int64_t n) {
@@ -193,6 +203,8 @@ struct DDView {
     const int64_t* off_S;
     const double* S;
     int b0, nF0, nP0, bL, nFL, nPL;
+    const int64_t *sub_g0, *sub_goff;  // per subdomain: first interface index and block of its problem
+    const int32_t* sub_gn;             // per subdomain: interface size of its problem
 };
 
 // Assemble, factor and Schur-reduce one subdomain per CTA.
@@ -258,7 +270,8 @@ __global__ void __launch_bounds__(256) k_dd_factor(DDView V, double* __restrict_
             int i = (int)(idx / nGs), j = (int)(idx % nGs);
             double acc = 0.0;
             for (int l = 0; l < nI; ++l) acc += AG[(int64_t)i * nI + l] * W[(int64_t)l * ldw + nI + j];
-            atomicAdd(&G[(int64_t)gam[i] * V.nG + gam[j]], AGG[idx] - acc);
+            const int64_t g0 = V.sub_g0[s];
+            atomicAdd(&G[V.sub_goff[s] + (gam[i] - g0) * V.sub_gn[s] + (gam[j] - g0)], AGG[idx] - acc);
         }
         __syncthreads();
     }
@@ -355,28 +368,6 @@ __global__ void k_dd_scatter_G(int64_t nG, const int32_t* __restrict__ gam_glob,
         c[gam_glob[g]] = cG[g];
 }
 
-template <typename T>
-__global__ void k_null_dot(int64_t n, const double* __restrict__ nv, const T* __restrict__ x, double* __restrict__ out) {
-    // single block, fixed order tree
-    __shared__ double sm[256];
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += nv[i] * (double)x[i];
-    sm[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = sm[0];
-}
-
-template <typename T>
-__global__ void k_null_sub(int64_t n, const double* __restrict__ nv, const double* __restrict__ dot, T* __restrict__ x) {
-    const double a = *dot;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = T((double)x[i] - a * nv[i]);
-}
-
 __global__ void k_to_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = (float)src[i];
@@ -388,7 +379,7 @@ struct CoarseSolver {
     int kind = 0;  // 0 dense inverse, 1 substructuring
     int64_t n = 0;
     double* Ainv = nullptr;   // dense path (n x n) or interface inverse (nG x nG)
-    double* nullv = nullptr;  // unit kernel vector at the coarse level (or null)
+    bool project = false;     // remove the pressure kernels of the problems that have one
     double* scal = nullptr;   // device scalars
     // substructuring
     int P = 0;
@@ -399,6 +390,10 @@ struct CoarseSolver {
     int64_t *offI = nullptr, *offA = nullptr, *offX = nullptr, *offAG = nullptr, *offGam = nullptr,
             *elem_loc_off = nullptr;
     double *AinvT = nullptr, *XT = nullptr, *AGI = nullptr, *dI = nullptr, *yI = nullptr, *rG = nullptr, *cG = nullptr;
+    // interface inverse stored as one dense block per problem of a batch
+    int nprob = 1, g_nmax = 0;
+    int64_t *g_prob0 = nullptr, *g_off = nullptr;  // first interface row / block offset per problem
+    int32_t *g_n = nullptr, *g_row = nullptr;      // block size per problem, problem per interface row
     // FP32 copies of the solve operators and work vectors (mixed-precision V-cycle)
     int64_t nAinv = 0, nAinvT = 0, nXT = 0, nAGI = 0;
     float *Ainv32 = nullptr, *AinvT32 = nullptr, *XT32 = nullptr, *AGI32 = nullptr, *dI32 = nullptr, *yI32 = nullptr,
@@ -408,13 +403,160 @@ struct CoarseSolver {
 void coarse_free(hho_ctx* ctx) {
     CoarseSolver* C = ctx->coarse;
     if (!C) return;
-    void* ps[] = {C->Ainv, C->nullv, C->scal, C->sub_elem_ptr, C->sub_elem, C->nI, C->nGs, C->flat_sub, C->flat_glob,
+    void* ps[] = {C->Ainv, C->scal, C->sub_elem_ptr, C->sub_elem, C->nI, C->nGs, C->flat_sub, C->flat_glob,
                   C->gam_list, C->gam_glob, C->g_ptr, C->g_s, C->g_j, C->elem_loc, C->offI, C->offA, C->offX,
                   C->offAG, C->offGam, C->elem_loc_off, C->AinvT, C->XT, C->AGI, C->dI, C->yI, C->rG, C->cG,
-                  C->Ainv32, C->AinvT32, C->XT32, C->AGI32, C->dI32, C->yI32, C->rG32, C->cG32};
+                  C->Ainv32, C->AinvT32, C->XT32, C->AGI32, C->dI32, C->yI32, C->rG32, C->cG32,
+                  C->g_prob0, C->g_off, C->g_n, C->g_row};
     for (void* p : ps) dfree(p);
     delete C;
     ctx->coarse = nullptr;
+}
+
+// Batched Gauss-Jordan with partial pivoting on dense blocks of different
+// sizes: block q is n_q x n_q at off[q]; column step j acts on the blocks with
+// n_q > j (one CTA each for the pivot, a 2D grid for the elimination).
+__global__ void k_eye_b(double* __restrict__ A, const int64_t* __restrict__ off, const int32_t* __restrict__ nn) {
+    const int q = blockIdx.y;
+    const int64_t n = nn[q];
+    double* Aq = A + off[q];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * n; i += (int64_t)gridDim.x * blockDim.x)
+        Aq[i] = (i / n == i % n) ? 1.0 : 0.0;
+}
+
+__global__ void k_gj_pivot_b(double* __restrict__ A, double* __restrict__ Ai, const int64_t* __restrict__ off,
+                             const int32_t* __restrict__ nn, int64_t j, double* __restrict__ f,
+                             const int64_t* __restrict__ foff, int* __restrict__ status) {
+    const int q = blockIdx.x;
+    const int64_t n = nn[q];
+    if (j >= n) return;
+    double* Aq = A + off[q];
+    double* Aiq = Ai + off[q];
+    double* fq = f + foff[q];
+    __shared__ double bv[256];
+    __shared__ int64_t bi[256];
+    double best = -1.0;
+    int64_t arg = n;
+    for (int64_t i = j + threadIdx.x; i < n; i += blockDim.x) {
+        double v = fabs(Aq[i * n + j]);
+        if (v > best) {
+            best = v;
+            arg = i;
+        }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = arg;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 1; t < (int)blockDim.x; ++t)
+            if (bv[t] > bv[0] || (bv[t] == bv[0] && bi[t] < bi[0])) {
+                bv[0] = bv[t];
+                bi[0] = bi[t];
+            }
+        if (!(bv[0] > 0.0)) atomicExch(status, (int)HHO_ERR_SINGULAR);
+    }
+    __syncthreads();
+    if (!(bv[0] > 0.0)) return;
+    const int64_t p = bi[0];
+    if (p != j)
+        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+            double t = Aq[j * n + c];
+            Aq[j * n + c] = Aq[p * n + c];
+            Aq[p * n + c] = t;
+            t = Aiq[j * n + c];
+            Aiq[j * n + c] = Aiq[p * n + c];
+            Aiq[p * n + c] = t;
+        }
+    __syncthreads();
+    const double inv = 1.0 / Aq[j * n + j];
+    __syncthreads();
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+        Aq[j * n + c] *= inv;
+        Aiq[j * n + c] *= inv;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) fq[i] = (i == j) ? 0.0 : Aq[i * n + j];
+}
+
+__global__ void k_gj_elim_b(double* __restrict__ A, double* __restrict__ Ai, const int64_t* __restrict__ off,
+                            const int32_t* __restrict__ nn, int64_t j, const double* __restrict__ f,
+                            const int64_t* __restrict__ foff) {
+    const int q = blockIdx.y;
+    const int64_t n = nn[q];
+    if (j >= n) return;
+    double* Aq = A + off[q];
+    double* Aiq = Ai + off[q];
+    const double* fq = f + foff[q];
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * n * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx % (n * n);
+        const int64_t i = k / n, c = k % n;
+        const double fi = fq[i];
+        if (fi == 0.0) continue;
+        if (idx < n * n) Aq[k] -= fi * Aq[j * n + c];
+        else Aiq[k] -= fi * Aiq[j * n + c];
+    }
+}
+
+// y = blockdiag(A_q) x: one warp per row; row r belongs to problem row_q[r],
+// whose block (n_q x n_q at off[q]) acts on x[prob0[q] ..]
+template <typename T>
+__global__ void k_gemv_blocks(const T* __restrict__ A, const int32_t* __restrict__ row_q,
+                              const int64_t* __restrict__ prob0, const int64_t* __restrict__ off,
+                              const int32_t* __restrict__ nn, int64_t nrows, const T* __restrict__ x,
+                              T* __restrict__ y) {
+    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = w; r < nrows; r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int q = row_q[r];
+        const int64_t n = nn[q], r0 = prob0[q];
+        const T* a = A + off[q] + (r - r0) * n;
+        const T* xq = x + r0;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        int64_t c = lane;
+        for (; c + 96 < n; c += 128) {
+            s0 += __ldg(a + c) * xq[c];
+            s1 += __ldg(a + c + 32) * xq[c + 32];
+            s2 += __ldg(a + c + 64) * xq[c + 64];
+            s3 += __ldg(a + c + 96) * xq[c + 96];
+        }
+        for (; c < n; c += 32) s0 += __ldg(a + c) * xq[c];
+        T s = (s0 + s1) + (s2 + s3);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) y[r] = s;
+    }
+}
+
+static hho_status dense_inverse_blocks(hho_ctx* ctx, double* A, double* Ainv, int nq, const int64_t* d_off,
+                                       const int32_t* d_n, const std::vector<int32_t>& h_n,
+                                       const int64_t* d_foff) {
+    int64_t nmax = 0;
+    for (int32_t v : h_n) nmax = std::max<int64_t>(nmax, v);
+    double* f = nullptr;
+    int64_t ftot = 0;
+    for (int32_t v : h_n) ftot += v;
+    HHO_TRY(dalloc(ctx, &f, (size_t)std::max<int64_t>(ftot, 1)));
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((2 * nmax * nmax + 255) / 256, 4096));
+    const int gy = nq;
+    k_eye_b<<<dim3(gx, gy), 256, 0, ctx->stream>>>(Ainv, d_off, d_n);
+    HHO_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    for (int64_t j = 0; j < nmax; ++j) {
+        k_gj_pivot_b<<<nq, 256, 0, ctx->stream>>>(A, Ainv, d_off, d_n, j, f, d_foff, ctx->d_flag);
+        k_gj_elim_b<<<dim3(gx, gy), 256, 0, ctx->stream>>>(A, Ainv, d_off, d_n, j, f, d_foff);
+    }
+    cudaError_t le = cudaGetLastError();
+    int flag = 0;
+    cudaError_t ce = cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    dfree(f);
+    HHO_CUDA(le);
+    HHO_CUDA(ce);
+    HHO_CUDA(se);
+    if (flag) {
+        ctx->err = "pmg_setup: singular coarse interface operator";
+        return HHO_ERR_SINGULAR;
+    }
+    return HHO_OK;
 }
 
 static hho_status dense_inverse(hho_ctx* ctx, double* A, double* Ainv, int64_t n) {
@@ -494,11 +636,20 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
         for (int j = 0; j < d; ++j) cen[(size_t)T * d + j] /= (double)vs.size();
     }
     const int64_t target = ctx->dd_elements > 0 ? ctx->dd_elements : ((d == 2) ? 128 : 64);
-    int P = 1;
-    while ((int64_t)P * 2 * target <= ne) P *= 2;
-    std::vector<int32_t> ids(ne), part(ne);
+    // every problem of a batch is partitioned on its own (subdomains never
+    // straddle two problems), so the interface matrix is block diagonal by problem
+    const Problems& pr = ctx->probs;
+    std::vector<int32_t> ids(ne), part(ne), sub_prob;
     std::iota(ids.begin(), ids.end(), 0);
-    rcb(ids, 0, ids.size(), P, 0, cen, d, part);
+    int P = 0;
+    for (int q = 0; q < pr.P; ++q) {
+        const int64_t neq = pr.elem_off[q + 1] - pr.elem_off[q];
+        int Pq = 1;
+        while ((int64_t)Pq * 2 * target <= neq) Pq *= 2;
+        rcb(ids, pr.elem_off[q], pr.elem_off[q + 1], Pq, P, cen, d, part);
+        for (int s = 0; s < Pq; ++s) sub_prob.push_back(q);
+        P += Pq;
+    }
     // subdomain element lists (increasing ids)
     std::vector<std::vector<int32_t>> elems(P);
     for (int64_t T = 0; T < ne; ++T) elems[part[T]].push_back((int32_t)T);
@@ -536,17 +687,28 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
                 kept[s].push_back(T);
                 is_kept[T] = 1;
             }
+    // interface unknowns numbered problem by problem: the problem's interface
+    // faces, then its subdomains' kept pressures
     std::vector<int32_t> gface(nf, -1);
+    std::vector<int64_t> gp0(P + 1), gprob0(pr.P + 1, 0);
     int64_t nG = 0;
-    for (int64_t F = 0; F < nf; ++F)
-        if (face_owner[F] < 0) {
-            gface[F] = (int32_t)nG;
-            nG += bL;
+    {
+        int s = 0;
+        for (int q = 0; q < pr.P; ++q) {
+            gprob0[q] = nG;
+            for (int64_t F = pr.face_off[q]; F < pr.face_off[q + 1]; ++F)
+                if (face_owner[F] < 0) {
+                    gface[F] = (int32_t)nG;
+                    nG += bL;
+                }
+            for (; s < P && sub_prob[s] == q; ++s) {
+                gp0[s] = nG;
+                nG += (int64_t)kept[s].size();
+            }
         }
-    std::vector<int64_t> gp0(P + 1);
-    gp0[0] = nG;
-    for (int s = 0; s < P; ++s) gp0[s + 1] = gp0[s] + (int64_t)kept[s].size();
-    nG = gp0[P];
+        gprob0[pr.P] = nG;
+        gp0[P] = nG;
+    }
     std::vector<int32_t> gam_glob(nG);
     for (int64_t F = 0; F < nf; ++F)
         if (gface[F] >= 0)
@@ -561,8 +723,7 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
         elem_loc_off(ne, 0);
     std::vector<std::vector<std::pair<int32_t, int32_t>>> gcontrib(nG);
     std::vector<int32_t> loc_of((size_t)L.n, -1);
-    int pin_j = -1;  // local interface index, in subdomain 0, of the pinned kept pressure
-    auto nGss_faces = [](size_t total, size_t nk) { return (int)(total - nk); };
+    int pin_j = -1;  // unused: pins are added to the assembled interface matrix (k_pin)
     int64_t tA = 0, tX = 0, tAG = 0, tW = 0;
     std::vector<int64_t> elem_loc_size(ne);
     for (int64_t T = 0; T < ne; ++T) elem_loc_size[T] = (D.h_ef_ptr[T + 1] - D.h_ef_ptr[T]) * bL + nPL;
@@ -606,7 +767,6 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
             unk.push_back((int32_t)(nf * bL + (int64_t)kept[s][q] * nPL));
             gl.push_back((int32_t)(gp0[s] + q));
         }
-        if (s == 0) pin_j = nGss_faces(gl.size(), kept[s].size());
         const int nGss = (int)gl.size();
         h_nI[s] = nIs;
         h_nGs[s] = nGss;
@@ -683,19 +843,56 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
     HHO_TRY(dalloc(ctx, &C->yI, std::max<int64_t>(C->nIt, 1)));
     HHO_TRY(dalloc(ctx, &C->rG, nG));
     HHO_TRY(dalloc(ctx, &C->cG, nG));
+    // interface matrix: one dense block per problem (n_q x n_q at goff[q])
+    std::vector<int64_t> goff(pr.P + 1, 0), h_sub_g0(P), h_sub_goff(P);
+    std::vector<int32_t> h_gn(pr.P), h_sub_gn(P), h_grow(nG);
+    for (int q = 0; q < pr.P; ++q) {
+        h_gn[q] = (int32_t)(gprob0[q + 1] - gprob0[q]);
+        goff[q + 1] = goff[q] + (int64_t)h_gn[q] * h_gn[q];
+        for (int64_t g = gprob0[q]; g < gprob0[q + 1]; ++g) h_grow[g] = q;
+    }
+    for (int s = 0; s < P; ++s) {
+        h_sub_g0[s] = gprob0[sub_prob[s]];
+        h_sub_goff[s] = goff[sub_prob[s]];
+        h_sub_gn[s] = h_gn[sub_prob[s]];
+    }
+    const int64_t nGG = goff[pr.P];
+    C->nprob = pr.P;
+    HHO_TRY(upload(ctx, &C->g_prob0, gprob0));
+    HHO_TRY(upload(ctx, &C->g_off, goff));
+    HHO_TRY(upload(ctx, &C->g_n, h_gn));
+    HHO_TRY(upload(ctx, &C->g_row, h_grow));
+    C->g_nmax = *std::max_element(h_gn.begin(), h_gn.end());
+    int64_t *d_sub_g0 = nullptr, *d_sub_goff = nullptr;
+    int32_t* d_sub_gn = nullptr;
+    HHO_TRY(upload(ctx, &d_sub_g0, h_sub_g0));
+    HHO_TRY(upload(ctx, &d_sub_goff, h_sub_goff));
+    HHO_TRY(upload(ctx, &d_sub_gn, h_sub_gn));
     double *scratch = nullptr, *G = nullptr;
     HHO_TRY(dalloc(ctx, &scratch, std::max<int64_t>(tW, 1)));
-    HHO_TRY(dalloc(ctx, &G, (size_t)nG * nG));
-    HHO_TRY(dalloc(ctx, &C->Ainv, (size_t)nG * nG));
-    C->nAinv = nG * nG;
+    HHO_TRY(dalloc(ctx, &G, (size_t)std::max<int64_t>(nGG, 1)));
+    HHO_TRY(dalloc(ctx, &C->Ainv, (size_t)std::max<int64_t>(nGG, 1)));
+    C->nAinv = nGG;
     C->nAinvT = tA;
     C->nXT = tX;
     C->nAGI = tAG;
-    HHO_CUDA(cudaMemsetAsync(G, 0, (size_t)nG * nG * sizeof(double), ctx->stream));
-    // pin of the pressure kernel (all-Dirichlet problems)
-    int pin_s = -1;
+    HHO_CUDA(cudaMemsetAsync(G, 0, (size_t)std::max<int64_t>(nGG, 1) * sizeof(double), ctx->stream));
+    // pins of the pressure kernels: for every problem with one, its first kept
+    // pressure (in interface order) gets alpha = mean |diag| on the diagonal of
+    // the interface matrix; the solve is projected afterwards
+    const int pin_s = -1;
+    std::vector<int64_t> pins;
     if (ctx->has_null) {
-        pin_s = 0;  // first kept pressure of subdomain 0
+        std::vector<char> done(pr.P, 0);
+        for (int s = 0; s < P; ++s)
+            for (size_t q = 0; q < kept[s].size(); ++q) {
+                const int pq = ctx->probs.elem_prob[kept[s][q]];
+                if (ctx->probs.has_null[pq] && !done[pq]) {
+                    done[pq] = 1;
+                    const int64_t g = gp0[s] + (int64_t)q - gprob0[pq];
+                    pins.push_back(goff[pq] + g * h_gn[pq] + g);
+                }
+            }
         k_mean_abs_diag_level<<<1, 32, 0, ctx->stream>>>(L.nf, L.ne, L.b, L.nP, L.ff, L.pp, C->scal);
     } else {
         HHO_CUDA(cudaMemsetAsync(C->scal, 0, sizeof(double), ctx->stream));
@@ -724,6 +921,9 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
     V.nP0 = D.nP;
     V.bL = bL;
     V.nFL = nFL;
+    V.sub_g0 = d_sub_g0;
+    V.sub_goff = d_sub_goff;
+    V.sub_gn = d_sub_gn;
     V.nPL = nPL;
     HHO_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
     k_dd_factor<<<P, 256, 0, ctx->stream>>>(V, scratch, C->AinvT, C->XT, C->AGI, G, C->scal, pin_s, pin_j,
@@ -742,8 +942,19 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
         ctx->err = "pmg_setup: singular subdomain block in the coarse solver";
         return HHO_ERR_SINGULAR;
     }
-    hho_status st = dense_inverse(ctx, G, C->Ainv, nG);
+    if (!pins.empty()) {
+        int64_t* d_pins = nullptr;
+        HHO_TRY(upload(ctx, &d_pins, pins));
+        k_pin<<<1, 256, 0, ctx->stream>>>(G, d_pins, (int)pins.size(), C->scal);
+        HHO_CUDA(cudaGetLastError());
+        HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+        dfree(d_pins);
+    }
+    hho_status st = dense_inverse_blocks(ctx, G, C->Ainv, pr.P, C->g_off, C->g_n, h_gn, C->g_prob0);
     dfree(G);
+    dfree(d_sub_g0);
+    dfree(d_sub_goff);
+    dfree(d_sub_gn);
     return st;
 }
 
@@ -785,15 +996,7 @@ static hho_status coarse_build(hho_ctx* ctx) {
     const LevelMat& L = ctx->levels.back();
     C->n = L.n;
     HHO_TRY(dalloc(ctx, &C->scal, 8));
-    if (ctx->has_null) {
-        std::vector<double> meas(L.ne), v(L.n, 0.0);
-        HHO_CUDA(cudaMemcpy(meas.data(), ctx->disc.emeas, L.ne * sizeof(double), cudaMemcpyDeviceToHost));
-        double s = 0.0;
-        for (int64_t T = 0; T < L.ne; ++T) s += meas[T];
-        double inv = 1.0 / std::sqrt(s);
-        for (int64_t T = 0; T < L.ne; ++T) v[L.nf * L.b + T * L.nP] = std::sqrt(meas[T]) * inv;
-        HHO_TRY(upload(ctx, &C->nullv, v));
-    }
+    C->project = ctx->has_null;
     if (L.n <= ctx->coarse_dense_max) {
         C->kind = 0;
         const int64_t n = L.n;
@@ -805,8 +1008,22 @@ static hho_status coarse_build(hho_ctx* ctx) {
         k_dense_from_level<<<grid1d(n, 128), 128, 0, ctx->stream>>>(L.nf, L.ne, L.b, L.nP, L.ff_col, L.ff_nsl, L.fp_col,
                                                                      L.pf_col, L.pf_nsl, L.ff, L.fp, L.pf, L.pp, A, n);
         if (ctx->has_null) {
+            std::vector<double> w(L.ne), v(n, 0.0);
+            std::vector<int32_t> rp(n, -1);
+            HHO_CUDA(cudaMemcpy(w.data(), ctx->null_w, L.ne * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int64_t T = 0; T < L.ne; ++T) {
+                v[L.nf * L.b + T * L.nP] = w[T];
+                rp[L.nf * L.b + T * L.nP] = ctx->probs.elem_prob[T];
+            }
+            double* nv = nullptr;
+            int32_t* rprob = nullptr;
+            HHO_TRY(upload(ctx, &nv, v));
+            HHO_TRY(upload(ctx, &rprob, rp));
             k_mean_abs_diag_dense<<<1, 32, 0, ctx->stream>>>(A, n, C->scal);
-            k_rank1<<<grid1d(n * n, 256), 256, 0, ctx->stream>>>(A, n, C->nullv, C->scal);
+            k_rank1<<<grid1d(n * n, 256), 256, 0, ctx->stream>>>(A, n, nv, rprob, C->scal);
+            HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+            dfree(nv);
+            dfree(rprob);
         }
         HHO_CUDA(cudaGetLastError());
         hho_status st = dense_inverse(ctx, A, C->Ainv, n);
@@ -829,16 +1046,18 @@ static hho_status coarse_apply_t(hho_ctx* ctx, CoarseSolver* C, const T* Ainv, c
                                                                  dI, yI);
         k_dd_rG<T><<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(C->nG, C->gam_glob, C->g_ptr, C->g_s, C->g_j,
                                                                      C->nI, C->offI, C->offAG, AGI, yI, d, rG);
-        k_gemv<T><<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(Ainv, C->nG, rG, cG);
+        k_gemv_blocks<T><<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(Ainv, C->g_row, C->g_prob0, C->g_off,
+                                                                          C->g_n, C->nG, rG, cG);
         k_dd_cI<T><<<grid1d(C->nIt, 128), 128, 0, ctx->stream>>>(C->nIt, C->flat_sub, C->flat_glob, C->offI, C->nI,
                                                                  C->nGs, C->offX, C->offGam, C->gam_list, XT, yI, cG,
                                                                  c);
         k_dd_scatter_G<T><<<grid1d(C->nG, 256), 256, 0, ctx->stream>>>(C->nG, C->gam_glob, cG, c);
         ctx->launches += 6;
-        if (C->nullv) {
-            k_null_dot<T><<<1, 256, 0, ctx->stream>>>(C->n, C->nullv, c, C->scal + 1);
-            k_null_sub<T><<<grid1d(C->n, 256), 256, 0, ctx->stream>>>(C->n, C->nullv, C->scal + 1, c);
-            ctx->launches += 2;
+        // the pinned solve differs from the kernel-free one by kernel vectors:
+        // remove them (the dense path's rank-one fix already gives n_p . c = n_p . d / alpha)
+        if (C->project) {
+            const LevelMat& L = ctx->levels.back();
+            HHO_TRY(null_project<T>(ctx, L.nf * L.b, L.nP, c));
         }
     }
     HHO_CUDA(cudaGetLastError());

@@ -122,6 +122,18 @@ struct Topo {
 
 struct Workspace;     // solver work vectors (solve.cu)
 struct CoarseSolver;  // coarse-level solver (coarse.cu)
+struct BatchWork;     // segmented FGMRES state of a batch (batch.cu)
+
+// Partition of the mesh into independent problems (a disjoint union): problem
+// p owns faces [face_off[p], face_off[p+1]) and elements [elem_off[p],
+// elem_off[p+1]).  A context without a declared batch is one problem.
+struct Problems {
+    int P = 1;
+    std::vector<int64_t> face_off, elem_off;
+    std::vector<int32_t> elem_prob;  // problem of every element
+    std::vector<char> has_null;      // no Neumann face: constant pressure in the kernel
+    bool declared = false;           // hho_set_batch was called
+};
 
 }  // namespace hho
 
@@ -137,8 +149,14 @@ struct hho_ctx {
     int smooth_its = 2;
     int prec = 0;
     std::vector<int> degrees;
-    double* null_vec0 = nullptr;         // unit constant-pressure vector at level 0 (or null)
-    bool has_null = false;
+    double* null_vec0 = nullptr;         // per-problem unit constant-pressure vectors at level 0 (or null)
+    bool has_null = false;               // some problem has a pressure kernel
+    hho::Problems probs;                 // problem partition (one problem unless a batch is declared)
+    double* null_w = nullptr;            // per element: weight of its first pressure unknown in its
+                                         // problem's unit kernel vector (0 for problems without kernel)
+    int64_t* d_elem_off = nullptr;       // device copy of probs.elem_off
+    hho::BatchWork* batch = nullptr;
+    int tile_rows = 2048;                // rows of the condensed vector per block in the segmented kernels
     hho::Workspace* ws = nullptr;
     hho::CoarseSolver* coarse = nullptr;
     int64_t coarse_its_total = 0;
@@ -201,6 +219,19 @@ hho_status vcycle(hho_ctx* ctx, const double* r, double* z);
 hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, hho_solve_info* info);
 void free_workspace(hho_ctx* ctx);
 void invalidate_graphs(hho_ctx* ctx);
+hho_status residual(hho_ctx* ctx, int l, const double* x, const double* b, double* r);
+hho_status null_build(hho_ctx* ctx);
+// x -= (n_p . x) n_p on the first pressure unknowns of every problem p with a
+// pressure kernel, at a level whose face blocks have b unknowns and element
+// blocks nP (one block per problem)
+template <typename T>
+hho_status null_project(hho_ctx* ctx, int64_t nf_rows, int nP, T* x);
+// batch.cu
+hho_status batch_set(hho_ctx* ctx, int P, const int64_t* face_off, const int64_t* elem_off);
+hho_status batch_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, int32_t* its,
+                       double* relres, hho_solve_info* info);
+hho_status autotune(hho_ctx* ctx, int reps, double* choice);
+void batch_free(hho_ctx* ctx);
 // coarse.cu
 hho_status coarse_setup(hho_ctx* ctx);
 hho_status coarse_apply(hho_ctx* ctx, const double* d, double* c);

@@ -43,6 +43,7 @@
 #include <map>
 
 #include "internal.h"
+#include "krylov.cuh"
 
 namespace hho {
 
@@ -51,7 +52,6 @@ namespace {
 constexpr int GMAX = 8192;  // largest grid of any reduction kernel
 constexpr int RT = 256;     // threads per block of the reduction kernels
 constexpr int NVMAX = 8;    // dot products per kernel
-constexpr int MMAX = 64;    // largest GMRES restart
 
 int grid1d(int64_t n, int tpb) {
     int64_t g = (n + tpb - 1) / tpb;
@@ -85,162 +85,6 @@ template <>
 LV<float> view<float>(const LevelMat& L) {
     return LV<float>{L.nf, L.ne, L.b, L.nP, L.ff_col, L.ff_nsl, L.fp_col, L.pf_col, L.pf_nsl,
                      L.ff32, L.fp32, L.pf32, L.pp32, L.dinv32, L.minv32};
-}
-
-// Scalar area of one GMRES instance with restart m.
-//   [0] beta^2  [1] beta  [2] m_eff  [3] residual estimate  [4] breakdown  [5] norm of the pending w
-//   H (m+1) x m column-major, cs[m], sn[m], g[m+1], t1[m+1], t2[m+1], nrm
-struct GS {
-    int m, H, cs, sn, g, t1, t2, nrm, total;
-};
-GS gs_layout(int m) {
-    GS s;
-    s.m = m;
-    int o = 8;
-    s.H = o;
-    o += (m + 1) * m;
-    s.cs = o;
-    o += m;
-    s.sn = o;
-    o += m;
-    s.g = o;
-    o += m + 1;
-    s.t1 = o;
-    o += m + 1;
-    s.t2 = o;
-    o += m + 1;
-    s.nrm = o;
-    o += 1;
-    s.total = o;
-    return s;
-}
-
-enum Hook { HOOK_NONE = 0, HOOK_START = 1, HOOK_COLUMN = 2, HOOK_COLUMN_PY = 3 };
-
-// Type of the per-thread and per-warp part of a dot product (see the header).
-template <typename T>
-struct AccT {
-    using type = double;
-};
-template <>
-struct AccT<float> {
-    using type = float;
-};
-
-
-// 1 / *den (0 when *den is 0) computed once per block: divisions, FP64 ones in
-// particular, are costly per thread.  Call from all threads of the block.
-template <typename T>
-__device__ __forceinline__ T block_inverse(const double* __restrict__ den) {
-    __shared__ T s_inv;
-    if (threadIdx.x == 0) {
-        const T dv = (T)*den;
-        s_inv = (dv == T(0)) ? T(0) : T(1) / dv;
-    }
-    __syncthreads();
-    return s_inv;
-}
-
-// Coefficients of a pending second Gram-Schmidt pass (FP64 storage) staged in
-// shared memory in the level type.  Call from all threads of the block.
-template <typename T>
-__device__ __forceinline__ const T* stage_pending(const double* __restrict__ pc, int npend) {
-    __shared__ T s_pc[MMAX];
-    for (int q = threadIdx.x; q < npend; q += blockDim.x) s_pc[q] = (T)pc[q];
-    __syncthreads();
-    return s_pc;
-}
-
-// w''[o] = w'[o] - sum_{q < npend} pc_q Vp_q[o]: the second pass of the last
-// Arnoldi step, applied where w'' is consumed
-template <typename T>
-__device__ __forceinline__ T pending(const T* __restrict__ w, const T* __restrict__ Vp, int64_t ld, int npend,
-                                     const T* s_pc, int64_t o) {
-    T u = w[o];
-    for (int q = 0; q < npend; ++q) u -= s_pc[q] * Vp[q * ld + o];
-    return u;
-}
-
-// Scalar work once the reductions of a kernel are final, run by the whole last
-// block: the operands are first staged in shared memory by all threads in one
-// round of loads, then one thread does the short serial recurrence there, in
-// the arithmetic type A of the kernel (FP32 for the FP32 V-cycle: FP64
-// arithmetic is scarce on this part, and storage stays FP64).
-//   START   fresh = ||r||^2: beta, residual estimate, g = beta e_1
-//   COLUMN  fresh = ||w||^2 after the second projection: Hessenberg column j
-//           (t1 + t2, ||w||), the earlier Givens rotations applied to it, the
-//           new rotation, and the updated residual estimate |g_{j+1}|
-//   COLUMN_PY  the same with fresh = ||w'||^2 before the second projection
-//           w'' = w' - V t2 (t2 = V^T w'), which is left to the consumer of
-//           w'': ||w''||^2 = ||w'||^2 - ||t2||^2 for orthonormal V (the
-//           correction t2 is small against w', so the difference is benign)
-template <typename A>
-__device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j, A fresh) {
-    __shared__ A s_h[MMAX + 2], s_cs[MMAX], s_sn[MMAX], s_misc[2];
-    if (hook == HOOK_START) {
-        const A beta = sqrt(fresh);
-        for (int i = threadIdx.x; i <= L.m; i += blockDim.x) sc[L.g + i] = (i == 0) ? (double)beta : 0.0;
-        if (threadIdx.x == 0) {
-            sc[1] = beta;
-            sc[2] = 0.0;
-            sc[3] = beta;
-            sc[4] = (beta == A(0)) ? 1.0 : 0.0;
-            sc[5] = beta;
-        }
-        return;
-    }
-    if (hook != HOOK_COLUMN && hook != HOOK_COLUMN_PY) return;
-    const int ld = L.m + 1;
-    double* H = sc + L.H;
-    __shared__ A s_t2sq[MMAX + 1];
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        const A t2 = (A)sc[L.t2 + i];
-        s_h[i] = (A)sc[L.t1 + i] + t2;
-        s_t2sq[i] = t2 * t2;
-        if (i < j) {
-            s_cs[i] = (A)sc[L.cs + i];
-            s_sn[i] = (A)sc[L.sn + i];
-        }
-    }
-    if (threadIdx.x == 0) {
-        s_misc[0] = (A)sc[4];
-        s_misc[1] = (A)sc[L.g + j];
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    if (s_misc[0] != A(0)) {  // after a breakdown the remaining columns are ignored
-        for (int i = 0; i <= L.m; ++i) H[j * ld + i] = 0.0;
-        sc[5] = 0.0;
-        return;
-    }
-    A hn2 = fresh;
-    if (hook == HOOK_COLUMN_PY) {
-        for (int i = 0; i <= j; ++i) hn2 -= s_t2sq[i];
-        hn2 = hn2 > A(0) ? hn2 : A(0);
-    }
-    const A hn = sqrt(hn2);
-    s_h[j + 1] = hn;
-    sc[5] = hn;
-    for (int i = 0; i < j; ++i) {
-        const A c = s_cs[i], s = s_sn[i];
-        const A a = s_h[i], bb = s_h[i + 1];
-        s_h[i] = c * a + s * bb;
-        s_h[i + 1] = -s * a + c * bb;
-    }
-    const A a = s_h[j], bb = s_h[j + 1];
-    const A r = hypot(a, bb);
-    const A c = (r == A(0)) ? A(1) : a / r, s = (r == A(0)) ? A(0) : bb / r;
-    s_h[j] = r;
-    s_h[j + 1] = A(0);
-    for (int i = 0; i <= j + 1; ++i) H[j * ld + i] = s_h[i];
-    sc[L.cs + j] = c;
-    sc[L.sn + j] = s;
-    const A gj = s_misc[1];
-    sc[L.g + j] = c * gj;
-    sc[L.g + j + 1] = -s * gj;
-    sc[3] = fabs(s * gj);
-    sc[2] = j + 1;
-    if (hn == A(0)) sc[4] = 1.0;
 }
 
 // Block reduction of the accumulators acc[0..nv0-1] and, when self is set, of
@@ -820,12 +664,26 @@ __global__ void k_zero(int64_t n, T* __restrict__ dst) {
         dst[i] = T(0);
 }
 
-// x -= (n.x) n, the dot product already in *dot
-__global__ void k_null_project(int64_t n, double* __restrict__ x, const double* __restrict__ nv,
-                               const double* __restrict__ dot) {
-    const double a = *dot;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] -= a * nv[i];
+// x -= (n_p . x) n_p for every problem p (one block each): n_p is non-zero
+// only on the first pressure unknown of p's elements, with weight w[T]
+// (0 throughout for a problem without pressure kernel).  xp points at the
+// element part of the vector (element blocks of nP).  Fixed-order tree.
+template <typename T>
+__global__ void __launch_bounds__(512) k_null_proj(const int64_t* __restrict__ elem_off,
+                                                   const double* __restrict__ w, T* __restrict__ xp, int nP) {
+    __shared__ double sm[512];
+    const int64_t e0 = elem_off[blockIdx.x], e1 = elem_off[blockIdx.x + 1];
+    double s = 0.0;
+    for (int64_t E = e0 + threadIdx.x; E < e1; E += blockDim.x) s += w[E] * (double)xp[E * nP];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double a = sm[0];
+    if (a == 0.0) return;
+    for (int64_t E = e0 + threadIdx.x; E < e1; E += blockDim.x) xp[E * nP] = T((double)xp[E * nP] - a * w[E]);
 }
 
 int rows_per_thread(int nrow) {
@@ -1067,6 +925,12 @@ hho_status spmv(hho_ctx* ctx, int l, const double* x, double* y) {
     return HHO_OK;
 }
 
+hho_status residual(hho_ctx* ctx, int l, const double* x, const double* b, double* r) {
+    launch_spmv_dot<double>(ctx, l, x, b, r, 1, nullptr, 0, 0, 0, nullptr, HOOK_NONE, nullptr, gs_layout(1), 0);
+    HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
+}
+
 hho_status spmv_f32(hho_ctx* ctx, int l, const float* x, float* y) {
     const LevelMat& L = ctx->levels[l];
     if (!L.ff32) {
@@ -1268,12 +1132,52 @@ hho_status vcycle(hho_ctx* ctx, const double* r, double* z) {
     return HHO_OK;
 }
 
-static hho_status project_null(hho_ctx* ctx, int64_t n, double* x, const double* nv, double* tmp) {
-    GS g = gs_layout(1);
-    launch_update_dot<double>(ctx, n, x, nullptr, n, 0, nullptr, 0.0, nv, 1, 0, tmp, HOOK_NONE, nullptr, g, 0);
-    k_null_project<<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x, nv, tmp);
+template <typename T>
+hho_status null_project(hho_ctx* ctx, int64_t nf_rows, int nP, T* x) {
+    if (!ctx->has_null) return HHO_OK;
+    k_null_proj<T><<<ctx->probs.P, 512, 0, ctx->stream>>>(ctx->d_elem_off, ctx->null_w, x + nf_rows, nP);
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
+}
+template hho_status null_project<double>(hho_ctx*, int64_t, int, double*);
+template hho_status null_project<float>(hho_ctx*, int64_t, int, float*);
+
+// Per-problem pressure kernels: a problem without Neumann face has the
+// constant pressure in the kernel of its operator; its unit kernel vector
+// has sqrt(|T|) / sqrt(|Omega_p|) on the first (constant) pressure unknown of
+// each element T (orthonormal bases: the constant 1 has coefficient sqrt|T|).
+hho_status null_build(hho_ctx* ctx) {
+    Problems& pr = ctx->probs;
+    const Disc& D = ctx->disc;
+    pr.has_null.assign(pr.P, 1);
+    for (int p = 0; p < pr.P; ++p)
+        for (int64_t F = pr.face_off[p]; F < pr.face_off[p + 1]; ++F)
+            if (D.h_fbc[F] == 2) {
+                pr.has_null[p] = 0;
+                break;
+            }
+    ctx->has_null = false;
+    for (char h : pr.has_null) ctx->has_null |= (h != 0);
+    dfree(ctx->null_w);
+    ctx->null_w = nullptr;
+    dfree(ctx->d_elem_off);
+    ctx->d_elem_off = nullptr;
+    if (!ctx->has_null) return HHO_OK;
+    std::vector<double> meas(D.ne), w(D.ne, 0.0);
+    HHO_CUDA(cudaMemcpy(meas.data(), D.emeas, D.ne * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int p = 0; p < pr.P; ++p) {
+        if (!pr.has_null[p]) continue;
+        double tot = 0.0;
+        for (int64_t T = pr.elem_off[p]; T < pr.elem_off[p + 1]; ++T) tot += meas[T];
+        const double inv = 1.0 / std::sqrt(tot);
+        for (int64_t T = pr.elem_off[p]; T < pr.elem_off[p + 1]; ++T) w[T] = std::sqrt(meas[T]) * inv;
+    }
+    HHO_TRY(dalloc(ctx, &ctx->null_w, w.size()));
+    HHO_CUDA(cudaMemcpy(ctx->null_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    HHO_TRY(dalloc(ctx, &ctx->d_elem_off, pr.elem_off.size()));
+    HHO_CUDA(cudaMemcpy(ctx->d_elem_off, pr.elem_off.data(), pr.elem_off.size() * sizeof(int64_t),
+                        cudaMemcpyHostToDevice));
     return HHO_OK;
 }
 
@@ -1324,22 +1228,7 @@ hho_status pmg_build(hho_ctx* ctx) {
     HHO_TRY(dalloc(ctx, &W->counter, 16));
     HHO_CUDA(cudaMemset(W->counter, 0, 16 * sizeof(unsigned)));
     HHO_CUDA(cudaMallocHost(&W->h_sc, 64 * sizeof(double)));
-    bool neumann = false;
-    for (auto b : ctx->disc.h_fbc) neumann |= (b == 2);
-    ctx->has_null = !neumann;
-    dfree(ctx->null_vec0);
-    ctx->null_vec0 = nullptr;
-    if (ctx->has_null) {
-        const LevelMat& L = ctx->levels[0];
-        std::vector<double> meas(L.ne), v(L.n, 0.0);
-        HHO_CUDA(cudaMemcpy(meas.data(), ctx->disc.emeas, L.ne * sizeof(double), cudaMemcpyDeviceToHost));
-        double s = 0.0;
-        for (int64_t T = 0; T < L.ne; ++T) s += meas[T];
-        const double inv = 1.0 / std::sqrt(s);
-        for (int64_t T = 0; T < L.ne; ++T) v[L.nf * L.b + T * L.nP] = std::sqrt(meas[T]) * inv;
-        HHO_TRY(dalloc(ctx, &ctx->null_vec0, v.size()));
-        HHO_CUDA(cudaMemcpy(ctx->null_vec0, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
-    }
+    HHO_TRY(null_build(ctx));
     HHO_TRY(coarse_setup(ctx));
     return HHO_OK;
 }
@@ -1368,7 +1257,6 @@ hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, 
     }
     GS G = gs_layout(restart);
     double* sc = W->fsc;
-    double* tmp = sc + G.total;
     double* hs = W->h_sc;
     double* bvec = W->fb;
     cudaEvent_t e0, e1;
@@ -1378,7 +1266,7 @@ hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, 
     ctx->coarse_its_total = 0;
     k_convert<double, double><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, ctx->rhs, bvec);
     ++ctx->launches;
-    if (ctx->has_null) HHO_TRY(project_null(ctx, n, bvec, ctx->null_vec0, tmp));
+    HHO_TRY(null_project<double>(ctx, L0.nf * L0.b, L0.nP, bvec));
     k_zero<double><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x);
     ++ctx->launches;
     // ||b||, which is also beta of the first restart cycle (r = b)
@@ -1436,7 +1324,7 @@ hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, 
             }
         }
         if (ctx->has_null) {
-            HHO_TRY(project_null(ctx, n, x, ctx->null_vec0, tmp));
+            HHO_TRY(null_project<double>(ctx, L0.nf * L0.b, L0.nP, x));
             launch_spmv_dot<double>(ctx, 0, x, bvec, W->fw, 1, nullptr, n, 0, 1, sc + 0, HOOK_START, sc, G, 0);
             HHO_TRY(host_read(ctx, sc + 1, hs, 1));
             beta = hs[0];

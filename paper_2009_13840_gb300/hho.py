@@ -27,7 +27,7 @@ NODES = {"elem": 0, "face": 1}
 SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "hho_assemble_noalloc", "pmg_setup", "pmg_vcycle", "hho_spmv", "hho_spmv_f32",
            "hho_solve", "hho_recover", "hho_errors", "hho_get_element_schur", "hho_get_level_coo",
            "hho_set_element_schur", "hho_launch_count", "hho_set_option", "hho_destroy",
-           "hho_last_error"]
+           "hho_last_error", "hho_set_batch", "hho_solve_batch", "hho_autotune"]
 
 
 class HHOError(RuntimeError):
@@ -83,6 +83,10 @@ def load(path: str = LIB_PATH):
         "hho_set_option": (C.c_int, [P, C.c_char_p, C.c_double]),
         "hho_destroy": (C.c_int, [P]),
         "hho_last_error": (C.c_char_p, [P]),
+        "hho_set_batch": (C.c_int, [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "hho_solve_batch": (C.c_int, [P, C.c_double, C.c_int, C.c_int, P, C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_double), C.POINTER(SolveInfo)]),
+        "hho_autotune": (C.c_int, [P, C.c_int, C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -205,6 +209,34 @@ class Context:
         if raise_on_fail:
             self._check(st)
         return info.as_dict()
+
+    def set_batch(self, face_off, elem_off):
+        """Declare the mesh a disjoint union of problems (offsets of n_prob + 1 entries)."""
+        fo = np.ascontiguousarray(face_off, dtype=np.int64)
+        eo = np.ascontiguousarray(elem_off, dtype=np.int64)
+        if fo.shape != eo.shape or fo.ndim != 1:
+            raise ValueError("face_off and elem_off must be 1-D of the same length")
+        self._check(self.lib.hho_set_batch(self.h, int(fo.size - 1), fo.ctypes.data_as(C.POINTER(C.c_int64)),
+                                           eo.ctypes.data_as(C.POINTER(C.c_int64))))
+        self.n_prob = int(fo.size - 1)
+
+    def solve_batch(self, x, rtol=1e-8, maxit=1000, restart=50, raise_on_fail=True):
+        """One FGMRES per problem of the declared batch; returns (info, iterations, relative residuals)."""
+        info = SolveInfo()
+        its = np.zeros(self.n_prob, dtype=np.int32)
+        rr = np.zeros(self.n_prob, dtype=np.float64)
+        st = self.lib.hho_solve_batch(self.h, rtol, maxit, restart, _ptr(x),
+                                      its.ctypes.data_as(C.POINTER(C.c_int32)),
+                                      rr.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info))
+        if raise_on_fail:
+            self._check(st)
+        return info.as_dict(), its, rr
+
+    def autotune(self, reps=5):
+        """Time the operator-kernel variants (and batch tile sizes) and keep the fastest."""
+        out = (C.c_double * 3)()
+        self._check(self.lib.hho_autotune(self.h, int(reps), out))
+        return dict(spmv_rows=int(out[0]), spmv_grid=int(out[1]), tile_rows=int(out[2]))
 
     def recover(self, x):
         n_loc = self.local_size()
