@@ -57,6 +57,13 @@ def parse():
     ap.add_argument("--probe-spmv", action="store_true", help="three FP32 and one FP64 level-0 operator launches")
     ap.add_argument("--coarse-fp32", type=int, default=1, choices=[0, 1],
                     help="FP32 coarse solve inside the FP32 V-cycle (velocity-only condensation default)")
+    ap.add_argument("--workload", default="solve", choices=["solve", "batch"],
+                    help="solve: the 128x128 triangle workload; batch: many independent small problems")
+    ap.add_argument("--batch-n", type=int, default=256, help="problems in the batched workload")
+    ap.add_argument("--batch-seed", type=int, default=12345)
+    ap.add_argument("--batch-cond", default="v", choices=["v", "vp"])
+    ap.add_argument("--batch-compare", type=int, default=16,
+                    help="problems of the batch also solved one by one for the batching speedup (0: skip)")
     return ap.parse_args()
 
 
@@ -352,10 +359,175 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def oracle_batch_sample(probs, cond, rtol, budget_s=15.0):
+    """The oracle as it stands on the first problems of the batch, solved one by
+    one until about budget_s seconds of solves: returns (DOF/s, problems, DOFs, seconds)."""
+    from oracle.hho import HHO
+    from oracle.pmg import PMG, fgmres
+    dofs, secs, done = 0, 0.0, 0
+    for pr in probs:
+        h = HHO(pr.mesh, pr.k, cond)
+        rhs = h.assemble_rhs(*h.data_values(pr.field))
+        pmg = PMG(h, list(range(pr.k, -1, -1)))
+        t0 = time.perf_counter()
+        fgmres(h.S, pmg.apply, rhs, rtol=rtol, null=h.null_vector())
+        secs += time.perf_counter() - t0
+        dofs += h.ndof
+        done += 1
+        if secs >= budget_s:
+            break
+    return dofs / secs, done, dofs, secs
+
+
+def run_batch(args):
+    """Batched workload: independent 2D problems (quad or triangle meshes of 8^2 to
+    64^2 cells, jitter 0.2h, k in 1..4, homogeneous Dirichlet data, forcing of 8
+    random trigonometric modes), one union context per degree k; one step solves
+    every problem to its own 1e-8 relative residual."""
+    import torch
+    from paper_2009_13840_gb300 import build, hho
+    from synthetic.batch import BatchField, batch_problems, group_by_degree, union_mesh
+    build.build()
+    probs = batch_problems(args.batch_n, seed=args.batch_seed)
+    groups = group_by_degree(probs)
+    stream = torch.cuda.Stream()
+    cf = 1 if (args.prec == "fp32" and args.batch_cond == "v") else 0
+
+    def make(idx, k):
+        m, fo, eo, sh = union_mesh([probs[i].mesh for i in idx])
+        ctx = hho.Context(m, k, args.batch_cond, stream=stream)
+        ctx.set_batch(fo, eo)
+        data = hho.data_arrays(ctx, BatchField([probs[i].field for i in idx], sh))
+        ctx.assemble(*data)
+        ctx.set_option("coarse_fp32", cf)
+        ctx.pmg_setup(list(range(k, -1, -1)), smooth_its=2, prec=args.prec)
+        return ctx, data
+
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        G = []
+        for k, idx in groups.items():
+            ctx, data = make(idx, k)
+            tune = ctx.autotune(reps=3)
+            x = torch.empty(ctx.ndof(0), dtype=torch.float64, device="cuda")
+            G.append(dict(k=k, idx=idx, ctx=ctx, x=x, tune=tune, data=data))
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        ndof = sum(g["ctx"].ndof(0) for g in G)
+        flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device="cuda")
+
+        def step():
+            res = []
+            for g in G:
+                info, its, rr = g["ctx"].solve_batch(g["x"], rtol=args.rtol)
+                res.append((info, its, rr))
+            return res
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        launches0 = sum(g["ctx"].launch_count() for g in G)
+        times, last = [], None
+        with Clocks(torch.cuda.current_device()) as clk:
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                last = step()
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        launches = sum(g["ctx"].launch_count() for g in G) - launches0
+        ms = float(np.mean(times))
+        its = np.concatenate([r[1] for r in last])
+        rr = np.concatenate([r[2] for r in last])
+        # end to end: data from pinned host memory, assembly, solve, solution back
+        hdata = [[t.cpu().pin_memory() for t in g["data"]] for g in G]
+        hx = [torch.empty(g["x"].numel(), dtype=torch.float64).pin_memory() for g in G]
+        et = []
+        for i in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for g, hd, hxx in zip(G, hdata, hx):
+                dd = [torch.empty_like(t, device="cuda").copy_(t, non_blocking=True) for t in hd]
+                g["ctx"].assemble(*dd)
+                g["ctx"].solve_batch(g["x"], rtol=args.rtol)
+                hxx.copy_(g["x"], non_blocking=True)
+            stream.synchronize()
+            if i >= args.warmup:
+                et.append(time.perf_counter() - t1)
+        e2e_s = float(np.mean(et))
+        h2d = int(sum(t.numel() * 8 for hd in hdata for t in hd))
+        d2h = int(ndof * 8)
+        # batching speedup: the first problems solved one by one against the same problems as a batch
+        cmp = None
+        if args.batch_compare > 0:
+            sub = list(range(min(args.batch_compare, len(probs))))
+            seq_ms = 0.0
+            seq_its = []
+            for i in sub:
+                pr = probs[i]
+                c1 = hho.Context(pr.mesh, pr.k, args.batch_cond, stream=stream)
+                c1.assemble(*hho.data_arrays(c1, pr.field))
+                c1.set_option("coarse_fp32", cf)
+                c1.pmg_setup(list(range(pr.k, -1, -1)), smooth_its=2, prec=args.prec)
+                x1 = torch.empty(c1.ndof(0), dtype=torch.float64, device="cuda")
+                c1.solve(x1, rtol=args.rtol)
+                info = c1.solve(x1, rtol=args.rtol)
+                seq_ms += info["solve_ms"]
+                seq_its.append(info["iterations"])
+                c1.close()
+            sg = group_by_degree([probs[i] for i in sub])
+            bat_ms = 0.0
+            bat_its = []
+            for k, idx in sg.items():
+                c2, _ = make([sub[i] for i in idx], k)
+                x2 = torch.empty(c2.ndof(0), dtype=torch.float64, device="cuda")
+                c2.solve_batch(x2, rtol=args.rtol)
+                info, its2, _ = c2.solve_batch(x2, rtol=args.rtol)
+                bat_ms += info["solve_ms"]
+                bat_its += list(its2)
+                c2.close()
+            cmp = {"problems": len(sub), "sequential_ms": seq_ms, "batched_ms": bat_ms,
+                   "speedup": seq_ms / bat_ms, "sequential_iterations_mean": float(np.mean(seq_its)),
+                   "batched_iterations_mean": float(np.mean(bat_its))}
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, npb, nd, dt = oracle_batch_sample(probs, args.batch_cond, args.rtol)
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"oracle FGMRES+p-MG solves of the first {npb} problems of the batch one by one "
+                         f"({nd} DOFs, {dt:.1f} s); setup excluded"}
+    wname = (f"batch{args.batch_n}-seed{args.batch_seed} quad/tri 8^2..64^2 jit0.2 k=1..4 "
+             f"{args.batch_cond}-cond all-Dirichlet trig-forcing, one union context per k")
+    line = {
+        "metric": METRIC, "value": ndof / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 FGMRES + f32 V-cycle" if args.prec == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": wname, "problems": len(probs), "dofs": ndof, "vcycle_precision": args.prec,
+                   "groups": [{"k": g["k"], "problems": len(g["idx"]), "dofs": g["ctx"].ndof(0),
+                               "autotuned": g["tune"]} for g in G],
+                   "iterations_max": int(its.max()), "iterations_mean": float(its.mean()),
+                   "rel_residual_max": float(rr.max()), "setup_s": setup_s,
+                   "l2": "flushed between steps (512 MiB write)", "parallelism": "single",
+                   "vs_sequential": cmp},
+        "cpu_baseline": cpu,
+        "e2e": {"value": ndof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    for g in G:
+        g["ctx"].close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 
