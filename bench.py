@@ -57,8 +57,10 @@ def parse():
     ap.add_argument("--probe-spmv", action="store_true", help="three FP32 and one FP64 level-0 operator launches")
     ap.add_argument("--coarse-fp32", type=int, default=1, choices=[0, 1],
                     help="FP32 coarse solve inside the FP32 V-cycle (velocity-only condensation default)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "batch"],
-                    help="solve: the 128x128 triangle workload; batch: many independent small problems")
+    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "learned"],
+                    help="solve: the 128x128 triangle workload; batch: many independent small problems; "
+                         "learned: the learned smoother against the plain one")
+    ap.add_argument("--learned-train-n", type=int, default=32, help="mesh size the learned smoother is trained on")
     ap.add_argument("--batch-n", type=int, default=256, help="problems in the batched workload")
     ap.add_argument("--batch-seed", type=int, default=12345)
     ap.add_argument("--batch-cond", default="v", choices=["v", "vp"])
@@ -522,12 +524,106 @@ def run_batch(args):
         g["ctx"].close()
 
 
+def run_learned(args):
+    """Learned smoother: a two-layer MLP (hidden 128, BF16) trained on the GPU on
+    the finest-level post-smoother pairs of the FP64 V-cycle on a smaller mesh of
+    the family, then used in the 128x128 triangle workload under
+    velocity-pressure condensation (where block-Jacobi smoothing is weak);
+    one step = one solve to 1e-8 with the learned smoother, timed against the
+    plain smoother on the same problem."""
+    import torch
+    from paper_2009_13840_gb300 import build, hho
+    build.build()
+    cond, k = "vp", args.k
+    stream = torch.cuda.Stream()
+    degrees = list(range(k, -1, -1))
+    with torch.cuda.stream(stream):
+        tmesh, fld, _ = workload(args.learned_train_n, k, cond)
+        tr = hho.Context(tmesh, k, cond, stream=stream)
+        tr.assemble(*hho.data_arrays(tr, fld))
+        tr.pmg_setup(degrees, smooth_its=2, prec="fp64")
+        tr.mlp_init(hidden=128, seed=11)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nsamp = tr.mlp_generate(n_vec=16, seed=3, kind=2)
+        loss = tr.mlp_train(steps=1500, batch=4096, lr=1e-3, seed=5)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        W = tr.mlp_weights()
+        tr.close()
+        mesh, fld, wname = workload(args.n, k, cond)
+        ctx = hho.Context(mesh, k, cond, stream=stream)
+        f, gD, gN = hho.data_arrays(ctx, fld)
+        ctx.assemble(f, gD, gN)
+        ctx.pmg_setup(degrees, smooth_its=2, prec=args.prec)
+        ctx.mlp_init(hidden=128, seed=0)
+        ctx.mlp_weights(W)
+        ndof = ctx.ndof(0)
+        x = torch.empty(ndof, dtype=torch.float64, device="cuda")
+        flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device="cuda")
+
+        def timed(learned, steps, clk=None):
+            ctx.set_option("learned_smoother", learned)
+            for _ in range(args.warmup):
+                ctx.solve(x, rtol=args.rtol, maxit=2000)
+            times, info = [], None
+            for _ in range(steps):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                info = ctx.solve(x, rtol=args.rtol, maxit=2000)
+                times.append(info["solve_ms"])
+            return float(np.mean(times)), info
+
+        ms_plain, inf_plain = timed(0, max(1, args.steps // 2))
+        launches0 = ctx.launch_count()
+        with Clocks(torch.cuda.current_device()) as clk:
+            ms, inf = timed(1, args.steps)
+        launches = ctx.launch_count() - launches0
+        hf, hgD, hgN = f.cpu().pin_memory(), gD.cpu().pin_memory(), gN.cpu().pin_memory()
+        hx = torch.empty(ndof, dtype=torch.float64).pin_memory()
+        et = []
+        for i in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            dd = [torch.empty_like(t, device="cuda").copy_(t, non_blocking=True) for t in (hf, hgD, hgN)]
+            ctx.assemble(*dd)
+            ctx.solve(x, rtol=args.rtol, maxit=2000)
+            hx.copy_(x, non_blocking=True)
+            stream.synchronize()
+            if i >= args.warmup:
+                et.append(time.perf_counter() - t1)
+        ctx.close()
+    line = {
+        "metric": METRIC, "value": ndof / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 FGMRES + f32 V-cycle + bf16 MLP" if args.prec == "fp32" else "f64 + bf16 MLP",
+        "data": "synthetic",
+        "config": {"workload": wname + " learned smoother", "dofs": ndof, "vcycle_precision": args.prec,
+                   "fgmres_iterations": inf["iterations"], "rel_residual_fp64": inf["rel_residual"],
+                   "plain_smoother": {"ms_per_solve": ms_plain, "fgmres_iterations": inf_plain["iterations"],
+                                      "dof_per_s": ndof / (ms_plain / 1e3)},
+                   "speedup_vs_plain": ms_plain / ms,
+                   "training": {"mesh": f"tri{args.learned_train_n}x{args.learned_train_n}", "samples": int(nsamp),
+                                "steps": 1500, "batch": 4096, "hidden": 128, "seconds": train_s,
+                                "loss_first": float(loss[:10].mean()), "loss_last": float(loss[-50:].mean())},
+                   "l2": "flushed between steps (512 MiB write)", "parallelism": "single"},
+        "cpu_baseline": None,
+        "e2e": {"value": ndof / float(np.mean(et)), "unit": UNIT, "h2d_bytes_per_step": int((f.numel() + gD.numel() + gN.numel()) * 8),
+                "d2h_bytes_per_step": int(ndof * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -171,6 +171,10 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
  *                       element per thread
  *   "spmv_grid"         blocks of 256 threads of the operator kernels,
  *                       1..8192 (0 = automatic: about one 32-row tile per warp)
+ *   "learned_smoother"  1: add the learned correction (hho_mlp_*) to the
+ *                       block-Jacobi output in the finest-level post-smoother;
+ *                       0 (default): plain smoother.  HHO_ERR_STATE without
+ *                       hho_mlp_init.
  *   "coarse_fp32"       with HHO_FP32: 1 keeps FP32 copies of the coarse
  *                       solver's inverse blocks and runs the coarse solve in
  *                       FP32 (FP32 multiply-adds, no FP64 round trip);
@@ -226,6 +230,54 @@ hho_status hho_set_batch(hho_ctx* ctx, int n_prob, const int64_t* face_off, cons
  * above rtol after maxit iterations. */
 hho_status hho_solve_batch(hho_ctx* ctx, double rtol, int maxit, int restart, double* d_x, int32_t* h_iters,
                            double* h_relres, hho_solve_info* info);
+
+/* Learned block smoother (no counterpart in the paper).  A two-layer MLP
+ * (hidden width `hidden`, BF16 weights, FP32 accumulation) maps the residual
+ * of a face's neighbourhood -- the residual blocks of the faces in the face's
+ * operator slots (the face, the other faces of its first element, of its
+ * second) and the pressure blocks of its two elements, divided by their norm
+ * s_F -- to a correction s_F y_F of the block-Jacobi output on the face's rows
+ * in the finest-level post-smoother (option "learned_smoother" = 1; the plain
+ * smoother is the fallback).  All entry points need pmg_setup first.
+ *
+ * hho_mlp_init: sizes from the finest level (d_in = slots*b + 2 nP padded to
+ * a multiple of 16, at most 256; d_out = b padded to a multiple of 8) and a
+ * seeded initialisation; hidden in 8..256, multiple of 8. */
+hho_status hho_mlp_init(hho_ctx* ctx, int hidden, uint64_t seed);
+
+/* dims (host, 4): {d_in, hidden, d_out, raw feature count}. */
+hho_status hho_mlp_dims(hho_ctx* ctx, int32_t* dims);
+
+/* Get (set = 0) or set (set = 1) the FP32 master parameters (host, row-major:
+ * W1 d_in x hidden, b1 hidden, W2 hidden x d_out, b2 d_out); setting refreshes
+ * the BF16 copies. */
+hho_status hho_mlp_weights(hho_ctx* ctx, int set, double* W1, double* b1, double* W2, double* b2);
+
+/* Network inputs of a finest-level vector d_r (device, ndof(0)): d_X (device,
+ * nf x d_in floats holding the BF16-rounded normalised features) and d_s
+ * (device, nf floats: the norms s_F). */
+hho_status hho_mlp_features(hho_ctx* ctx, const double* d_r, float* d_X, float* d_s);
+
+/* Training set from the FP64 V-cycle (pmg_setup with HHO_FP64, learned
+ * smoother off) applied to r0 = S e0 for n_vec (1..4096) seeded white-noise
+ * errors e0: kind 0 takes the pair it is applied to (e = e0, r = r0), kind 1
+ * the pair it leaves (e = e0 - MG(r0), r = S e), kind 2 the pair its
+ * finest-level post-smoother meets (e = e0 - x with x the iterate after the
+ * coarse correction, r = S e; the distribution the learned correction acts
+ * on).  One sample per face, target (e_F - (M_J^{-1} r)_F) / s_F.
+ * *n_samples (may be NULL) = n_vec * nf. */
+hho_status hho_mlp_generate(hho_ctx* ctx, int n_vec, uint64_t seed, int kind, int64_t* n_samples);
+
+/* `steps` Adam steps (lr, beta = 0.9 / 0.999) on minibatches of `batch` samples
+ * drawn with `seed`; loss = mean over samples of ||y - t||^2.  h_loss (host,
+ * steps doubles, may be NULL) receives each step's loss. */
+hho_status hho_mlp_train(hho_ctx* ctx, int steps, int batch, double lr, uint64_t seed, double* h_loss);
+
+/* Loss and parameter gradients of the training kernels for a given
+ * minibatch: d_X (device, batch x d_in floats), d_T (device, batch x d_out);
+ * host outputs as in hho_mlp_weights. */
+hho_status hho_mlp_grads(hho_ctx* ctx, const float* d_X, const float* d_T, int batch, double* h_loss, double* h_gW1,
+                         double* h_gb1, double* h_gW2, double* h_gb2);
 
 /* Autotuner (after pmg_setup): times `reps` V-cycles for every candidate of
  * "spmv_rows" (0, 2, 4) x "spmv_grid" (automatic, 1216, 2432) and, for a

@@ -122,6 +122,49 @@ hho_status hho_solve_batch(hho_ctx* ctx, double rtol, int maxit, int restart, do
     return batch_solve(ctx, rtol, maxit, restart, d_x, h_iters, h_relres, info);
 }
 
+hho_status hho_mlp_init(hho_ctx* ctx, int hidden, uint64_t seed) {
+    if (!ctx) return HHO_ERR_ARG;
+    return mlp_init(ctx, hidden, seed);
+}
+
+hho_status hho_mlp_dims(hho_ctx* ctx, int32_t* dims) {
+    if (!ctx || !dims) return HHO_ERR_ARG;
+    int d[4];
+    HHO_TRY(mlp_dims(ctx, d));
+    for (int i = 0; i < 4; ++i) dims[i] = d[i];
+    return HHO_OK;
+}
+
+hho_status hho_mlp_weights(hho_ctx* ctx, int set, double* W1, double* b1, double* W2, double* b2) {
+    if (!ctx || !W1 || !b1 || !W2 || !b2 || (set != 0 && set != 1)) return HHO_ERR_ARG;
+    return mlp_weights(ctx, set, W1, b1, W2, b2);
+}
+
+hho_status hho_mlp_features(hho_ctx* ctx, const double* d_r, float* d_X, float* d_s) {
+    if (!ctx || !d_r || !d_X || !d_s) return HHO_ERR_ARG;
+    return mlp_features(ctx, d_r, d_X, d_s);
+}
+
+hho_status hho_mlp_generate(hho_ctx* ctx, int n_vec, uint64_t seed, int kind, int64_t* n_samples) {
+    if (!ctx) return HHO_ERR_ARG;
+    if (!ctx->have_pmg) {
+        ctx->err = "hho_mlp_generate: call pmg_setup first";
+        return HHO_ERR_STATE;
+    }
+    return mlp_generate(ctx, n_vec, seed, kind, n_samples);
+}
+
+hho_status hho_mlp_train(hho_ctx* ctx, int steps, int batch, double lr, uint64_t seed, double* h_loss) {
+    if (!ctx) return HHO_ERR_ARG;
+    return mlp_train(ctx, steps, batch, lr, seed, h_loss);
+}
+
+hho_status hho_mlp_grads(hho_ctx* ctx, const float* d_X, const float* d_T, int batch, double* h_loss, double* h_gW1,
+                         double* h_gb1, double* h_gW2, double* h_gb2) {
+    if (!ctx || !d_X || !d_T || !h_loss || !h_gW1 || !h_gb1 || !h_gW2 || !h_gb2) return HHO_ERR_ARG;
+    return mlp_grads(ctx, d_X, d_T, batch, h_loss, h_gW1, h_gb1, h_gW2, h_gb2);
+}
+
 hho_status hho_autotune(hho_ctx* ctx, int reps, double* h_choice) {
     if (!ctx || reps < 1 || reps > 1000) return HHO_ERR_ARG;
     if (!ctx->have_pmg) {
@@ -204,6 +247,18 @@ hho_status hho_set_option(hho_ctx* ctx, const char* key, double value) {
             return HHO_ERR_ARG;
         }
         ctx->use_graphs = value != 0.0;
+        return HHO_OK;
+    }
+    if (k == "learned_smoother") {
+        if (value != 0.0 && value != 1.0) {
+            ctx->err = "hho_set_option: learned_smoother must be 0 or 1";
+            return HHO_ERR_ARG;
+        }
+        if (value != 0.0 && !ctx->learned) {
+            ctx->err = "hho_set_option: learned_smoother needs hho_mlp_init (and training) first";
+            return HHO_ERR_STATE;
+        }
+        ctx->use_learned = value != 0.0 ? 1 : 0;
         return HHO_OK;
     }
     if (k == "coarse_fp32") {
@@ -339,6 +394,7 @@ hho_status hho_destroy(hho_ctx* ctx) {
     void* pt[] = {T.ff_col, T.ff_nsl, T.fp_col, T.pf_col, T.pf_nsl, T.asm_T, T.asm_lf, T.asm_lg};
     for (void* p : pt) dfree(p);
     batch_free(ctx);
+    mlp_free(ctx);
     dfree(ctx->rhs);
     dfree(ctx->null_vec0);
     dfree(ctx->null_w);

@@ -123,6 +123,7 @@ struct Topo {
 struct Workspace;     // solver work vectors (solve.cu)
 struct CoarseSolver;  // coarse-level solver (coarse.cu)
 struct BatchWork;     // segmented FGMRES state of a batch (batch.cu)
+struct Learned;       // learned block smoother (learned.cu)
 
 // Partition of the mesh into independent problems (a disjoint union): problem
 // p owns faces [face_off[p], face_off[p+1]) and elements [elem_off[p],
@@ -157,6 +158,10 @@ struct hho_ctx {
     int64_t* d_elem_off = nullptr;       // device copy of probs.elem_off
     hho::BatchWork* batch = nullptr;
     int tile_rows = 2048;                // rows of the condensed vector per block in the segmented kernels
+    hho::Learned* learned = nullptr;     // learned smoother network (or null)
+    int use_learned = 0;                 // apply it in the finest-level post-smoother
+    void* capture = nullptr;             // when set: the finest-level iterate after the coarse correction
+                                         // is copied here (direct V-cycles only)
     hho::Workspace* ws = nullptr;
     hho::CoarseSolver* coarse = nullptr;
     int64_t coarse_its_total = 0;
@@ -226,6 +231,20 @@ hho_status null_build(hho_ctx* ctx);
 // blocks nP (one block per problem)
 template <typename T>
 hho_status null_project(hho_ctx* ctx, int64_t nf_rows, int nP, T* x);
+// v = r / *den, z = M^{-1} v with the level-0 block-Jacobi preconditioner (FP64)
+hho_status jacobi_apply(hho_ctx* ctx, const double* r, const double* den, double* v, double* z);
+// learned.cu
+hho_status mlp_init(hho_ctx* ctx, int hidden, uint64_t seed);
+void mlp_free(hho_ctx* ctx);
+hho_status mlp_dims(hho_ctx* ctx, int* dims);
+hho_status mlp_weights(hho_ctx* ctx, int set, double* W1, double* b1, double* W2, double* b2);
+hho_status mlp_features(hho_ctx* ctx, const double* r, float* X, float* s);
+template <typename T>
+hho_status mlp_apply(hho_ctx* ctx, const T* v, T* z);
+hho_status mlp_generate(hho_ctx* ctx, int n_vec, uint64_t seed, int kind, int64_t* nsamp);
+hho_status mlp_train(hho_ctx* ctx, int steps, int batch, double lr, uint64_t seed, double* h_loss);
+hho_status mlp_grads(hho_ctx* ctx, const float* X, const float* T, int B, double* loss, double* gW1, double* gb1,
+                     double* gW2, double* gb2);
 // batch.cu
 hho_status batch_set(hho_ctx* ctx, int P, const int64_t* face_off, const int64_t* elem_off);
 hho_status batch_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, int32_t* its,

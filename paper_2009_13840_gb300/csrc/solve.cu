@@ -925,6 +925,12 @@ hho_status spmv(hho_ctx* ctx, int l, const double* x, double* y) {
     return HHO_OK;
 }
 
+hho_status jacobi_apply(hho_ctx* ctx, const double* r, const double* den, double* v, double* z) {
+    launch_jacobi<double>(ctx, ctx->levels[0], r, den, v, z, nullptr, 0, 0, nullptr);
+    HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
+}
+
 hho_status residual(hho_ctx* ctx, int l, const double* x, const double* b, double* r) {
     launch_spmv_dot<double>(ctx, l, x, b, r, 1, nullptr, 0, 0, 0, nullptr, HOOK_NONE, nullptr, gs_layout(1), 0);
     HHO_CUDA(cudaGetLastError());
@@ -965,7 +971,7 @@ static void dots(hho_ctx* ctx, int64_t n, const double* V, int64_t ld, int nv, d
 // m iterations of right-preconditioned GMRES on level l: x <- x + Z y (x = Z y when x_zero).
 // beta_ready: ||bv||^2 is already in sc[0] with the START hook run (by the restriction kernel).
 template <typename T>
-static hho_status smooth(hho_ctx* ctx, int l, const T* bv, T* x, bool x_zero, bool beta_ready) {
+static hho_status smooth(hho_ctx* ctx, int l, const T* bv, T* x, bool x_zero, bool beta_ready, bool post) {
     const LevelMat& L = ctx->levels[l];
     LevelWork& lw = ctx->ws->lv[l];
     const int m = ctx->smooth_its;
@@ -997,6 +1003,9 @@ static hho_status smooth(hho_ctx* ctx, int l, const T* bv, T* x, bool x_zero, bo
         T* zj = Z + (int64_t)j * n;
         // the second pass of step j-1 (w'' = w' - V t2) is applied inside the Jacobi kernel
         launch_jacobi<T>(ctx, L, j == 0 ? w0 : w, sc + 5, vj, zj, V, n, j, sc + G.t2);
+        // learned correction in the finest-level post-smoother, whose error the coarse correction has
+        // stripped of its low-frequency part (the distribution of the training pairs)
+        if (l == 0 && post && ctx->use_learned && ctx->learned) HHO_TRY(mlp_apply<T>(ctx, vj, zj));
         launch_spmv_dot<T>(ctx, l, zj, nullptr, w, 0, V, n, j + 1, 0, sc + G.t1, HOOK_NONE, sc, G, j);
         // w' = w - V t1, t2 = V^T w', ||w'||^2; Hessenberg column with ||w''||^2 = ||w'||^2 - ||t2||^2
         launch_update_dot<T>(ctx, n, w, V, n, j + 1, sc + G.t1, -1.0, V, j + 1, 1, sc + G.t2, HOOK_COLUMN_PY, sc, G,
@@ -1052,7 +1061,7 @@ static hho_status vcycle_level(hho_ctx* ctx, int l, const T* bv, T* x, bool x_ze
     LevelWork& cw = ctx->ws->lv[l + 1];
     T* cbv = static_cast<T*>(cw.bv);
     T* cx = static_cast<T*>(cw.x);
-    HHO_TRY(smooth<T>(ctx, l, bv, x, x_zero, beta_ready));
+    HHO_TRY(smooth<T>(ctx, l, bv, x, x_zero, beta_ready, false));
     const bool coarse_next = (l + 1 == Lc);
     const int Rc = op_rows(ctx, std::max(C.b, C.nP));
     Items it = items_for(F, Rc, C.b, C.nP);
@@ -1075,7 +1084,11 @@ static hho_status vcycle_level(hho_ctx* ctx, int l, const T* bv, T* x, bool x_ze
     k_prolong_add<T><<<grid1d(C.n, 256), 256, 0, ctx->stream>>>(F.nf, F.ne, F.b, F.nF, F.nP, C.b, C.nF, C.nP, cx, x);
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());
-    HHO_TRY(smooth<T>(ctx, l, bv, x, false, false));
+    // the iterate after the coarse correction, for the learned smoother's training pairs
+    if (l == 0 && ctx->capture) {
+        HHO_CUDA(cudaMemcpyAsync(ctx->capture, x, (size_t)F.n * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    HHO_TRY(smooth<T>(ctx, l, bv, x, false, false, true));
     return HHO_OK;
 }
 

@@ -27,7 +27,8 @@ NODES = {"elem": 0, "face": 1}
 SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "hho_assemble_noalloc", "pmg_setup", "pmg_vcycle", "hho_spmv", "hho_spmv_f32",
            "hho_solve", "hho_recover", "hho_errors", "hho_get_element_schur", "hho_get_level_coo",
            "hho_set_element_schur", "hho_launch_count", "hho_set_option", "hho_destroy",
-           "hho_last_error", "hho_set_batch", "hho_solve_batch", "hho_autotune"]
+           "hho_last_error", "hho_set_batch", "hho_solve_batch", "hho_autotune", "hho_mlp_init", "hho_mlp_dims",
+           "hho_mlp_weights", "hho_mlp_features", "hho_mlp_generate", "hho_mlp_train", "hho_mlp_grads"]
 
 
 class HHOError(RuntimeError):
@@ -87,6 +88,13 @@ def load(path: str = LIB_PATH):
         "hho_solve_batch": (C.c_int, [P, C.c_double, C.c_int, C.c_int, P, C.POINTER(C.c_int32),
                                       C.POINTER(C.c_double), C.POINTER(SolveInfo)]),
         "hho_autotune": (C.c_int, [P, C.c_int, C.POINTER(C.c_double)]),
+        "hho_mlp_init": (C.c_int, [P, C.c_int, C.c_uint64]),
+        "hho_mlp_dims": (C.c_int, [P, C.POINTER(C.c_int32)]),
+        "hho_mlp_weights": (C.c_int, [P, C.c_int] + [C.POINTER(C.c_double)] * 4),
+        "hho_mlp_features": (C.c_int, [P, P, P, P]),
+        "hho_mlp_generate": (C.c_int, [P, C.c_int, C.c_uint64, C.c_int, C.POINTER(C.c_int64)]),
+        "hho_mlp_train": (C.c_int, [P, C.c_int, C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double)]),
+        "hho_mlp_grads": (C.c_int, [P, P, P, C.c_int, C.POINTER(C.c_double)] + [C.POINTER(C.c_double)] * 4),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -237,6 +245,54 @@ class Context:
         out = (C.c_double * 3)()
         self._check(self.lib.hho_autotune(self.h, int(reps), out))
         return dict(spmv_rows=int(out[0]), spmv_grid=int(out[1]), tile_rows=int(out[2]))
+
+    # ---- learned smoother ----
+    def mlp_init(self, hidden=128, seed=0):
+        self._check(self.lib.hho_mlp_init(self.h, int(hidden), int(seed)))
+        return self.mlp_dims()
+
+    def mlp_dims(self):
+        d = (C.c_int32 * 4)()
+        self._check(self.lib.hho_mlp_dims(self.h, d))
+        return dict(din=d[0], hid=d[1], dout=d[2], raw=d[3])
+
+    def mlp_weights(self, new=None):
+        """Current FP32 master parameters (dict of numpy arrays), or set them from `new`."""
+        d = self.mlp_dims()
+        shapes = dict(W1=(d["din"], d["hid"]), b1=(d["hid"],), W2=(d["hid"], d["dout"]), b2=(d["dout"],))
+        arrs = {k: np.zeros(v) if new is None else np.ascontiguousarray(new[k], dtype=np.float64).reshape(v)
+                for k, v in shapes.items()}
+        ptrs = [arrs[k].ctypes.data_as(C.POINTER(C.c_double)) for k in ("W1", "b1", "W2", "b2")]
+        self._check(self.lib.hho_mlp_weights(self.h, 0 if new is None else 1, *ptrs))
+        return arrs
+
+    def mlp_features(self, r):
+        d = self.mlp_dims()
+        nf = self.mesh.n_face
+        X = self._torch.empty((nf, d["din"]), dtype=self._torch.float32, device="cuda")
+        s = self._torch.empty(nf, dtype=self._torch.float32, device="cuda")
+        self._check(self.lib.hho_mlp_features(self.h, _ptr(r), _ptr(X), _ptr(s)))
+        return X, s
+
+    def mlp_generate(self, n_vec, seed=0, kind=2):
+        n = C.c_int64()
+        self._check(self.lib.hho_mlp_generate(self.h, int(n_vec), int(seed), int(kind), C.byref(n)))
+        return n.value
+
+    def mlp_train(self, steps, batch=4096, lr=1e-3, seed=0):
+        loss = np.zeros(steps)
+        self._check(self.lib.hho_mlp_train(self.h, int(steps), int(batch), float(lr), int(seed),
+                                           loss.ctypes.data_as(C.POINTER(C.c_double))))
+        return loss
+
+    def mlp_grads(self, X, T):
+        d = self.mlp_dims()
+        g = dict(W1=np.zeros((d["din"], d["hid"])), b1=np.zeros(d["hid"]), W2=np.zeros((d["hid"], d["dout"])),
+                 b2=np.zeros(d["dout"]))
+        loss = C.c_double()
+        ptrs = [g[k].ctypes.data_as(C.POINTER(C.c_double)) for k in ("W1", "b1", "W2", "b2")]
+        self._check(self.lib.hho_mlp_grads(self.h, _ptr(X), _ptr(T), int(X.shape[0]), C.byref(loss), *ptrs))
+        return loss.value, g
 
     def recover(self, x):
         n_loc = self.local_size()
