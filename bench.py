@@ -35,9 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "FGMRES+p-MG time & DOFs/s to 1e-8 rel. residual; V-cycle GB/s vs HBM peak"
 UNIT = "DOF/s"
 # DRAM bytes (read + write) of one FP32 level-0 operator launch on the default
-# workload, from the ncu capture summarised in
-# profiles/k_spmv_b_level0_tri128_k3_vcond.md (kernel unchanged since)
-SPMV_F32_TRAFFIC = {("tri", 128, 3, "v"): 144320512 + 3594240}
+# workload, from an ncu capture of the current kernel (empty until one exists)
+SPMV_F32_TRAFFIC = {}
 
 
 def parse():
@@ -294,7 +293,7 @@ def run_ours(args):
             xs32, ys32 = xs.float(), torch.empty(ndof, dtype=torch.float32, device="cuda")
             ms_k = time_kernel(lambda: ctx.spmv_f32(0, xs32, ys32))
             nbytes = spmv_bytes(ctx, 0, 4)
-            kname = "k_spmv_b<float> (level 0, V-cycle operator, FP32)"
+            kname = "k_spmv_v<float> (level 0, V-cycle operator, FP32, row-interleaved)"
         else:
             ms_k, nbytes, kname = ms64_k, nb64, "k_spmv_b<double> (level 0)"
         achieved = nbytes / (ms_k / 1e3) / 1e9

@@ -374,6 +374,7 @@ void free_level(LevelMat& L) {
     dfree(L.dinv32);
     dfree(L.minv32);
     L.ff32 = L.fp32 = L.pf32 = L.pp32 = L.dinv32 = L.minv32 = nullptr;
+    L.ilv = false;
 }
 
 hho_status assemble_level0(hho_ctx* ctx) {

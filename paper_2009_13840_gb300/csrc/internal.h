@@ -106,8 +106,12 @@ struct LevelMat {
     // smoother data
     double* dinv = nullptr; // [b c][b r][nf]
     double* minv = nullptr; // [nP c][nP r][ne]
-    // FP32 copies used by a mixed-precision V-cycle (same layouts)
+    // FP32 copies used by a mixed-precision V-cycle: the layouts above, or with
+    // ilv set the row-interleaved layouts (rows of one face / element block
+    // contiguous for each column: ff[s][c][F][r], fp[p][c][F][r], pf[f][c][T][r],
+    // pp[c][T][r], dinv[c][F][r], minv[c][T][r]) read by the one-thread-per-block kernels
     float *ff32 = nullptr, *fp32 = nullptr, *pf32 = nullptr, *pp32 = nullptr, *dinv32 = nullptr, *minv32 = nullptr;
+    bool ilv = false;
 };
 
 struct Topo {

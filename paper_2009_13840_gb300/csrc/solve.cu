@@ -41,6 +41,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 
 #include "internal.h"
 #include "krylov.cuh"
@@ -568,6 +569,219 @@ __global__ void __launch_bounds__(RT) k_jacobi_b(LV<T> L, Items it, const T* __r
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 kernels on the row-interleaved layouts (LevelMat::ilv): one thread owns
+// a whole face block (B rows) or element block (NP rows); for every column the
+// block's rows are contiguous, so a thread reads them with 16- or 8-byte
+// loads and a warp reads one contiguous span per column.  NP is the pressure
+// block size the degree behind B gives under velocity-only condensation, or 1.
+// ---------------------------------------------------------------------------
+constexpr int np_full(int B) {
+    return B == 2 ? 1 : B == 4 ? 3 : B == 6 ? 6 : B == 8 ? 10 : B == 10 ? 15 : B == 12 ? 21 : B == 3 ? 1 : B == 9 ? 4
+         : B == 18 ? 10 : B == 30 ? 20 : 0;
+}
+
+// v[0..N) = p[0..N), 16-byte loads when N % 4 == 0, 8-byte when N is even
+// (operator values only: every run starts at a multiple of N floats of a
+// separately allocated array, so it is aligned for the chosen width)
+template <int N>
+__device__ __forceinline__ void load_run(const float* __restrict__ p, float (&v)[N]) {
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(p) + i);
+            v[4 * i] = t.x;
+            v[4 * i + 1] = t.y;
+            v[4 * i + 2] = t.z;
+            v[4 * i + 3] = t.w;
+        }
+    } else if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const float2 t = __ldg(reinterpret_cast<const float2*>(p) + i);
+            v[2 * i] = t.x;
+            v[2 * i + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = __ldg(p + i);
+    }
+}
+
+// v[0..N) = p[0..N) with scalar loads: vectors of the smoother (the Arnoldi
+// and preconditioned vectors sit at offsets j n that need not be 16-byte
+// aligned), read through L1
+template <int N>
+__device__ __forceinline__ void load_run_plain(const float* __restrict__ p, float (&v)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = p[i];
+}
+
+// acc[r] += sum_c A_c[r] xv[c] for a block of R rows and C columns; column c's
+// R rows start at a + c * cs
+template <int R, int C>
+__device__ __forceinline__ void block_mv(const float* __restrict__ a, int64_t cs, const float (&xv)[C],
+                                         float (&acc)[R]) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        float col[R];
+        load_run<R>(a + (int64_t)c * cs, col);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += col[r] * xv[c];
+    }
+}
+
+// The level operator on the interleaved FP32 layout, with the modes, dots and
+// hooks of k_spmv_b (mode 0: y = S x, 1: y = bv - S x, 2: restriction).
+template <int B, int NP, int RF>
+__global__ void __launch_bounds__(RT, 4) k_spmv_v(LV<float> L, Items it, const float* __restrict__ x,
+                                                const float* __restrict__ bv, float* __restrict__ y, int mode,
+                                                const float* __restrict__ V, int64_t ld, int nv, int self,
+                                                double* __restrict__ partial, unsigned* __restrict__ counter,
+                                                double* __restrict__ out, int hook, double* sc, GS gsl, int j,
+                                                Restr rs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nf = L.nf, ne = L.ne;
+    float dacc[NVMAX + 1];
+#pragma unroll
+    for (int v = 0; v <= NVMAX; ++v) dacc[v] = 0.f;
+    const int64_t nfi = it.ftiles * it.fgroups;
+    for (int64_t w = warp; w < it.total(); w += nwarps) {
+        if (w < nfi) {
+            const int64_t F = (w / it.fgroups) * 32 + lane;
+            const int r0 = (int)(w % it.fgroups) * RF;
+            if (F >= nf) continue;
+            float acc[RF];
+#pragma unroll
+            for (int r = 0; r < RF; ++r) acc[r] = 0.f;
+            const int ns = L.ff_nsl[F];
+            for (int s = 0; s < ns; ++s) {
+                float xv[B];
+                load_run_plain<B>(x + (int64_t)L.ff_col[s * nf + F] * B, xv);
+                block_mv<RF, B>(L.ff + ((int64_t)s * B * nf + F) * B + r0, nf * B, xv, acc);
+            }
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const int T = L.fp_col[p * nf + F];
+                if (T < 0) continue;
+                float xp[NP];
+                load_run_plain<NP>(x + nf * B + (int64_t)T * NP, xp);
+                block_mv<RF, NP>(L.fp + ((int64_t)p * NP * nf + F) * B + r0, nf * B, xp, acc);
+            }
+#pragma unroll
+            for (int i = 0; i < RF; ++i) {
+                const int r = r0 + i;
+                const int64_t o = F * B + r;
+                const float v = mode ? bv[o] - acc[i] : acc[i];
+                if (mode == 2) {
+                    const int comp = r / rs.nFf, rr = r - comp * rs.nFf;
+                    if (rr < rs.nFc) {
+                        y[F * rs.bc + comp * rs.nFc + rr] = v;
+                        if (self) dacc[NVMAX] += v * v;
+                    }
+                } else {
+                    y[o] = v;
+                    accumulate_dots(dacc, V, ld, o, nv, self, v);
+                }
+            }
+        } else {
+            const int64_t E = (w - nfi) * 32 + lane;  // one thread per element block (egroups = 1)
+            if (E >= ne) continue;
+            float acc[NP];
+#pragma unroll
+            for (int r = 0; r < NP; ++r) acc[r] = 0.f;
+            const int N = L.pf_nsl[E];
+            for (int f = 0; f < N; ++f) {
+                float xv[B];
+                load_run_plain<B>(x + (int64_t)L.pf_col[f * ne + E] * B, xv);
+                block_mv<NP, B>(L.pf + ((int64_t)f * B * ne + E) * NP, ne * NP, xv, acc);
+            }
+            {
+                float xp[NP];
+                load_run_plain<NP>(x + nf * B + E * NP, xp);
+                block_mv<NP, NP>(L.pp + E * NP, ne * NP, xp, acc);
+            }
+#pragma unroll
+            for (int r = 0; r < NP; ++r) {
+                const int64_t o = nf * B + E * NP + r;
+                const float v = mode ? bv[o] - acc[r] : acc[r];
+                if (mode == 2) {
+                    if (r < rs.nPc) {
+                        y[nf * rs.bc + E * rs.nPc + r] = v;
+                        if (self) dacc[NVMAX] += v * v;
+                    }
+                } else {
+                    y[o] = v;
+                    accumulate_dots(dacc, V, ld, o, nv, self, v);
+                }
+            }
+        }
+    }
+    if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
+}
+
+// Block Jacobi on the interleaved FP32 layout, with the pending second
+// Gram-Schmidt pass of k_jacobi_b.
+template <int B, int NP>
+__global__ void __launch_bounds__(RT) k_jacobi_v(LV<float> L, Items it, const float* __restrict__ w,
+                                                  const double* __restrict__ den, float* __restrict__ v,
+                                                  float* __restrict__ z, const float* __restrict__ Vp, int64_t ld,
+                                                  int npend, const double* __restrict__ pc) {
+    const float inv = block_inverse<float>(den);
+    const float* s_pc = stage_pending<float>(pc, npend);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nf = L.nf, ne = L.ne;
+    for (int64_t wi = warp; wi < it.total(); wi += nwarps) {
+        if (wi < it.ftiles) {
+            const int64_t F = wi * 32 + lane;
+            if (F >= nf) continue;
+            float u[B], acc[B];
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+                u[c] = pending(w, Vp, ld, npend, s_pc, F * B + c);
+                acc[c] = 0.f;
+            }
+            block_mv<B, B>(L.dinv + F * B, nf * B, u, acc);
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                z[F * B + r] = acc[r] * inv;
+                v[F * B + r] = u[r] * inv;
+            }
+        } else {
+            const int64_t E = (wi - it.ftiles) * 32 + lane;
+            if (E >= ne) continue;
+            const int64_t ob = nf * B + E * NP;
+            float u[NP], acc[NP];
+#pragma unroll
+            for (int c = 0; c < NP; ++c) {
+                u[c] = pending(w, Vp, ld, npend, s_pc, ob + c);
+                acc[c] = 0.f;
+            }
+            block_mv<NP, NP>(L.minv + E * NP, ne * NP, u, acc);
+#pragma unroll
+            for (int r = 0; r < NP; ++r) {
+                z[ob + r] = acc[r] * inv;
+                v[ob + r] = u[r] * inv;
+            }
+        }
+    }
+}
+
+// dst[(p N + i) R + r] = src[(p R + r) N + i]: FP32 row-interleaved copy of a
+// [planes][R][N] FP64 array
+__global__ void k_interleave(int64_t planes, int R, int64_t N, const double* __restrict__ src,
+                             float* __restrict__ dst) {
+    const int64_t tot = planes * R * N;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < tot; o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = o % R, i = (o / R) % N, p = o / ((int64_t)R * N);
+        dst[o] = (float)src[(p * R + r) * N + i];
+    }
+}
+
 // v = w / den (FGMRES basis vector)
 __global__ void k_scale(int64_t n, const double* __restrict__ w, const double* __restrict__ den, double* __restrict__ v) {
     const double inv = block_inverse<double>(den);
@@ -837,6 +1051,12 @@ static void launch_jacobi_b_B(hho_ctx* ctx, const LevelMat& L, const T* w, const
 template <typename T>
 static void launch_jacobi(hho_ctx* ctx, const LevelMat& L, const T* w, const double* den, T* v, T* z, const T* Vp,
                           int64_t ld, int npend, const double* pc) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (L.ilv && launch_jacobi_v(ctx, L, w, den, v, z, Vp, ld, npend, pc)) {
+            ++ctx->launches;
+            return;
+        }
+    }
     switch (L.b) {
         case 2: launch_jacobi_b_B<2, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
         case 3: launch_jacobi_b_B<3, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
@@ -855,10 +1075,91 @@ static void launch_jacobi(hho_ctx* ctx, const LevelMat& L, const T* w, const dou
     ++ctx->launches;
 }
 
+// ---- interleaved FP32 kernels (LevelMat::ilv) ----
+static bool ilv_supported(int b, int nP) { return np_full(b) > 0 && (nP == 1 || nP == np_full(b)); }
+
+static Items items_v(const LevelMat& L) {
+    Items it;
+    it.ftiles = (L.nf + 31) / 32;
+    it.etiles = (L.ne + 31) / 32;
+    it.fgroups = 1;
+    it.egroups = 1;
+    return it;
+}
+
+// rows of a face block per thread in k_spmv_v: blocks of 8 or more unknowns are
+// split in two, so that a face's rows keep 8- or 16-byte alignment
+constexpr int rf_v(int B) { return B >= 8 ? B / 2 : B; }
+
+template <int B, int NP>
+static void launch_spmv_v_BN(hho_ctx* ctx, const LevelMat& L, const float* x, const float* bv, float* y, int mode,
+                             const float* V, int64_t ld, int nv, int self, double* partial, unsigned* counter,
+                             double* out, int hook, double* sc, GS gsl, int j, Restr rs) {
+    constexpr int RF = rf_v(B);
+    Items it = items_v(L);
+    it.fgroups = B / RF;
+    const int g = op_grid(ctx, it);
+    k_spmv_v<B, NP, RF><<<g, RT, 0, ctx->stream>>>(view<float>(L), it, x, bv, y, mode, V, ld, nv, self, partial,
+                                                   counter, out, hook, sc, gsl, j, rs);
+}
+
+template <int B, int NP>
+static void launch_jacobi_v_BN(hho_ctx* ctx, const LevelMat& L, const float* w, const double* den, float* v,
+                               float* z, const float* Vp, int64_t ld, int npend, const double* pc) {
+    const Items it = items_v(L);
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>((it.total() + RT / 32 - 1) / (RT / 32), GMAX));
+    k_jacobi_v<B, NP><<<(int)g, RT, 0, ctx->stream>>>(view<float>(L), it, w, den, v, z, Vp, ld, npend, pc);
+}
+
+#define HHO_BN_SWITCH(CALL)                                                                                        \
+    switch (L.b * 64 + L.nP) {                                                                                     \
+        case 2 * 64 + 1: CALL(2, 1); break;                                                                        \
+        case 4 * 64 + 3: CALL(4, 3); break;                                                                        \
+        case 4 * 64 + 1: CALL(4, 1); break;                                                                        \
+        case 6 * 64 + 6: CALL(6, 6); break;                                                                        \
+        case 6 * 64 + 1: CALL(6, 1); break;                                                                        \
+        case 8 * 64 + 10: CALL(8, 10); break;                                                                      \
+        case 8 * 64 + 1: CALL(8, 1); break;                                                                        \
+        case 10 * 64 + 15: CALL(10, 15); break;                                                                    \
+        case 10 * 64 + 1: CALL(10, 1); break;                                                                      \
+        case 12 * 64 + 21: CALL(12, 21); break;                                                                    \
+        case 12 * 64 + 1: CALL(12, 1); break;                                                                      \
+        case 3 * 64 + 1: CALL(3, 1); break;                                                                        \
+        case 9 * 64 + 4: CALL(9, 4); break;                                                                        \
+        case 9 * 64 + 1: CALL(9, 1); break;                                                                        \
+        case 18 * 64 + 10: CALL(18, 10); break;                                                                    \
+        case 18 * 64 + 1: CALL(18, 1); break;                                                                      \
+        case 30 * 64 + 20: CALL(30, 20); break;                                                                    \
+        case 30 * 64 + 1: CALL(30, 1); break;                                                                      \
+        default: return false;                                                                                     \
+    }
+
+static bool launch_spmv_v(hho_ctx* ctx, const LevelMat& L, const float* x, const float* bv, float* y, int mode,
+                          const float* V, int64_t ld, int nv, int self, double* partial, unsigned* counter,
+                          double* out, int hook, double* sc, GS gsl, int j, Restr rs) {
+#define HHO_SPMV_V(BB, NN) \
+    launch_spmv_v_BN<BB, NN>(ctx, L, x, bv, y, mode, V, ld, nv, self, partial, counter, out, hook, sc, gsl, j, rs)
+    HHO_BN_SWITCH(HHO_SPMV_V)
+#undef HHO_SPMV_V
+    return true;
+}
+
+static bool launch_jacobi_v(hho_ctx* ctx, const LevelMat& L, const float* w, const double* den, float* v, float* z,
+                            const float* Vp, int64_t ld, int npend, const double* pc) {
+#define HHO_JAC_V(BB, NN) launch_jacobi_v_BN<BB, NN>(ctx, L, w, den, v, z, Vp, ld, npend, pc)
+    HHO_BN_SWITCH(HHO_JAC_V)
+#undef HHO_JAC_V
+    return true;
+}
+
 template <typename T>
 static bool launch_spmv_b(hho_ctx* ctx, const LevelMat& L, const T* x, const T* bv, T* y, int mode, const T* V,
                           int64_t ld, int nv, int self, double* partial, unsigned* counter, double* out, int hook,
                           double* sc, GS gsl, int j, Restr rs = Restr{0, 0, 0, 0}) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (L.ilv) return launch_spmv_v(ctx, L, x, bv, y, mode, V, ld, nv, self, partial, counter, out, hook, sc, gsl,
+                                        j, rs);
+    }
     if (ctx->spmv_rows > 0) return false;  // explicit row grouping requested: generic kernel
 #define HHO_B_CASE(BB)                                                                                             \
     case BB:                                                                                                       \
@@ -1203,6 +1504,16 @@ static hho_status make_fp32_copy(hho_ctx* ctx, const double* src, float** dst, s
     return HHO_OK;
 }
 
+static hho_status make_fp32_interleaved(hho_ctx* ctx, const double* src, float** dst, int64_t planes, int R,
+                                        int64_t N) {
+    dfree(*dst);
+    *dst = nullptr;
+    HHO_TRY(dalloc(ctx, dst, (size_t)planes * R * N));
+    k_interleave<<<grid1d(planes * R * N, 256), 256, 0, ctx->stream>>>(planes, R, N, src, *dst);
+    HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
+}
+
 hho_status pmg_build(hho_ctx* ctx) {
     free_workspace(ctx);
     Workspace* W = new Workspace();
@@ -1225,12 +1536,22 @@ hho_status pmg_build(hho_ctx* ctx) {
         HHO_TRY(dalloc(ctx, &w.sc, G.total));
         HHO_CUDA(cudaMemset(w.sc, 0, G.total * sizeof(double)));
         if (mixed && l < nl - 1) {
-            HHO_TRY(make_fp32_copy(ctx, L.ff, &L.ff32, (size_t)L.S_max * L.b * L.b * L.nf));
-            HHO_TRY(make_fp32_copy(ctx, L.fp, &L.fp32, (size_t)2 * L.nP * L.b * L.nf));
-            HHO_TRY(make_fp32_copy(ctx, L.pf, &L.pf32, (size_t)L.N_max * L.b * L.nP * L.ne));
-            HHO_TRY(make_fp32_copy(ctx, L.pp, &L.pp32, (size_t)L.nP * L.nP * L.ne));
-            HHO_TRY(make_fp32_copy(ctx, L.dinv, &L.dinv32, (size_t)L.b * L.b * L.nf));
-            HHO_TRY(make_fp32_copy(ctx, L.minv, &L.minv32, (size_t)L.nP * L.nP * L.ne));
+            L.ilv = ilv_supported(L.b, L.nP);
+            if (L.ilv) {
+                HHO_TRY(make_fp32_interleaved(ctx, L.ff, &L.ff32, (int64_t)L.S_max * L.b, L.b, L.nf));
+                HHO_TRY(make_fp32_interleaved(ctx, L.fp, &L.fp32, (int64_t)2 * L.nP, L.b, L.nf));
+                HHO_TRY(make_fp32_interleaved(ctx, L.pf, &L.pf32, (int64_t)L.N_max * L.b, L.nP, L.ne));
+                HHO_TRY(make_fp32_interleaved(ctx, L.pp, &L.pp32, L.nP, L.nP, L.ne));
+                HHO_TRY(make_fp32_interleaved(ctx, L.dinv, &L.dinv32, L.b, L.b, L.nf));
+                HHO_TRY(make_fp32_interleaved(ctx, L.minv, &L.minv32, L.nP, L.nP, L.ne));
+            } else {
+                HHO_TRY(make_fp32_copy(ctx, L.ff, &L.ff32, (size_t)L.S_max * L.b * L.b * L.nf));
+                HHO_TRY(make_fp32_copy(ctx, L.fp, &L.fp32, (size_t)2 * L.nP * L.b * L.nf));
+                HHO_TRY(make_fp32_copy(ctx, L.pf, &L.pf32, (size_t)L.N_max * L.b * L.nP * L.ne));
+                HHO_TRY(make_fp32_copy(ctx, L.pp, &L.pp32, (size_t)L.nP * L.nP * L.ne));
+                HHO_TRY(make_fp32_copy(ctx, L.dinv, &L.dinv32, (size_t)L.b * L.b * L.nf));
+                HHO_TRY(make_fp32_copy(ctx, L.minv, &L.minv32, (size_t)L.nP * L.nP * L.ne));
+            }
         }
         if (mixed && l == nl - 1 && nl > 1) {
             HHO_TRY(dalloc(ctx, &w.cd, n));
