@@ -35,8 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "FGMRES+p-MG time & DOFs/s to 1e-8 rel. residual; V-cycle GB/s vs HBM peak"
 UNIT = "DOF/s"
 # DRAM bytes (read + write) of one FP32 level-0 operator launch on the default
-# workload, from an ncu capture of the current kernel (empty until one exists)
-SPMV_F32_TRAFFIC = {}
+# workload, from the ncu capture summarised in
+# profiles/k_spmv_level0_tri128_k3_vcond.md (kernel unchanged since)
+SPMV_F32_TRAFFIC = {("tri", 128, 3, "v"): 144289024 + 3541248}
 
 
 def parse():
