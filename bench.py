@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--mesh", default="tri", choices=["tri", "hex"],
+                    help="tri: n x n squares split into triangles (2D); hex: n^3 jittered hexahedra (3D)")
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--cond", default="v", choices=["v", "vp"])
     ap.add_argument("--rtol", type=float, default=1e-8)
@@ -69,8 +71,14 @@ def parse():
     return ap.parse_args()
 
 
-def workload(n, k, cond):
-    from synthetic import tri_mesh, fields
+MESH = "tri"
+
+
+def workload(n, k, cond, mesh_kind=None):
+    from synthetic import tri_mesh, hex_mesh, fields
+    if (mesh_kind or MESH) == "hex":
+        mesh = hex_mesh(n, jitter=0.15, seed=0)
+        return mesh, fields.CurlStokes3D(), f"hex{n}^3-jit0.15-seed0-allDirichlet k={k} {cond}-cond levels {k}..0"
     mesh = tri_mesh(n, jitter=0.2, seed=0, neumann_sides=(1,))
     return mesh, fields.TrigStokes2D(), f"tri{n}x{n}-jit0.2-seed0-mixedBC k={k} {cond}-cond levels {k}..0"
 
@@ -136,9 +144,12 @@ class Clocks:
 
 
 def oracle_sample(n_s, k, cond, rtol):
-    """The oracle as it stands on a bounded sample: returns (DOF/s, ndof, its, seconds)."""
+    """The oracle as it stands on a bounded sample: returns (DOF/s, ndof, its, seconds).
+    3D samples are capped at 5^3 hexahedra (a bounded CPU run)."""
     from oracle.hho import HHO
     from oracle.pmg import PMG, fgmres
+    if MESH == "hex":
+        n_s = min(n_s, 5)
     mesh, fld, _ = workload(n_s, k, cond)
     h = HHO(mesh, k, cond)
     rhs = h.assemble_rhs(*h.data_values(fld))
@@ -325,7 +336,7 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, nd, its, dt = oracle_sample(args.sample_n, args.k, args.cond, args.rtol)
         cpu = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"oracle FGMRES+p-MG solve on tri{args.sample_n}x{args.sample_n} of the same family "
+               "sample": f"oracle FGMRES+p-MG solve on {args.mesh}{args.sample_n if args.mesh == 'tri' else min(args.sample_n, 5)} of the same family "
                          f"({nd} DOFs, {its} its, {dt:.2f} s); setup excluded"}
     if rank == 0:
         last = infos[-1]
@@ -343,7 +354,7 @@ def run_ours(args):
                        "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": (SPMV_F32_TRAFFIC.get(("tri", args.n, args.k, args.cond))
+                         "traffic": (SPMV_F32_TRAFFIC.get((args.mesh, args.n, args.k, args.cond))
                                      if args.prec == "fp32" else None),
                          "bytes_per_launch": nbytes, "ms_per_launch": ms_k,
                          "fp64_outer_spmv": {"achieved": nb64 / (ms64_k / 1e3) / 1e9, "bytes_per_launch": nb64,
@@ -617,7 +628,9 @@ def run_learned(args):
 
 
 def main():
+    global MESH
     args = parse()
+    MESH = args.mesh
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

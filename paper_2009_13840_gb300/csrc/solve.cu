@@ -1087,9 +1087,15 @@ static Items items_v(const LevelMat& L) {
     return it;
 }
 
-// rows of a face block per thread in k_spmv_v: blocks of 8 or more unknowns are
-// split in two, so that a face's rows keep 8- or 16-byte alignment
-constexpr int rf_v(int B) { return B >= 8 ? B / 2 : B; }
+// rows of a face block per thread in k_spmv_v: even blocks of 8 or more
+// unknowns are split in two halves, others are kept whole.  The half must
+// divide B, and a vector load of it must stay aligned: load_run uses 16-byte
+// loads only when RF % 4 == 0 (then B % 8 == 0, so every half starts at a
+// multiple of 4 floats) and 8-byte loads only when RF is even (B even, every
+// run starts at an even float); odd RF (B = 10, 18, 30 halves; B = 3, 9 whole)
+// uses scalar loads.
+constexpr int rf_v(int B) { return (B >= 8 && B % 2 == 0) ? B / 2 : B; }
+static_assert(rf_v(9) == 9 && rf_v(8) == 4 && rf_v(12) == 6 && rf_v(18) == 9 && rf_v(30) == 15, "row split");
 
 template <int B, int NP>
 static void launch_spmv_v_BN(hho_ctx* ctx, const LevelMat& L, const float* x, const float* bv, float* y, int mode,
