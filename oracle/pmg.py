@@ -199,7 +199,7 @@ class PMG:
     """Hierarchy of Galerkin-inherited levels and the V-cycle (Sec. 3.3)."""
 
     def __init__(self, hho, degrees, smooth_its=2, coarse="auto", coarse_rtol=1e-3,
-                 lu_max=10000):
+                 lu_max=10000, smoother="jacobi"):
         assert degrees[0] == hho.k and all(a > b for a, b in zip(degrees, degrees[1:]))
         self.hho = hho
         self.degrees = list(degrees)
@@ -214,6 +214,11 @@ class PMG:
                 self.R.append(R)
                 S = (R @ S @ R.T).tocsr()
             self.levels.append(Level(S, mesh, d, kl, cond, None))
+        if smoother == "ilu":  # block ILU(0), multicolour faces then pressures (oracle/ilu.py)
+            from .ilu import BlockILU
+            for lev in self.levels[:-1]:
+                lev.ilu = BlockILU(lev.S, mesh, lev.b, lev.nP)
+                lev.precond = lev.ilu.apply
         L = self.levels[-1]
         self.coarse_rtol = coarse_rtol
         if coarse == "auto":
