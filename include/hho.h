@@ -151,8 +151,8 @@ hho_status hho_assemble_noalloc(hho_ctx* ctx, const double* d_f, const double* d
  * smoothing (the paper uses 2). */
 hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, int smooth_its);
 
-/* Solver options.  "coarse_dense_max", "dd_elements" and "coarse_fp32" take
- * effect at the next pmg_setup.  Keys:
+/* Solver options.  "coarse_dense_max", "dd_elements", "coarse_fp32" and
+ * "smoother" take effect at the next pmg_setup.  Keys:
  *   "coarse_dense_max"  largest coarse level solved by the dense inverse
  *                       (default 10000 unknowns); larger coarse levels use
  *                       the substructured direct solver
@@ -171,6 +171,12 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
  *                       element per thread
  *   "spmv_grid"         blocks of 256 threads of the operator kernels,
  *                       1..8192 (0 = automatic: about one 32-row tile per warp)
+ *   "smoother"          0 (default): block-Jacobi preconditioner in the
+ *                       smoother's GMRES; 1: block ILU(0) (faces in greedy
+ *                       multicolour order, element pressures last; factored
+ *                       at pmg_setup on every level above the coarse one,
+ *                       face blocks of at most 18 and pressure blocks of at
+ *                       most 32 unknowns).  Takes effect at the next pmg_setup.
  *   "learned_smoother"  1: add the learned correction (hho_mlp_*) to the
  *                       block-Jacobi output in the finest-level post-smoother;
  *                       0 (default): plain smoother.  HHO_ERR_STATE without
@@ -278,6 +284,11 @@ hho_status hho_mlp_train(hho_ctx* ctx, int steps, int batch, double lr, uint64_t
  * host outputs as in hho_mlp_weights. */
 hho_status hho_mlp_grads(hho_ctx* ctx, const float* d_X, const float* d_T, int batch, double* h_loss, double* h_gW1,
                          double* h_gb1, double* h_gW2, double* h_gb2);
+
+/* Block ILU(0) smoother preconditioner of level `level` (option "smoother" = 1
+ * before pmg_setup): d_z = (L U)^{-1} d_v (device, ndof(level) doubles, FP64
+ * factors).  HHO_ERR_STATE if the level has no factors. */
+hho_status hho_ilu_apply(hho_ctx* ctx, int level, const double* d_v, double* d_z);
 
 /* Autotuner (after pmg_setup): times `reps` V-cycles for every candidate of
  * "spmv_rows" (0, 2, 4) x "spmv_grid" (automatic, 1216, 2432) and, for a

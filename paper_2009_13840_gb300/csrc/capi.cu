@@ -165,6 +165,23 @@ hho_status hho_mlp_grads(hho_ctx* ctx, const float* d_X, const float* d_T, int b
     return mlp_grads(ctx, d_X, d_T, batch, h_loss, h_gW1, h_gb1, h_gW2, h_gb2);
 }
 
+hho_status hho_ilu_apply(hho_ctx* ctx, int level, const double* d_v, double* d_z) {
+    if (!ctx || !d_v || !d_z || d_v == d_z) return HHO_ERR_ARG;
+    if (!ctx->have_pmg || level < 0 || level >= (int)ctx->ilu.size() || !ctx->ilu[level]) {
+        ctx->err = "hho_ilu_apply: no ILU factors on this level (option smoother = 1, then pmg_setup)";
+        return HHO_ERR_STATE;
+    }
+    const LevelMat& L = ctx->levels[level];
+    double* tmp = nullptr;
+    HHO_TRY(dalloc(ctx, &tmp, (size_t)std::max<int64_t>(L.ne * L.nP, 1)));
+    hho_status st = ilu_apply<double>(ctx, level, d_v, d_z, tmp);
+    cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    dfree(tmp);
+    HHO_TRY(st);
+    HHO_CUDA(se);
+    return HHO_OK;
+}
+
 hho_status hho_autotune(hho_ctx* ctx, int reps, double* h_choice) {
     if (!ctx || reps < 1 || reps > 1000) return HHO_ERR_ARG;
     if (!ctx->have_pmg) {
@@ -247,6 +264,14 @@ hho_status hho_set_option(hho_ctx* ctx, const char* key, double value) {
             return HHO_ERR_ARG;
         }
         ctx->use_graphs = value != 0.0;
+        return HHO_OK;
+    }
+    if (k == "smoother") {
+        if (value != 0.0 && value != 1.0) {
+            ctx->err = "hho_set_option: smoother must be 0 (block Jacobi) or 1 (block ILU(0))";
+            return HHO_ERR_ARG;
+        }
+        ctx->smoother_kind = (int)value;
         return HHO_OK;
     }
     if (k == "learned_smoother") {
@@ -395,6 +420,7 @@ hho_status hho_destroy(hho_ctx* ctx) {
     for (void* p : pt) dfree(p);
     batch_free(ctx);
     mlp_free(ctx);
+    ilu_free(ctx);
     dfree(ctx->rhs);
     dfree(ctx->null_vec0);
     dfree(ctx->null_w);

@@ -128,6 +128,7 @@ struct Workspace;     // solver work vectors (solve.cu)
 struct CoarseSolver;  // coarse-level solver (coarse.cu)
 struct BatchWork;     // segmented FGMRES state of a batch (batch.cu)
 struct Learned;       // learned block smoother (learned.cu)
+struct IluLevel;      // block ILU(0) factors of one level (ilu.cu)
 
 // Partition of the mesh into independent problems (a disjoint union): problem
 // p owns faces [face_off[p], face_off[p+1]) and elements [elem_off[p],
@@ -163,6 +164,8 @@ struct hho_ctx {
     hho::BatchWork* batch = nullptr;
     int tile_rows = 2048;                // rows of the condensed vector per block in the segmented kernels
     hho::Learned* learned = nullptr;     // learned smoother network (or null)
+    int smoother_kind = 0;               // 0 block Jacobi, 1 block ILU(0) (from the next pmg_setup)
+    std::vector<hho::IluLevel*> ilu;     // ILU factors per level (smoother_kind 1)
     int use_learned = 0;                 // apply it in the finest-level post-smoother
     void* capture = nullptr;             // when set: the finest-level iterate after the coarse correction
                                          // is copied here (direct V-cycles only)
@@ -249,6 +252,11 @@ hho_status mlp_generate(hho_ctx* ctx, int n_vec, uint64_t seed, int kind, int64_
 hho_status mlp_train(hho_ctx* ctx, int steps, int batch, double lr, uint64_t seed, double* h_loss);
 hho_status mlp_grads(hho_ctx* ctx, const float* X, const float* T, int B, double* loss, double* gW1, double* gb1,
                      double* gW2, double* gb2);
+// ilu.cu
+hho_status ilu_setup(hho_ctx* ctx, int l, bool fp32);
+template <typename T>
+hho_status ilu_apply(hho_ctx* ctx, int l, const T* v, T* z, T* tmp);
+void ilu_free(hho_ctx* ctx);
 // batch.cu
 hho_status batch_set(hho_ctx* ctx, int P, const int64_t* face_off, const int64_t* elem_off);
 hho_status batch_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, int32_t* its,

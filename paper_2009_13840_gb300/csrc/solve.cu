@@ -782,6 +782,17 @@ __global__ void k_interleave(int64_t planes, int R, int64_t N, const double* __r
     }
 }
 
+// v = (w' - sum_{q < npend} pc_q Vp_q) / den: the pending second pass and the
+// basis scaling of a smoother step whose preconditioner is not block Jacobi
+template <typename T>
+__global__ void k_pend_scale(int64_t n, const T* __restrict__ w, const double* __restrict__ den, T* __restrict__ v,
+                             const T* __restrict__ Vp, int64_t ld, int npend, const double* __restrict__ pc) {
+    const T inv = block_inverse<T>(den);
+    const T* s_pc = stage_pending<T>(pc, npend);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = pending(w, Vp, ld, npend, s_pc, i) * inv;
+}
+
 // v = w / den (FGMRES basis vector)
 __global__ void k_scale(int64_t n, const double* __restrict__ w, const double* __restrict__ den, double* __restrict__ v) {
     const double inv = block_inverse<double>(den);
@@ -924,6 +935,7 @@ Items items_for(const LevelMat& L, int R, int frows, int erows) {
 struct LevelWork {
     // smoother vectors in the V-cycle type (double or float)
     void *bv = nullptr, *x = nullptr, *w = nullptr, *V = nullptr, *Z = nullptr;
+    void* ilu_tmp = nullptr;  // element-block scratch of the ILU backward sweep
     double* sc = nullptr;
     double *cd = nullptr, *cc = nullptr;  // FP64 coarse right-hand side and solution (mixed precision)
 };
@@ -961,6 +973,7 @@ void free_workspace(hho_ctx* ctx) {
         dfree(l.w);
         dfree(l.V);
         dfree(l.Z);
+        dfree(l.ilu_tmp);
         dfree(l.sc);
         dfree(l.cd);
         dfree(l.cc);
@@ -1309,7 +1322,14 @@ static hho_status smooth(hho_ctx* ctx, int l, const T* bv, T* x, bool x_zero, bo
         T* vj = V + (int64_t)j * n;
         T* zj = Z + (int64_t)j * n;
         // the second pass of step j-1 (w'' = w' - V t2) is applied inside the Jacobi kernel
-        launch_jacobi<T>(ctx, L, j == 0 ? w0 : w, sc + 5, vj, zj, V, n, j, sc + G.t2);
+        if (ctx->smoother_kind == 1 && l < (int)ctx->ilu.size() && ctx->ilu[l]) {
+            k_pend_scale<T><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, j == 0 ? w0 : w, sc + 5, vj, V, n, j,
+                                                                     sc + G.t2);
+            ++ctx->launches;
+            HHO_TRY(ilu_apply<T>(ctx, l, vj, zj, static_cast<T*>(lw.ilu_tmp)));
+        } else {
+            launch_jacobi<T>(ctx, L, j == 0 ? w0 : w, sc + 5, vj, zj, V, n, j, sc + G.t2);
+        }
         // learned correction in the finest-level post-smoother, whose error the coarse correction has
         // stripped of its low-frequency part (the distribution of the training pairs)
         if (l == 0 && post && ctx->use_learned && ctx->learned) HHO_TRY(mlp_apply<T>(ctx, vj, zj));
@@ -1539,6 +1559,7 @@ hho_status pmg_build(hho_ctx* ctx) {
         HHO_TRY(device_alloc(ctx, &w.w, n * es));
         HHO_TRY(device_alloc(ctx, &w.V, (size_t)(m + 1) * n * es));
         HHO_TRY(device_alloc(ctx, &w.Z, (size_t)m * n * es));
+        HHO_TRY(device_alloc(ctx, &w.ilu_tmp, (size_t)std::max<int64_t>(L.ne * L.nP, 1) * es));
         HHO_TRY(dalloc(ctx, &w.sc, G.total));
         HHO_CUDA(cudaMemset(w.sc, 0, G.total * sizeof(double)));
         if (mixed && l < nl - 1) {
@@ -1569,6 +1590,9 @@ hho_status pmg_build(hho_ctx* ctx) {
     HHO_CUDA(cudaMemset(W->counter, 0, 16 * sizeof(unsigned)));
     HHO_CUDA(cudaMallocHost(&W->h_sc, 64 * sizeof(double)));
     HHO_TRY(null_build(ctx));
+    ilu_free(ctx);
+    if (ctx->smoother_kind == 1)
+        for (int l = 0; l < nl - 1; ++l) HHO_TRY(ilu_setup(ctx, l, mixed));
     HHO_TRY(coarse_setup(ctx));
     return HHO_OK;
 }

@@ -28,7 +28,8 @@ SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "hho_assem
            "hho_solve", "hho_recover", "hho_errors", "hho_get_element_schur", "hho_get_level_coo",
            "hho_set_element_schur", "hho_launch_count", "hho_set_option", "hho_destroy",
            "hho_last_error", "hho_set_batch", "hho_solve_batch", "hho_autotune", "hho_mlp_init", "hho_mlp_dims",
-           "hho_mlp_weights", "hho_mlp_features", "hho_mlp_generate", "hho_mlp_train", "hho_mlp_grads"]
+           "hho_mlp_weights", "hho_mlp_features", "hho_mlp_generate", "hho_mlp_train", "hho_mlp_grads",
+           "hho_ilu_apply"]
 
 
 class HHOError(RuntimeError):
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH):
         "hho_mlp_generate": (C.c_int, [P, C.c_int, C.c_uint64, C.c_int, C.POINTER(C.c_int64)]),
         "hho_mlp_train": (C.c_int, [P, C.c_int, C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double)]),
         "hho_mlp_grads": (C.c_int, [P, P, P, C.c_int, C.POINTER(C.c_double)] + [C.POINTER(C.c_double)] * 4),
+        "hho_ilu_apply": (C.c_int, [P, C.c_int, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -245,6 +247,10 @@ class Context:
         out = (C.c_double * 3)()
         self._check(self.lib.hho_autotune(self.h, int(reps), out))
         return dict(spmv_rows=int(out[0]), spmv_grid=int(out[1]), tile_rows=int(out[2]))
+
+    def ilu_apply(self, level, v, z):
+        """z = (L U)^{-1} v with the level's block ILU(0) factors (FP64)."""
+        self._check(self.lib.hho_ilu_apply(self.h, int(level), _ptr(v), _ptr(z)))
 
     # ---- learned smoother ----
     def mlp_init(self, hidden=128, seed=0):
