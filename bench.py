@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "ilu"],
+                    help="preconditioner of the smoother's GMRES: block Jacobi or block ILU(0)")
     ap.add_argument("--mesh", default="tri", choices=["tri", "hex"],
                     help="tri: n x n squares split into triangles (2D); hex: n^3 jittered hexahedra (3D)")
     ap.add_argument("--k", type=int, default=3)
@@ -257,6 +259,7 @@ def run_ours(args):
         # plain FP64 V-cycle on the same problem (for the speedup of the mixed one)
         fp64 = None
         if args.prec == "fp32" and not args.no_fp64_compare:
+            ctx.set_option("smoother", 1 if args.smoother == "ilu" else 0)
             ctx.pmg_setup(degrees, smooth_its=2, prec="fp64")
             for _ in range(args.warmup):
                 ctx.solve(x, rtol=args.rtol)
@@ -264,6 +267,7 @@ def run_ours(args):
             fp64 = {"ms_per_solve": ms64, "fgmres_iterations": inf64[-1]["iterations"],
                     "rel_residual": inf64[-1]["rel_residual"], "dof_per_s": ndof / (ms64 / 1e3)}
         ctx.set_option("coarse_fp32", args.coarse_fp32 if args.prec == "fp32" else 0)
+        ctx.set_option("smoother", 1 if args.smoother == "ilu" else 0)
         ctx.pmg_setup(degrees, smooth_its=2, prec=args.prec)
         for _ in range(args.warmup):
             info = ctx.solve(x, rtol=args.rtol)
@@ -345,7 +349,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 FGMRES + f32 V-cycle" if args.prec == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": wname, "vcycle_precision": args.prec,
+            "config": {"workload": wname, "vcycle_precision": args.prec, "smoother": args.smoother,
                        "coarse_precision": "fp32" if (args.prec == "fp32" and args.coarse_fp32) else "fp64",
                        "dofs": ndof,
                        "fgmres_iterations": last["iterations"], "coarse_iterations": last["coarse_iterations"],
