@@ -512,16 +512,16 @@ __global__ void k_gemv_blocks(const T* __restrict__ A, const int32_t* __restrict
         const int64_t n = nn[q], r0 = prob0[q];
         const T* a = A + off[q] + (r - r0) * n;
         const T* xq = x + r0;
-        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        T sp[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sp[u] = T(0);
         int64_t c = lane;
-        for (; c + 96 < n; c += 128) {
-            s0 += __ldg(a + c) * xq[c];
-            s1 += __ldg(a + c + 32) * xq[c + 32];
-            s2 += __ldg(a + c + 64) * xq[c + 64];
-            s3 += __ldg(a + c + 96) * xq[c + 96];
+        for (; c + 224 < n; c += 256) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sp[u] += __ldg(a + c + 32 * u) * xq[c + 32 * u];
         }
-        for (; c < n; c += 32) s0 += __ldg(a + c) * xq[c];
-        T s = (s0 + s1) + (s2 + s3);
+        for (; c < n; c += 32) sp[0] += __ldg(a + c) * xq[c];
+        T s = ((sp[0] + sp[1]) + (sp[2] + sp[3])) + ((sp[4] + sp[5]) + (sp[6] + sp[7]));
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) y[r] = s;
     }
