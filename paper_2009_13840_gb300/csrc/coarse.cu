@@ -191,6 +191,11 @@ __global__ void k_gemv(const T* __restrict__ A, int64_t n, const T* __restrict__
 // ---------------------------------------------------------------------------
 // substructuring path
 // ---------------------------------------------------------------------------
+// Leading dimension of a subdomain's column-major interior inverse: nI rounded
+// up to 4, so that every column starts on a 16-byte boundary in FP32 and FP64
+// (the padding rows are zero).
+__host__ __device__ inline int dd_ld(int nI) { return (nI + 3) & ~3; }
+
 struct DDView {
     int P;
     int64_t nG;
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(256) k_dd_factor(DDView V, double* __restrict_
         double* Xt = XT + V.offX[s];
         for (int64_t idx = threadIdx.x; idx < (int64_t)nI * nI; idx += blockDim.x) {
             int i = (int)(idx / nI), j = (int)(idx % nI);
-            At[(int64_t)j * nI + i] = W[(int64_t)i * ldw + nI + nGs + j];
+            At[(int64_t)j * dd_ld(nI) + i] = W[(int64_t)i * ldw + nI + nGs + j];
         }
         for (int64_t idx = threadIdx.x; idx < (int64_t)nI * nGs; idx += blockDim.x) {
             int i = (int)(idx / nGs), j = (int)(idx % nGs);
@@ -297,25 +302,81 @@ __global__ void k_dd_gather(int64_t nIt, const int32_t* __restrict__ flat_glob, 
         dI[i] = d[flat_glob[i]];
 }
 
-// yI = A_II^{-1} dI per subdomain (thread per interior unknown)
+// Vector of interior-inverse rows one lane loads per column
+template <typename T> struct DDVec;
+template <> struct DDVec<float> {
+    using V = float4;
+    static constexpr int W = 4;
+    __device__ static void fma(float a[4], const float4& v, float x) {
+        a[0] += v.x * x; a[1] += v.y * x; a[2] += v.z * x; a[3] += v.w * x;
+    }
+};
+template <> struct DDVec<double> {
+    using V = double2;
+    static constexpr int W = 2;
+    __device__ static void fma(double a[2], const double2& v, double x) {
+        a[0] += v.x * x; a[1] += v.y * x;
+    }
+};
+
+constexpr int DD_YI_WARPS = 8;
+constexpr int DD_YI_UNROLL = 8;
+
+// yI = A_II^{-1} dI.  One CTA per (subdomain, block of 32 * W rows): lane l of
+// every warp owns rows l*W .. l*W+W-1 of the block (one 16-byte load per
+// column, 512 contiguous bytes per warp); warp w takes the columns w, w+8, ...
+// with dI staged in shared memory; the eight warp partials are summed in a
+// fixed order, so the result does not depend on scheduling.
 template <typename T>
-__global__ void k_dd_yI(int64_t nIt, const int32_t* __restrict__ flat_sub, const int64_t* __restrict__ offI,
-                        const int32_t* __restrict__ nI, const int64_t* __restrict__ offA, const T* __restrict__ AinvT,
-                        const T* __restrict__ dI, T* __restrict__ yI) {
-    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nIt; f += (int64_t)gridDim.x * blockDim.x) {
-        int s = flat_sub[f];
-        int64_t o = offI[s];
-        int n = nI[s], i = (int)(f - o);
-        const T* A = AinvT + offA[s] + i;
-        const T* x = dI + o;
-        T a0 = T(0), a1 = T(0);
-        int j = 0;
-        for (; j + 1 < n; j += 2) {
-            a0 += __ldg(A + (int64_t)j * n) * x[j];
-            a1 += __ldg(A + (int64_t)(j + 1) * n) * x[j + 1];
+__global__ void __launch_bounds__(256) k_dd_yI(int P, int rb_max, const int64_t* __restrict__ offI,
+                                               const int32_t* __restrict__ nI, const int64_t* __restrict__ offA,
+                                               const T* __restrict__ AinvT, const T* __restrict__ dI,
+                                               T* __restrict__ yI) {
+    using DV = DDVec<T>;
+    using V = typename DV::V;
+    constexpr int W = DV::W, RB = 32 * W;
+    extern __shared__ unsigned char s_raw[];
+    T* sred = reinterpret_cast<T*>(s_raw);  // [DD_YI_WARPS][RB]
+    T* sx = sred + DD_YI_WARPS * RB;        // [nI]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t blk = blockIdx.x; blk < (int64_t)P * rb_max; blk += gridDim.x) {
+        const int s = (int)(blk / rb_max), rb = (int)(blk % rb_max);
+        const int n = nI[s];
+        if (rb * RB >= n) continue;  // uniform across the CTA
+        const int ld = dd_ld(n);
+        const int64_t o = offI[s];
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) sx[j] = dI[o + j];
+        __syncthreads();
+        const int r0 = rb * RB + lane * W;
+        T acc[W];
+#pragma unroll
+        for (int v = 0; v < W; ++v) acc[v] = T(0);
+        if (r0 < ld) {
+            const T* A = AinvT + offA[s] + r0;
+            int j = w;
+            for (; j + DD_YI_WARPS * (DD_YI_UNROLL - 1) < n; j += DD_YI_WARPS * DD_YI_UNROLL) {
+                V q[DD_YI_UNROLL];
+#pragma unroll
+                for (int u = 0; u < DD_YI_UNROLL; ++u)
+                    q[u] = __ldg(reinterpret_cast<const V*>(A + (int64_t)(j + DD_YI_WARPS * u) * ld));
+#pragma unroll
+                for (int u = 0; u < DD_YI_UNROLL; ++u) DV::fma(acc, q[u], sx[j + DD_YI_WARPS * u]);
+            }
+            for (; j < n; j += DD_YI_WARPS) DV::fma(acc, __ldg(reinterpret_cast<const V*>(A + (int64_t)j * ld)), sx[j]);
         }
-        if (j < n) a0 += __ldg(A + (int64_t)j * n) * x[j];
-        yI[f] = a0 + a1;
+#pragma unroll
+        for (int v = 0; v < W; ++v) sred[w * RB + lane * W + v] = acc[v];
+        __syncthreads();
+        for (int r = threadIdx.x; r < RB; r += blockDim.x) {
+            const int row = rb * RB + r;
+            if (row < n) {
+                T t = sred[r];
+#pragma unroll
+                for (int q = 1; q < DD_YI_WARPS; ++q) t += sred[q * RB + r];
+                yI[o + row] = t;
+            }
+        }
     }
 }
 
@@ -384,6 +445,7 @@ struct CoarseSolver {
     // substructuring
     int P = 0;
     int64_t nG = 0, nIt = 0;
+    int nI_max = 0;  // largest subdomain interior (shared-memory size of the interior GEMV)
     int32_t *sub_elem_ptr = nullptr, *sub_elem = nullptr, *nI = nullptr, *nGs = nullptr, *flat_sub = nullptr,
             *flat_glob = nullptr, *gam_list = nullptr, *gam_glob = nullptr, *g_ptr = nullptr, *g_s = nullptr,
             *g_j = nullptr, *elem_loc = nullptr;
@@ -781,7 +843,7 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
         }
         offGam[s + 1] = offGam[s] + nGss;
         offA[s] = tA;
-        tA += (int64_t)nIs * nIs;
+        tA += (int64_t)nIs * dd_ld(nIs);
         offX[s] = tX;
         tX += (int64_t)nIs * nGss;
         offAG[s] = tAG;
@@ -816,6 +878,11 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
     C->P = P;
     C->nG = nG;
     C->nIt = offI[P];
+    C->nI_max = *std::max_element(h_nI.begin(), h_nI.end());
+    if ((size_t)(C->nI_max + DD_YI_WARPS * 64) * sizeof(double) > 48 * 1024) {
+        ctx->err = "pmg_setup: a coarse subdomain has more than 5632 interior unknowns (lower dd_elements)";
+        return HHO_ERR_UNSUPPORTED;
+    }
     HHO_TRY(upload(ctx, &C->sub_elem_ptr, sub_elem_ptr));
     HHO_TRY(upload(ctx, &C->sub_elem, sub_elem));
     HHO_TRY(upload(ctx, &C->nI, h_nI));
@@ -926,6 +993,7 @@ static hho_status build_dd(hho_ctx* ctx, CoarseSolver* C) {
     V.sub_gn = d_sub_gn;
     V.nPL = nPL;
     HHO_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    HHO_CUDA(cudaMemsetAsync(C->AinvT, 0, (size_t)std::max<int64_t>(C->nAinvT, 1) * sizeof(double), ctx->stream));
     k_dd_factor<<<P, 256, 0, ctx->stream>>>(V, scratch, C->AinvT, C->XT, C->AGI, G, C->scal, pin_s, pin_j,
                                             ctx->d_flag);
     cudaError_t le = cudaGetLastError();
@@ -1042,8 +1110,13 @@ static hho_status coarse_apply_t(hho_ctx* ctx, CoarseSolver* C, const T* Ainv, c
         ++ctx->launches;
     } else {
         k_dd_gather<T><<<grid1d(C->nIt, 256), 256, 0, ctx->stream>>>(C->nIt, C->flat_glob, d, dI);
-        k_dd_yI<T><<<grid1d(C->nIt, 128), 128, 0, ctx->stream>>>(C->nIt, C->flat_sub, C->offI, C->nI, C->offA, AinvT,
-                                                                 dI, yI);
+        {
+            constexpr int RB = 32 * DDVec<T>::W;
+            const int rb_max = (C->nI_max + RB - 1) / RB;
+            const size_t shm = (size_t)(DD_YI_WARPS * RB + C->nI_max) * sizeof(T);
+            k_dd_yI<T><<<(unsigned)std::min<int64_t>((int64_t)C->P * rb_max, 1 << 30), DD_YI_WARPS * 32, shm,
+                         ctx->stream>>>(C->P, rb_max, C->offI, C->nI, C->offA, AinvT, dI, yI);
+        }
         k_dd_rG<T><<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(C->nG, C->gam_glob, C->g_ptr, C->g_s, C->g_j,
                                                                      C->nI, C->offI, C->offAG, AGI, yI, d, rG);
         k_gemv_blocks<T><<<grid1d(C->nG * 32, 256), 256, 0, ctx->stream>>>(Ainv, C->g_row, C->g_prob0, C->g_off,

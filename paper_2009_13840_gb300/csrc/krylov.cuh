@@ -40,7 +40,7 @@ GS gs_layout(int m) {
     return s;
 }
 
-enum Hook { HOOK_NONE = 0, HOOK_START = 1, HOOK_COLUMN = 2, HOOK_COLUMN_PY = 3 };
+enum Hook { HOOK_NONE = 0, HOOK_START = 1, HOOK_COLUMN = 2, HOOK_COLUMN_PY = 3, HOOK_COLUMN_1R = 4 };
 
 // Type of the per-thread and per-warp part of a dot product: FP32 inside the
 // FP32 V-cycle (FP64 arithmetic is a narrow pipe on this part), FP64 otherwise.
@@ -100,6 +100,10 @@ __device__ __forceinline__ T pending(const T* __restrict__ w, const T* __restric
 //           w'' = w' - V t2 (t2 = V^T w'), which is left to the consumer of
 //           w'': ||w''||^2 = ||w'||^2 - ||t2||^2 for orthonormal V (the
 //           correction t2 is small against w', so the difference is benign)
+//   COLUMN_1R  one-reduction classical Gram-Schmidt: t2 = V^T w of the
+//           unprojected w (the only pass, t1 unused), fresh = ||w||^2; the
+//           column is t2 with ||w - V t2||^2 = ||w||^2 - ||t2||^2, and the
+//           projection w - V t2 is left to the consumer
 template <typename A>
 __device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j, A fresh) {
     __shared__ A s_h[MMAX + 2], s_cs[MMAX], s_sn[MMAX], s_misc[2];
@@ -115,13 +119,13 @@ __device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j, A fr
         }
         return;
     }
-    if (hook != HOOK_COLUMN && hook != HOOK_COLUMN_PY) return;
+    if (hook != HOOK_COLUMN && hook != HOOK_COLUMN_PY && hook != HOOK_COLUMN_1R) return;
     const int ld = L.m + 1;
     double* H = sc + L.H;
     __shared__ A s_t2sq[MMAX + 1];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         const A t2 = (A)sc[L.t2 + i];
-        s_h[i] = (A)sc[L.t1 + i] + t2;
+        s_h[i] = (hook == HOOK_COLUMN_1R) ? t2 : (A)sc[L.t1 + i] + t2;
         s_t2sq[i] = t2 * t2;
         if (i < j) {
             s_cs[i] = (A)sc[L.cs + i];
@@ -140,7 +144,7 @@ __device__ __forceinline__ void run_hook(int hook, double* sc, GS L, int j, A fr
         return;
     }
     A hn2 = fresh;
-    if (hook == HOOK_COLUMN_PY) {
+    if (hook == HOOK_COLUMN_PY || hook == HOOK_COLUMN_1R) {
         for (int i = 0; i <= j; ++i) hn2 -= s_t2sq[i];
         hn2 = hn2 > A(0) ? hn2 : A(0);
     }

@@ -53,6 +53,8 @@ namespace {
 constexpr int GMAX = 8192;  // largest grid of any reduction kernel
 constexpr int RT = 256;     // threads per block of the reduction kernels
 constexpr int NVMAX = 8;    // dot products per kernel
+constexpr int EPT = 4;      // elements per thread of the streaming vector kernels (see vgrid)
+constexpr int NCCH = 4;     // combination vectors whose loads a streaming kernel issues together
 
 int grid1d(int64_t n, int tpb) {
     int64_t g = (n + tpb - 1) / tpb;
@@ -61,7 +63,7 @@ int grid1d(int64_t n, int tpb) {
 
 // grid of the streaming vector kernels: about 4 elements per thread
 int vgrid(int64_t n) {
-    int64_t g = (n + 4LL * RT - 1) / (4LL * RT);
+    int64_t g = (n + (int64_t)EPT * RT - 1) / ((int64_t)EPT * RT);
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, GMAX));
 }
 
@@ -807,18 +809,18 @@ __global__ void __launch_bounds__(RT) k_update_dot(int64_t n, T* __restrict__ w,
                                                     const T* __restrict__ Vd, int nv, int self,
                                                     double* __restrict__ partial, unsigned* __restrict__ counter,
                                                     double* __restrict__ out, int hook, double* sc, GS gsl, int j) {
-    __shared__ T s_coef[64];
-    for (int q = threadIdx.x; q < ncomb && q < 64; q += blockDim.x) s_coef[q] = T(sgn * coef[q]);
+    __shared__ T s_coef[MMAX + NCCH];
+    for (int q = threadIdx.x; q < MMAX + NCCH; q += blockDim.x) s_coef[q] = (q < ncomb) ? T(sgn * coef[q]) : T(0);
     __syncthreads();
     using A = typename AccT<T>::type;
     A dacc[NVMAX + 1];
 #pragma unroll
     for (int v = 0; v <= NVMAX; ++v) dacc[v] = A(0);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        T s = w[i];
-        for (int q = 0; q < ncomb; ++q) s += s_coef[q] * V[q * ld + i];
-        if (ncomb > 0) w[i] = s;
-        accumulate_dots(dacc, Vd, ld, i, nv, self, s);
+        T v = w[i];
+        for (int q = 0; q < ncomb; ++q) v += s_coef[q] * V[q * ld + i];
+        if (ncomb > 0) w[i] = v;
+        accumulate_dots(dacc, Vd, ld, i, nv, self, v);
     }
     if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
 }
@@ -831,7 +833,7 @@ __global__ void k_update_x(int64_t n, T* __restrict__ x, double a0, const T* __r
                            const double* __restrict__ sc, GS L) {
     extern __shared__ double s_dyn[];
     using A = typename AccT<T>::type;
-    __shared__ A ya[MMAX];
+    __shared__ A ya[MMAX + NCCH];
     const int ld2 = L.m + 1;
     double* Hs = s_dyn;
     double* y = s_dyn + ld2 * L.m;
@@ -848,13 +850,30 @@ __global__ void k_update_x(int64_t n, T* __restrict__ x, double a0, const T* __r
         }
     }
     __syncthreads();
-    if (threadIdx.x < MMAX) ya[threadIdx.x] = ((int)threadIdx.x < me) ? (A)y[threadIdx.x] : A(0);
+    if (threadIdx.x < MMAX + NCCH) ya[threadIdx.x] = ((int)threadIdx.x < me) ? (A)y[threadIdx.x] : A(0);
     __syncthreads();
     const A a0a = (A)a0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        A s = (a0 == 0.0) ? A(0) : a0a * (A)x[i];
-        for (int q = 0; q < me; ++q) s += ya[q] * (A)Z[q * ld + i];
-        x[i] = T(s);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += EPT * stride) {
+        A sv[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+            sv[e] = (a0 == 0.0 || i0 + e * stride >= n) ? A(0) : a0a * (A)x[i0 + e * stride];
+        for (int q0 = 0; q0 < me; q0 += NCCH) {
+            T z[NCCH][EPT];
+#pragma unroll
+            for (int q = 0; q < NCCH; ++q)
+#pragma unroll
+                for (int e = 0; e < EPT; ++e)
+                    z[q][e] = (q0 + q < me && i0 + e * stride < n) ? __ldg(Z + (q0 + q) * ld + i0 + e * stride) : T(0);
+#pragma unroll
+            for (int q = 0; q < NCCH; ++q)
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) sv[e] += ya[q0 + q] * (A)z[q][e];
+        }
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+            if (i0 + e * stride < n) x[i0 + e * stride] = T(sv[e]);
     }
 }
 
@@ -1333,10 +1352,16 @@ static hho_status smooth(hho_ctx* ctx, int l, const T* bv, T* x, bool x_zero, bo
         // learned correction in the finest-level post-smoother, whose error the coarse correction has
         // stripped of its low-frequency part (the distribution of the training pairs)
         if (l == 0 && post && ctx->use_learned && ctx->learned) HHO_TRY(mlp_apply<T>(ctx, vj, zj));
-        launch_spmv_dot<T>(ctx, l, zj, nullptr, w, 0, V, n, j + 1, 0, sc + G.t1, HOOK_NONE, sc, G, j);
-        // w' = w - V t1, t2 = V^T w', ||w'||^2; Hessenberg column with ||w''||^2 = ||w'||^2 - ||t2||^2
-        launch_update_dot<T>(ctx, n, w, V, n, j + 1, sc + G.t1, -1.0, V, j + 1, 1, sc + G.t2, HOOK_COLUMN_PY, sc, G,
-                             j);
+        if (std::is_same<T, float>::value) {
+            // FP32 V-cycle: one reduction per step, w = S z_j, t2 = V^T w and ||w||^2 together; Hessenberg
+            // column t2 with ||w - V t2||^2 = ||w||^2 - ||t2||^2, the projection left to the consumer
+            launch_spmv_dot<T>(ctx, l, zj, nullptr, w, 0, V, n, j + 1, 1, sc + G.t2, HOOK_COLUMN_1R, sc, G, j);
+        } else {
+            launch_spmv_dot<T>(ctx, l, zj, nullptr, w, 0, V, n, j + 1, 0, sc + G.t1, HOOK_NONE, sc, G, j);
+            // w' = w - V t1, t2 = V^T w', ||w'||^2; Hessenberg column with ||w''||^2 = ||w'||^2 - ||t2||^2
+            launch_update_dot<T>(ctx, n, w, V, n, j + 1, sc + G.t1, -1.0, V, j + 1, 1, sc + G.t2, HOOK_COLUMN_PY, sc,
+                                 G, j);
+        }
     }
     k_update_x<T><<<vgrid(n), RT, xupd_smem(G.m), ctx->stream>>>(n, x, x_zero ? 0.0 : 1.0, Z, n, sc, G);
     ++ctx->launches;
