@@ -310,12 +310,18 @@ template <> struct DDVec<float> {
     __device__ static void fma(float a[4], const float4& v, float x) {
         a[0] += v.x * x; a[1] += v.y * x; a[2] += v.z * x; a[3] += v.w * x;
     }
+    __device__ static void mul_add(float a[4], const float4& v, const float x[4]) {
+        a[0] += v.x * x[0]; a[1] += v.y * x[1]; a[2] += v.z * x[2]; a[3] += v.w * x[3];
+    }
 };
 template <> struct DDVec<double> {
     using V = double2;
     static constexpr int W = 2;
     __device__ static void fma(double a[2], const double2& v, double x) {
         a[0] += v.x * x; a[1] += v.y * x;
+    }
+    __device__ static void mul_add(double a[2], const double2& v, const double x[2]) {
+        a[0] += v.x * x[0]; a[1] += v.y * x[1];
     }
 };
 
@@ -561,12 +567,17 @@ __global__ void k_gj_elim_b(double* __restrict__ A, double* __restrict__ Ai, con
 }
 
 // y = blockdiag(A_q) x: one warp per row; row r belongs to problem row_q[r],
-// whose block (n_q x n_q at off[q]) acts on x[prob0[q] ..]
+// whose block (n_q x n_q at off[q]) acts on x[prob0[q] ..].  The row is read
+// with 16-byte loads from its first 16-byte boundary on (the few elements
+// before it and the ragged end with scalar loads); x comes through L1.
 template <typename T>
 __global__ void k_gemv_blocks(const T* __restrict__ A, const int32_t* __restrict__ row_q,
                               const int64_t* __restrict__ prob0, const int64_t* __restrict__ off,
                               const int32_t* __restrict__ nn, int64_t nrows, const T* __restrict__ x,
                               T* __restrict__ y) {
+    using DV = DDVec<T>;
+    using V = typename DV::V;
+    constexpr int W = DV::W, U = 4;
     int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     for (int64_t r = w; r < nrows; r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -574,16 +585,45 @@ __global__ void k_gemv_blocks(const T* __restrict__ A, const int32_t* __restrict
         const int64_t n = nn[q], r0 = prob0[q];
         const T* a = A + off[q] + (r - r0) * n;
         const T* xq = x + r0;
-        T sp[8];
+        const int mis = (int)((reinterpret_cast<uintptr_t>(a) / sizeof(T)) & (W - 1));
+        const int64_t head = mis ? ((W - mis < n) ? W - mis : n) : 0;
+        const int64_t nvec = (n - head) / W;
+        const V* av = reinterpret_cast<const V*>(a + head);
+        const T* xv = xq + head;
+        T sp[U][W];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) sp[u] = T(0);
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int v = 0; v < W; ++v) sp[u][v] = T(0);
+        if (lane < head) sp[0][0] += __ldg(a + lane) * xq[lane];
         int64_t c = lane;
-        for (; c + 224 < n; c += 256) {
+        for (; c + 32 * (U - 1) < nvec; c += 32 * U) {
+            V q4[U];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) sp[u] += __ldg(a + c + 32 * u) * xq[c + 32 * u];
+            for (int u = 0; u < U; ++u) q4[u] = __ldg(av + c + 32 * u);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const T* xx = xv + (c + 32 * u) * W;
+                T t[W];
+#pragma unroll
+                for (int v = 0; v < W; ++v) t[v] = xx[v];
+                DV::mul_add(sp[u], q4[u], t);
+            }
         }
-        for (; c < n; c += 32) sp[0] += __ldg(a + c) * xq[c];
-        T s = ((sp[0] + sp[1]) + (sp[2] + sp[3])) + ((sp[4] + sp[5]) + (sp[6] + sp[7]));
+        for (; c < nvec; c += 32) {
+            const V q1 = __ldg(av + c);
+            const T* xx = xv + c * W;
+            T t[W];
+#pragma unroll
+            for (int v = 0; v < W; ++v) t[v] = xx[v];
+            DV::mul_add(sp[0], q1, t);
+        }
+        for (int64_t e = head + nvec * W + lane; e < n; e += 32) sp[1][0] += __ldg(a + e) * xq[e];
+        T s = T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int v = 0; v < W; ++v) s += sp[u][v];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) y[r] = s;
     }
