@@ -53,6 +53,7 @@ namespace {
 constexpr int GMAX = 8192;  // largest grid of any reduction kernel
 constexpr int RT = 256;     // threads per block of the reduction kernels
 constexpr int NVMAX = 8;    // dot products per kernel
+constexpr int FP64_GRID = 2 * 152;  // blocks of the FP64 reduction kernels (two per SM)
 constexpr int EPT = 4;      // elements per thread of the streaming vector kernels (see vgrid)
 constexpr int NCCH = 4;     // combination vectors whose loads a streaming kernel issues together
 
@@ -168,6 +169,17 @@ __device__ __forceinline__ void accumulate_dots(A (&dacc)[NVMAX + 1], const T* _
 #pragma unroll
     for (int q = 0; q < NVMAX; ++q)
         if (q < nv) dacc[q] += (A)V[q * ld + o] * dv;
+    if (self) dacc[NVMAX] += dv * dv;
+}
+
+// accumulate_dots with a compile-time number of dot vectors (no predicated
+// FMAs: the FP64 pipe of this part is narrow enough for them to matter)
+template <int NVC, typename T, typename A>
+__device__ __forceinline__ void accumulate_dots_n(A (&dacc)[NVMAX + 1], const T* __restrict__ V, int64_t ld,
+                                                  int64_t o, int self, T v) {
+    const A dv = (A)v;
+#pragma unroll
+    for (int q = 0; q < NVC; ++q) dacc[q] += (A)V[q * ld + o] * dv;
     if (self) dacc[NVMAX] += dv * dv;
 }
 
@@ -658,11 +670,16 @@ __global__ void __launch_bounds__(RT, 4) k_spmv_v(LV<float> L, Items it, const f
             float acc[RF];
 #pragma unroll
             for (int r = 0; r < RF; ++r) acc[r] = 0.f;
+            // the next slot's column index is fetched one slot ahead, so that
+            // each slot waits for one round of loads (x and values) only
             const int ns = L.ff_nsl[F];
+            int64_t G = (ns > 0) ? L.ff_col[F] : 0;
             for (int s = 0; s < ns; ++s) {
+                const int64_t Gn = (s + 1 < ns) ? L.ff_col[(s + 1) * nf + F] : 0;
                 float xv[B];
-                load_run_plain<B>(x + (int64_t)L.ff_col[s * nf + F] * B, xv);
+                load_run_plain<B>(x + G * B, xv);
                 block_mv<RF, B>(L.ff + ((int64_t)s * B * nf + F) * B + r0, nf * B, xv, acc);
+                G = Gn;
             }
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
@@ -695,10 +712,13 @@ __global__ void __launch_bounds__(RT, 4) k_spmv_v(LV<float> L, Items it, const f
 #pragma unroll
             for (int r = 0; r < NP; ++r) acc[r] = 0.f;
             const int N = L.pf_nsl[E];
+            int64_t G = (N > 0) ? L.pf_col[E] : 0;
             for (int f = 0; f < N; ++f) {
+                const int64_t Gn = (f + 1 < N) ? L.pf_col[(f + 1) * ne + E] : 0;
                 float xv[B];
-                load_run_plain<B>(x + (int64_t)L.pf_col[f * ne + E] * B, xv);
+                load_run_plain<B>(x + G * B, xv);
                 block_mv<NP, B>(L.pf + ((int64_t)f * B * ne + E) * NP, ne * NP, xv, acc);
+                G = Gn;
             }
             {
                 float xp[NP];
@@ -803,10 +823,10 @@ __global__ void k_scale(int64_t n, const double* __restrict__ w, const double* _
 }
 
 // w += sgn * sum_{q<ncomb} coef[q] V_q, then FP64 dots of the new w with Vd_0..Vd_{nv-1} and itself.
-template <typename T>
+template <typename T, int NVC>
 __global__ void __launch_bounds__(RT) k_update_dot(int64_t n, T* __restrict__ w, const T* __restrict__ V, int64_t ld,
                                                     int ncomb, const double* __restrict__ coef, double sgn,
-                                                    const T* __restrict__ Vd, int nv, int self,
+                                                    const T* __restrict__ Vd, int self,
                                                     double* __restrict__ partial, unsigned* __restrict__ counter,
                                                     double* __restrict__ out, int hook, double* sc, GS gsl, int j) {
     __shared__ T s_coef[MMAX + NCCH];
@@ -820,9 +840,9 @@ __global__ void __launch_bounds__(RT) k_update_dot(int64_t n, T* __restrict__ w,
         T v = w[i];
         for (int q = 0; q < ncomb; ++q) v += s_coef[q] * V[q * ld + i];
         if (ncomb > 0) w[i] = v;
-        accumulate_dots(dacc, Vd, ld, i, nv, self, v);
+        accumulate_dots_n<NVC>(dacc, Vd, ld, i, self, v);
     }
-    if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
+    if (NVC + self > 0) finish_dots(dacc, NVC, self, partial, counter, out, hook, sc, gsl, j);
 }
 
 // x = a0 x + Z y with y = R^{-1} g solved redundantly by every block (m <= 64):
@@ -1292,8 +1312,24 @@ static void launch_update_dot(hho_ctx* ctx, int64_t n, T* w, const T* V, int64_t
                               double sgn, const T* Vd, int nv, int self, double* out, int hook, double* sc, GS gsl,
                               int j) {
     Workspace* W = ctx->ws;
-    k_update_dot<T><<<vgrid(n), RT, 0, ctx->stream>>>(n, w, V, ld, ncomb, coef, sgn, Vd, nv, self, W->partial,
-                                                      W->counter, out, hook, sc, gsl, j);
+    // FP64: fewer, longer threads, since every warp's share of the block
+    // reductions costs FP64 additions on this part's narrow FP64 pipe
+    const int g = std::is_same<T, double>::value ? std::min(vgrid(n), FP64_GRID) : vgrid(n);
+#define HHO_UPD(NVC)                                                                                               \
+    k_update_dot<T, NVC><<<g, RT, 0, ctx->stream>>>(n, w, V, ld, ncomb, coef, sgn, Vd, self, W->partial, W->counter, \
+                                                    out, hook, sc, gsl, j)
+    switch (nv) {
+        case 0: HHO_UPD(0); break;
+        case 1: HHO_UPD(1); break;
+        case 2: HHO_UPD(2); break;
+        case 3: HHO_UPD(3); break;
+        case 4: HHO_UPD(4); break;
+        case 5: HHO_UPD(5); break;
+        case 6: HHO_UPD(6); break;
+        case 7: HHO_UPD(7); break;
+        default: HHO_UPD(8); break;
+    }
+#undef HHO_UPD
     ++ctx->launches;
 }
 
