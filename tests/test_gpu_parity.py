@@ -234,6 +234,34 @@ def test_substructured_coarse_solver(hho_mod, name, mk, cond):
     ctx.close()
 
 
+@pytest.mark.parametrize("cond", ["v", "vp"])
+def test_substructured_coarse_large_subdomains(hho_mod, cond):
+    """Subdomains of about 96 elements: each interior inverse spans several row
+    blocks of the interior solve kernel (64 rows per block in FP64, 128 in
+    FP32) with a ragged last block.  FP64 V-cycle against the oracle's sparse
+    direct coarse solve; the FP32 coarse solve against the FP64 one."""
+    mesh = tri_mesh(20, 18, jitter=0.2, seed=21, neumann_sides=(1,))
+    k = 1
+    h, _ = _oracle(mesh, k, cond, fields.TrigStokes2D())
+    ctx = hho_mod.Context(mesh, k, cond)
+    ctx.set_element_schur(np.concatenate([s.ravel() for s in h.S_T]))
+    ctx.set_option("coarse_dense_max", 100)
+    ctx.set_option("dd_elements", 96)
+    ctx.pmg_setup([1, 0], smooth_its=2)
+    pmg = PMG(h, [1, 0], coarse="splu")
+    b = np.random.default_rng(22).standard_normal(ctx.ndof(0))
+    z = torch.empty(ctx.ndof(0), dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.from_numpy(b).cuda(), z)
+    ref = pmg.apply(b)
+    assert np.linalg.norm(z.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
+    ctx.set_option("coarse_fp32", 1)
+    ctx.pmg_setup([1, 0], smooth_its=2, prec="fp32")
+    z32 = torch.empty(ctx.ndof(0), dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.from_numpy(b).cuda(), z32)
+    assert np.linalg.norm(z32.cpu().numpy() - ref) <= 1e-3 * np.linalg.norm(ref)
+    ctx.close()
+
+
 @pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("cond", ["vp", "v"])
 def test_mixed_precision_fp32_coarse(hho_mod, name, mk, cond):
