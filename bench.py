@@ -37,7 +37,7 @@ UNIT = "DOF/s"
 # DRAM bytes (read + write) of one FP32 level-0 operator launch on the default
 # workload, from the ncu capture summarised in
 # profiles/k_spmv_level0_tri128_k3_vcond.md (kernel unchanged since)
-SPMV_F32_TRAFFIC = {("tri", 128, 3, "v"): 144289024 + 3541248}
+SPMV_F32_TRAFFIC = {("tri", 128, 3, "v"): 144286208 + 3245056}
 
 
 def parse():
