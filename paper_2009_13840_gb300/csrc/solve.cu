@@ -12,11 +12,12 @@
 // The V-cycle runs in FP64 or, for the mixed-precision option, with FP32
 // level operators, smoother blocks and smoother vectors (FP32 multiply-adds).
 // In the FP32 V-cycle a dot product is summed in FP32 inside a thread (a few
-// terms) and across the 32 lanes of a warp, and in FP64 from there on (warps,
-// blocks); the relative rounding error stays near (terms per thread + 5) FP32
-// ulps of sum |x_i y_i|, far below what the smoother needs, and the FP64 pipe
-// (about 1/64 of the FP32 rate on this part) stays off the streaming loops.
-// The Hessenberg algebra and the coarse solve are FP64, and the outer FGMRES
+// terms), across the 32 lanes of a warp and across the warps of a block, and
+// each block's partial is stored in FP64 and added in the last block; the
+// relative rounding error stays near (terms per thread + 13) FP32 ulps of
+// sum |x_i y_i|, far below what the smoother needs, and the FP64 pipe (about
+// 1/64 of the FP32 rate on this part) stays off the FP32 kernels.  The
+// smoother's Hessenberg recurrence runs in the level type; the outer FGMRES
 // with its operator stays FP64.
 //
 // Arnoldi steps use classical Gram-Schmidt applied twice (CGS2).  Kernel
@@ -26,12 +27,17 @@
 //   upd+dot    w -= V t1,  t2 = V^T w
 //   upd+norm   w -= V t2,  ||w||^2, then the Hessenberg column, Givens rotation
 //              and residual estimate in the last block of the grid
-// and of the smoother, one kernel shorter:
+// and of the FP64 smoother, one kernel shorter:
 //   apply      w'' = w' - V t2 (second pass of step j-1), v_j = w'' / ||w''||,
 //              z_j = M^{-1} v_j  (block Jacobi)
 //   spmv+dot   w = S z_j,  t1 = V^T w
 //   upd+dot    w' = w - V t1,  t2 = V^T w',  ||w'||^2, then the Hessenberg
 //              column with ||w''||^2 = ||w'||^2 - ||t2||^2
+// and of the FP32 smoother (at most m = 2 basis vectors), one more kernel
+// shorter, by one-reduction classical Gram-Schmidt:
+//   apply      w' = w - V t (step j-1), v_j = w' / ||w'||, z_j = M^{-1} v_j
+//   spmv+dot   w = S z_j,  t = V^T w,  ||w||^2, then the Hessenberg column
+//              with ||w'||^2 = ||w||^2 - ||t||^2
 // Every dot product is a deterministic two-level reduction inside the kernel
 // that produces its operand: each block writes a partial sum and the last
 // block to finish adds the partials in index order, so results are bitwise
