@@ -92,6 +92,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(v, ws, device):
+    """Max of a per-rank scalar over the process group (the slowest rank's
+    time); v itself when ws == 1."""
+    if ws <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, seconds):
+    """Whole-job throughput of ws replicas: the units all ranks processed over
+    the slowest rank's time."""
+    return ws * units_per_rank / seconds
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -279,11 +297,8 @@ def run_ours(args):
             ms, infos = timed_solves(args.steps, "timed_step")
             torch.cuda.synchronize()
         launches = ctx.launch_count() - l0
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        value = ws * ndof / (ms / 1e3)
+        ms = max_over_ranks(ms, ws, "cuda")
+        value = whole_job_rate(ndof, ws, ms / 1e3)
 
         # dominant kernel: the level-0 operator of the V-cycle, timed live with CUDA events on its stream
         def time_kernel(fn, reps=20):
@@ -331,11 +346,7 @@ def run_ours(args):
             stream.synchronize()
             if i >= args.warmup:
                 et.append(time.perf_counter() - t0)
-        e2e_s = float(np.mean(et))
-        if ws > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(float(np.mean(et)), ws, "cuda")
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, nd, its, dt = oracle_sample(args.sample_n, args.k, args.cond, args.rtol)
@@ -364,7 +375,7 @@ def run_ours(args):
                          "fp64_outer_spmv": {"achieved": nb64 / (ms64_k / 1e3) / 1e9, "bytes_per_launch": nb64,
                                              "ms_per_launch": ms64_k}},
             "cpu_baseline": cpu,
-            "e2e": {"value": ws * ndof / e2e_s, "unit": UNIT,
+            "e2e": {"value": whole_job_rate(ndof, ws, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": int((f.numel() + gD.numel() + gN.numel()) * 8),
                     "d2h_bytes_per_step": int(ndof * 8)},
             "gpu_launches": int(launches),
