@@ -165,6 +165,96 @@ __device__ int elem_start(const ElemSh& E, int d, int K, const double* x, double
     return m;
 }
 
+// Coefficients of the three-term recursions of elem_start divided through by
+// their leading factor once per CTA, so that value-only evaluations need no
+// FP64 division (a multi-instruction sequence on this part's narrow FP64 pipe):
+//   Legendre / Dubiner radial part  P_{n+1} = qa[n] x P_n - qb[n] y P_{n-1}
+//       qa[n] = (2n+1)/(n+1), qb[n] = n/(n+1)
+//   Jacobi P^{(a,0)}, a = 2p+1      J_{n} = (ja x + jb) J_{n-1} - jc J_{n-2},
+//       (ja, jb, jc)[p][n] = (c1, c2, c3)[n, a] / c0[n, a]   (n >= 2)
+struct RecTab {
+    double qa[MAX_K2 + 1], qb[MAX_K2 + 1];
+    double ja[MAX_K2 + 1][MAX_K2 + 1], jb[MAX_K2 + 1][MAX_K2 + 1], jc[MAX_K2 + 1][MAX_K2 + 1];
+};
+
+// Fill a RecTab (all threads of the CTA; ends with a barrier).
+__device__ void rec_tab_fill(RecTab& T) {
+    for (int i = threadIdx.x; i <= MAX_K2; i += blockDim.x) {
+        T.qa[i] = (2.0 * i + 1.0) / (i + 1.0);
+        T.qb[i] = (double)i / (i + 1.0);
+    }
+    for (int i = threadIdx.x; i < (MAX_K2 + 1) * (MAX_K2 + 1); i += blockDim.x) {
+        const int p = i / (MAX_K2 + 1), n = i % (MAX_K2 + 1), a = 2 * p + 1;
+        double A = 0.0, B = 0.0, C = 0.0;
+        if (n >= 2) {
+            const double c0 = 2.0 * n * (n + a) * (2 * n + a - 2);
+            const double c1 = (double)(2 * n + a - 1) * (2 * n + a) * (2 * n + a - 2);
+            const double c2 = (double)(2 * n + a - 1) * a * a;
+            const double c3 = 2.0 * (n + a - 1) * (n - 1) * (2 * n + a);
+            A = c1 / c0;
+            B = c2 / c0;
+            C = c3 / c0;
+        }
+        T.ja[p][n] = A;
+        T.jb[p][n] = B;
+        T.jc[p][n] = C;
+    }
+    __syncthreads();
+}
+
+// Values of the element starting functions of elem_start (same functions,
+// same order; no gradients) at x, K <= MAX_K2, with the recursion
+// coefficients of T; returns the count.
+__device__ int elem_start_val(const ElemSh& E, int d, int K, const double* x, double* val, const RecTab& T) {
+    if (E.simplex) {
+        const double dx = x[0] - E.v0[0], dy = x[1] - E.v0[1];
+        const double r = 2.0 * (E.Minv[0][0] * dx + E.Minv[0][1] * dy) - 1.0;
+        const double s = 2.0 * (E.Minv[1][0] * dx + E.Minv[1][1] * dy) - 1.0;
+        const double t = 0.5 * (1.0 - s), u = r + 0.5 * (1.0 + s), tt = t * t;
+        double Q[MAX_K2 + 2];
+        Q[0] = 1.0;
+        if (K >= 1) Q[1] = u;
+        for (int p = 1; p < K; ++p) Q[p + 1] = T.qa[p] * u * Q[p] - T.qb[p] * tt * Q[p - 1];
+        // function (l, p) with q = l - p sits at index l (l + 1) / 2 + q
+        for (int p = 0; p <= K; ++p) {
+            const int a = 2 * p + 1;
+            double j0 = 1.0, j1 = 0.5 * ((a + 2) * s + a);
+            for (int q = 0; q <= K - p; ++q) {
+                double J;
+                if (q == 0) {
+                    J = 1.0;
+                } else if (q == 1) {
+                    J = j1;
+                } else {
+                    J = (T.ja[p][q] * s + T.jb[p][q]) * j1 - T.jc[p][q] * j0;
+                    j0 = j1;
+                    j1 = J;
+                }
+                const int l = p + q;
+                val[l * (l + 1) / 2 + q] = Q[p] * J;
+            }
+        }
+        return (K + 1) * (K + 2) / 2;
+    }
+    double P[3][MAX_K2 + 2];
+    for (int i = 0; i < d; ++i) {
+        const double xi = (x[i] - E.bc[i]) / E.br[i];
+        P[i][0] = 1.0;
+        if (K >= 1) P[i][1] = xi;
+        for (int n = 1; n < K; ++n) P[i][n + 1] = T.qa[n] * xi * P[i][n] - T.qb[n] * P[i][n - 1];
+    }
+    int m = 0;
+    if (d == 2) {
+        for (int l = 0; l <= K; ++l)
+            for (int a = l; a >= 0; --a) val[m++] = P[0][a] * P[1][l - a];
+    } else {
+        for (int l = 0; l <= K; ++l)
+            for (int a = l; a >= 0; --a)
+                for (int b = l - a; b >= 0; --b) val[m++] = P[0][a] * P[1][b] * P[2][l - a - b];
+    }
+    return m;
+}
+
 // Face starting functions (values) at x.
 __device__ int face_start(const FaceGeo& g, int d, int K, const double* x, double* val) {
     double y0 = 0.0, y1 = 0.0;
@@ -975,6 +1065,8 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
                                              double* __restrict__ yT, double* __restrict__ scratch, int64_t scratch_per) {
     __shared__ ElemSh E;
     __shared__ double s_acc[3 * 36 + 3 * 10 + 36];
+    __shared__ RecTab tab;
+    rec_tab_fill(tab);
     const int nR = dimP(d, k + 1), nE = dimP(d, k), nF = dimP(d - 1, k);
     const int pd = 2 * k + 6;
     double* ws = scratch + (int64_t)blockIdx.x * scratch_per;
@@ -997,9 +1089,9 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
             double part[3 * 21];
             for (int i = 0; i < d * nE; ++i) part[i] = 0.0;
             for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-                double x[3] = {0, 0, 0}, w, val[36], grad[36 * 3];
+                double x[3] = {0, 0, 0}, w, val[36];
                 elem_point(E, d, gl, pd, q, x, &w);
-                elem_start(E, d, k, x, val, grad);
+                elem_start_val(E, d, k, x, val, tab);
                 for (int c = 0; c < d; ++c) {
                     double wf = w * fdat[(o + q) * d + c];
                     for (int a = 0; a < nE; ++a) part[c * nE + a] += wf * val[a];
