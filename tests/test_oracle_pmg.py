@@ -119,3 +119,67 @@ def test_iteration_counts_mesh_independent_vcond():
         _, it, _ = fgmres(h.S, pmg.apply, rhs, rtol=1e-8, null=h.null_vector())
         its.append(it)
     assert its[-1] <= its[0] + 6, its
+
+
+def _dense_block_jacobi(S, mesh, b, nP):
+    """The smoother preconditioner (face diagonal blocks, element pressure pivot
+    blocks S_TT - sum_F S_TF S_FF^-1 S_FT) as one dense matrix, from index sets
+    of its own."""
+    nf = mesh.n_face
+    Minv = np.zeros_like(S)
+    fidx = [np.arange(F * b, (F + 1) * b) for F in range(nf)]
+    for F in range(nf):
+        Minv[np.ix_(fidx[F], fidx[F])] = np.linalg.inv(S[np.ix_(fidx[F], fidx[F])])
+    for T in range(mesh.n_elem):
+        t = nf * b + T * nP + np.arange(nP)
+        M = S[np.ix_(t, t)].copy()
+        for F in mesh.faces_of(T):
+            f = fidx[int(F)]
+            M -= S[np.ix_(t, f)] @ np.linalg.solve(S[np.ix_(f, f)], S[np.ix_(f, t)])
+        Minv[np.ix_(t, t)] = np.linalg.inv(M)
+    return Minv
+
+
+def _dense_smooth(S, Minv, b, x0, m):
+    """m GMRES iterations with right preconditioning as an explicit least-squares
+    problem over the monomial Krylov basis of S Minv (no Arnoldi)."""
+    r0 = b - S @ x0
+    K = [r0]
+    for _ in range(m - 1):
+        K.append(S @ (Minv @ K[-1]))
+    Z = Minv @ np.stack(K, axis=1)
+    y = np.linalg.lstsq(S @ Z, r0, rcond=None)[0]
+    return x0 + Z @ y
+
+
+@pytest.mark.parametrize("cond", ["v", "vp"])
+def test_vcycle_against_dense_brute_force(cond):
+    """One V-cycle (Algorithm MG_V, Sec. 3.3) on three levels with two smoothing
+    iterations, against a dense restatement: dense Galerkin operators, dense
+    block-Jacobi preconditioners, smoothing by explicit Krylov least squares,
+    dense coarse solve."""
+    mesh = tri_mesh(3, 2, jitter=0.2, seed=11, neumann_sides=(1,))
+    h = HHO(mesh, 2, cond)
+    degrees = [2, 1, 0]
+    pmg = PMG(h, degrees, smooth_its=2, coarse="lu")
+    Rs = [restriction(mesh, 2, degrees[l], degrees[l + 1], cond).toarray() for l in range(2)]
+    Ss = [h.S.toarray()]
+    for R in Rs:
+        Ss.append(R @ Ss[-1] @ R.T)
+    Ms = [_dense_block_jacobi(Ss[l], mesh, pmg.levels[l].b, pmg.levels[l].nP) for l in range(2)]
+    rng = np.random.default_rng(12)
+    for l in range(2):  # the oracle's preconditioner is the dense one
+        v = rng.standard_normal(Ss[l].shape[0])
+        assert np.linalg.norm(pmg.levels[l].precond(v) - Ms[l] @ v) < 1e-11 * np.linalg.norm(Ms[l] @ v)
+
+    def vcycle(l, b):
+        w = _dense_smooth(Ss[l], Ms[l], b, np.zeros_like(b), 2)
+        d = Rs[l] @ (b - Ss[l] @ w)
+        c = np.linalg.solve(Ss[l + 1], d) if l + 1 == 2 else vcycle(l + 1, d)
+        w = w + Rs[l].T @ c
+        return _dense_smooth(Ss[l], Ms[l], b, w, 2)
+
+    b = rng.standard_normal(h.ndof)
+    ref = vcycle(0, b)
+    z = pmg.apply(b)
+    assert np.linalg.norm(z - ref) < 1e-9 * np.linalg.norm(ref)
