@@ -92,3 +92,28 @@ def test_bases_orthonormal_and_hierarchical(mesh):
         X, W = F.rule(2 * K + 2)
         V = B.eval(X)
         assert np.abs(V.T @ (W[:, None] * V) - np.eye(B.n)).max() < 1e-13
+
+
+@pytest.mark.parametrize("mk", [lambda: tri_mesh(5, 4, jitter=0.25, seed=2),
+                                lambda: quad_mesh(4, jitter=0.25, seed=3),
+                                lambda: hex_mesh(3, jitter=0.15, seed=4)])
+def test_closed_elements_and_outward_normals(mk):
+    """Each element is closed (sum over its faces of |F| n_TF = 0, the
+    divergence theorem for a constant field), n_TF is a unit vector pointing
+    away from x_T, |T| = (1/d) sum_F |F| x_F . n_TF (the divergence theorem for
+    the field x on planar faces), and the element measures tile the unit domain."""
+    m = mk()
+    elems, faces = mesh_geometry(m)
+    d = m.dim
+    total = 0.0
+    for e in elems:
+        s = sum(F.meas * n for F, n in zip(e.faces, e.nTF))
+        assert np.abs(s).max() < 1e-13
+        for F, n in zip(e.faces, e.nTF):
+            assert float(n @ (F.xF - e.xT)) > 0.0
+            assert abs(np.linalg.norm(n) - 1.0) < 1e-14
+        # divergence theorem for the field x / d: |T| = (1/d) sum_F |F| (x_F . n_TF) on planar faces
+        vol = sum(F.meas * float(F.xF @ n) for F, n in zip(e.faces, e.nTF)) / d
+        assert abs(vol - e.meas) < 1e-13
+        total += e.meas
+    assert abs(total - 1.0) < 1e-13
