@@ -39,6 +39,7 @@ namespace hho {
 namespace {
 
 constexpr int TPB = 128;     // threads per element CTA
+static_assert(TPB % 32 == 0, "element CTAs are whole warps (warp-shuffle reductions)");
 constexpr int TQ = 32;       // quadrature points per tile
 
 __device__ __forceinline__ double glx(const double* gl, int n, int i) { return gl[n * MAX_GL + i]; }
@@ -1083,7 +1084,7 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
         __syncthreads();
         // body force: int f_c phi_j, j < nE (starting basis, then transform)
         {
-            __shared__ double red[TPB];
+            __shared__ double red[TPB / 32][3 * 21];
             int nq = elem_npts(E, d, pd);
             int64_t o = enode_off[t];
             double part[3 * 21];
@@ -1097,16 +1098,20 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
                     for (int a = 0; a < nE; ++a) part[c * nE + a] += wf * val[a];
                 }
             }
+            // warp sums by shuffles (every lane of the CTA is here), then the
+            // TPB / 32 warp sums in warp order: no serial chain on one thread
             for (int i = 0; i < d * nE; ++i) {
-                red[threadIdx.x] = part[i];
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    double tot = 0.0;
-                    for (int r = 0; r < TPB; ++r) tot += red[r];
-                    s_acc[i] = tot;
-                }
-                __syncthreads();
+                double v = part[i];
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i] = v;
             }
+            __syncthreads();
+            for (int i = threadIdx.x; i < d * nE; i += blockDim.x) {
+                double tot = 0.0;
+                for (int w = 0; w < TPB / 32; ++w) tot += red[w][i];
+                s_acc[i] = tot;
+            }
+            __syncthreads();
             for (int idx = threadIdx.x; idx < d * nE; idx += blockDim.x) {
                 int c = idx / nE, j = idx % nE;
                 double v = 0.0;
