@@ -158,7 +158,10 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
  *                       the substructured direct solver
  *   "dd_elements"       target number of elements per subdomain of the
  *                       substructured coarse solver (default 128 in 2D, 64 in
- *                       3D; rounded so the subdomain count is a power of two)
+ *                       3D; rounded so the subdomain count is a power of two);
+ *                       pmg_setup returns HHO_ERR_UNSUPPORTED when a subdomain
+ *                       has more than 5632 interior unknowns (the interior
+ *                       solve stages them in 48 KB of shared memory)
  *   "graphs"            1 (default): pmg_vcycle and hho_solve replay a CUDA
  *                       graph of the V-cycle captured on first use for each
  *                       (input, output) pair of device buffers; 0: launch
