@@ -115,6 +115,19 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _vec(t, dtype, n, what):
+    """Device pointer of a contiguous CUDA tensor of `dtype` holding at least
+    n values: the library reads and writes exactly n, so a smaller or
+    mistyped buffer is refused here rather than overrun on the device."""
+    if t is None:
+        raise ValueError(f"{what}: a tensor is required")
+    if t.dtype != dtype:
+        raise TypeError(f"{what}: expected {dtype}, got {t.dtype}")
+    if t.numel() < n:
+        raise ValueError(f"{what}: expected {n} values, got {t.numel()}")
+    return _ptr(t)
+
+
 @dataclass
 class MeshArrays:
     """Host arrays of a mesh in the layout of the C ABI."""
@@ -192,11 +205,22 @@ class Context:
         self._check(self.lib.hho_quad_nodes(self.h, NODES[which], C.byref(n), _ptr(xyz), _ptr(nrm)))
         return (xyz, nrm) if which == "face" else xyz
 
+    def _node_count(self, which):
+        n = C.c_int64()
+        self._check(self.lib.hho_quad_nodes(self.h, NODES[which], C.byref(n), None, None))
+        return n.value
+
+    def _data_ptrs(self, f, gD, gN, rhs_out):
+        f64 = self._torch.float64
+        ne, nf = self._node_count("elem") * self.dim, self._node_count("face") * self.dim
+        return (_vec(f, f64, ne, "f"), _vec(gD, f64, nf, "gD"), _vec(gN, f64, nf, "gN"),
+                None if rhs_out is None else _vec(rhs_out, f64, self.ndof(0), "rhs_out"))
+
     def assemble(self, f, gD, gN, rhs_out=None):
-        self._check(self.lib.hho_assemble(self.h, _ptr(f), _ptr(gD), _ptr(gN), _ptr(rhs_out)))
+        self._check(self.lib.hho_assemble(self.h, *self._data_ptrs(f, gD, gN, rhs_out)))
 
     def assemble_noalloc(self, f, gD, gN, rhs_out=None):
-        self._check(self.lib.hho_assemble_noalloc(self.h, _ptr(f), _ptr(gD), _ptr(gN), _ptr(rhs_out)))
+        self._check(self.lib.hho_assemble_noalloc(self.h, *self._data_ptrs(f, gD, gN, rhs_out)))
 
     def pmg_setup(self, degrees, smooth_its: int = 2, prec="fp64"):
         prec = {"fp64": 0, "fp32": 1, 0: 0, 1: 1}[prec]
@@ -205,17 +229,24 @@ class Context:
         self.degrees = list(degrees)
 
     def vcycle(self, r, z):
-        self._check(self.lib.pmg_vcycle(self.h, _ptr(r), _ptr(z)))
+        n, f64 = self.ndof(0), self._torch.float64
+        pr, pz = _vec(r, f64, n, "r"), _vec(z, f64, n, "z")
+        if pr.value == pz.value:
+            raise ValueError("vcycle: r and z must be different buffers")
+        self._check(self.lib.pmg_vcycle(self.h, pr, pz))
 
     def spmv(self, level, x, y):
-        self._check(self.lib.hho_spmv(self.h, level, _ptr(x), _ptr(y)))
+        n, f64 = self.ndof(level), self._torch.float64
+        self._check(self.lib.hho_spmv(self.h, level, _vec(x, f64, n, "x"), _vec(y, f64, n, "y")))
 
     def spmv_f32(self, level, x, y):
-        self._check(self.lib.hho_spmv_f32(self.h, level, _ptr(x), _ptr(y)))
+        n, f32 = self.ndof(level), self._torch.float32
+        self._check(self.lib.hho_spmv_f32(self.h, level, _vec(x, f32, n, "x"), _vec(y, f32, n, "y")))
 
     def solve(self, x, rtol=1e-8, maxit=1000, restart=50, raise_on_fail=True):
         info = SolveInfo()
-        st = self.lib.hho_solve(self.h, rtol, maxit, restart, _ptr(x), C.byref(info))
+        px = _vec(x, self._torch.float64, self.ndof(0), "x")
+        st = self.lib.hho_solve(self.h, rtol, maxit, restart, px, C.byref(info))
         if raise_on_fail:
             self._check(st)
         return info.as_dict()
@@ -235,7 +266,7 @@ class Context:
         info = SolveInfo()
         its = np.zeros(self.n_prob, dtype=np.int32)
         rr = np.zeros(self.n_prob, dtype=np.float64)
-        st = self.lib.hho_solve_batch(self.h, rtol, maxit, restart, _ptr(x),
+        st = self.lib.hho_solve_batch(self.h, rtol, maxit, restart, _vec(x, self._torch.float64, self.ndof(0), "x"),
                                       its.ctypes.data_as(C.POINTER(C.c_int32)),
                                       rr.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info))
         if raise_on_fail:
@@ -250,7 +281,8 @@ class Context:
 
     def ilu_apply(self, level, v, z):
         """z = (L U)^{-1} v with the level's block ILU(0) factors (FP64)."""
-        self._check(self.lib.hho_ilu_apply(self.h, int(level), _ptr(v), _ptr(z)))
+        n, f64 = self.ndof(int(level)), self._torch.float64
+        self._check(self.lib.hho_ilu_apply(self.h, int(level), _vec(v, f64, n, "v"), _vec(z, f64, n, "z")))
 
     # ---- learned smoother ----
     def mlp_init(self, hidden=128, seed=0):
@@ -303,7 +335,7 @@ class Context:
     def recover(self, x):
         n_loc = self.local_size()
         out = self._empty(n_loc)
-        self._check(self.lib.hho_recover(self.h, _ptr(x), _ptr(out)))
+        self._check(self.lib.hho_recover(self.h, _vec(x, self._torch.float64, self.ndof(0), "x"), _ptr(out)))
         return out
 
     def local_size(self):

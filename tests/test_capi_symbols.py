@@ -35,3 +35,18 @@ def test_null_arguments_return_status_without_gpu():
     assert lib.hho_destroy(out) == 0
     assert lib.hho_ndof(None, 0, None) == 1
     assert lib.hho_destroy(None) == 0
+
+
+def test_binding_refuses_mistyped_or_short_buffers():
+    """The binding checks dtype and length before a pointer reaches the library."""
+    torch = pytest.importorskip("torch")
+    from paper_2009_13840_gb300 import hho
+    x = torch.zeros(10, dtype=torch.float32)
+    with pytest.raises(TypeError):
+        hho._vec(x, torch.float64, 10, "x")
+    with pytest.raises(ValueError):
+        hho._vec(torch.zeros(9, dtype=torch.float64), torch.float64, 10, "x")
+    with pytest.raises(ValueError):
+        hho._vec(None, torch.float64, 10, "x")
+    with pytest.raises(ValueError):  # right type and size, but not a CUDA tensor
+        hho._vec(torch.zeros(10, dtype=torch.float64), torch.float64, 10, "x")
