@@ -293,8 +293,11 @@ static hho_status batch_work(hho_ctx* ctx, int restart) {
     }
     HHO_TRY(build_tiles(ctx, B, ctx->tile_rows));
     if (B->restart != restart) {
+        B->restart = 0;  // until every buffer below exists (a failed allocation must not leave stale ones)
         void* ps[] = {B->V, B->Z, B->w, B->b, B->fsc, B->stat, B->frz};
         for (void* p : ps) dfree(p);
+        B->V = B->Z = B->w = B->b = B->fsc = B->stat = nullptr;
+        B->frz = nullptr;
         const int64_t GT = (gs_layout(restart).total + 7) / 8 * 8;
         HHO_TRY(dalloc(ctx, &B->V, (size_t)(restart + 1) * n));
         HHO_TRY(dalloc(ctx, &B->Z, (size_t)restart * n));

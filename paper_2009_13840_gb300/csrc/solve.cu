@@ -1673,11 +1673,11 @@ hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, 
         return HHO_ERR_ARG;
     }
     if (W->restart != restart) {
-        dfree(W->fV);
-        dfree(W->fZ);
-        dfree(W->fw);
-        dfree(W->fb);
-        dfree(W->fsc);
+        W->restart = 0;  // until every buffer below exists (a failed allocation must not leave stale ones)
+        for (double** p : {&W->fV, &W->fZ, &W->fw, &W->fb, &W->fsc}) {
+            dfree(*p);
+            *p = nullptr;
+        }
         HHO_TRY(dalloc(ctx, &W->fV, (size_t)(restart + 1) * n));
         HHO_TRY(dalloc(ctx, &W->fZ, (size_t)restart * n));
         HHO_TRY(dalloc(ctx, &W->fw, n));
