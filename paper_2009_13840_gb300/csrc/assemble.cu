@@ -449,6 +449,7 @@ hho_status build_smoother(hho_ctx* ctx, int l) {
     }
     dfree(L.dinv);
     dfree(L.minv);
+    L.dinv = L.minv = nullptr;
     HHO_TRY(dalloc(ctx, &L.dinv, (size_t)L.b * L.b * L.nf));
     HHO_TRY(dalloc(ctx, &L.minv, (size_t)L.nP * L.nP * L.ne));
     double* scratch = nullptr;

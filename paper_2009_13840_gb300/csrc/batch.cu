@@ -268,6 +268,9 @@ static hho_status build_tiles(hho_ctx* ctx, BatchWork* B, int tile_rows) {
     dfree(B->tile_r0);
     dfree(B->prob_t0);
     dfree(B->partial);
+    B->tile_prob = B->tile_len = B->prob_t0 = nullptr;
+    B->tile_r0 = nullptr;
+    B->partial = nullptr;
     B->nt = (int)tp.size();
     HHO_TRY(dalloc(ctx, &B->tile_prob, tp.size()));
     HHO_TRY(dalloc(ctx, &B->tile_len, tl.size()));
