@@ -263,6 +263,7 @@ static hho_status build_tiles(hho_ctx* ctx, BatchWork* B, int tile_rows) {
             }
     }
     t0[pr.P] = (int32_t)tp.size();
+    B->tile_rows = 0;  // set again once every tile buffer below exists
     dfree(B->tile_prob);
     dfree(B->tile_len);
     dfree(B->tile_r0);
