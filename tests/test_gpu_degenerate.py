@@ -7,7 +7,8 @@
 * a zero right-hand side (FGMRES returns x = 0 at once);
 * zero smoothing iterations (the V-cycle is transfers and the coarse solve);
 * an element with four faces next to triangles (mixed element shapes);
-* the restart boundary of FGMRES (restart 1, several cycles).
+* the restart boundary of FGMRES (restart 1, several cycles);
+* maxit reached above the tolerance (status HHO_ERR_NOT_CONVERGED).
 """
 import numpy as np
 import pytest
@@ -128,3 +129,21 @@ def test_restart_one(hho_mod):
     info, err = _solve_vs_oracle(hho_mod, mesh, 2, "v", [2, 1, 0], restart=1)
     assert info["rel_residual"] <= 1e-10 and err < 1e-8, (info, err)
     assert info["iterations"] > 1
+
+
+def test_maxit_reached_reports_not_converged(hho_mod):
+    """FGMRES stopped by maxit above the tolerance: HHO_ERR_NOT_CONVERGED (6)
+    with the information filled in, and the context stays usable."""
+    mesh = tri_mesh(8, jitter=0.2, seed=6, neumann_sides=(1,))
+    ctx = hho_mod.Context(mesh, 2, "v")
+    ctx.assemble(*hho_mod.data_arrays(ctx, fields.TrigStokes2D()))
+    ctx.pmg_setup([2, 1, 0])
+    x = torch.empty(ctx.ndof(0), dtype=torch.float64, device="cuda")
+    info = ctx.solve(x, rtol=1e-14, maxit=2, raise_on_fail=False)
+    assert info["status"] == 6 and info["iterations"] == 2 and info["rel_residual"] > 1e-14, info
+    with pytest.raises(hho_mod.HHOError) as exc:
+        ctx.solve(x, rtol=1e-14, maxit=2)
+    assert exc.value.status == 6
+    info = ctx.solve(x, rtol=1e-8)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-8, info
+    ctx.close()
