@@ -44,7 +44,8 @@ typedef enum {
 
 typedef enum { HHO_VCOND = 0, HHO_VPCOND = 1 } hho_cond;
 typedef enum { HHO_FP64 = 0, HHO_FP32 = 1 } hho_prec;
-typedef enum { HHO_SMOOTH_BJACOBI = 0 } hho_smoother;
+/* Preconditioner of the smoother's GMRES, selected by hho_set_option("smoother", v) before pmg_setup. */
+typedef enum { HHO_SMOOTH_BJACOBI = 0, HHO_SMOOTH_ILU = 1 } hho_smoother;
 typedef enum { HHO_NODES_ELEM = 0, HHO_NODES_FACE = 1 } hho_node_set;
 
 typedef struct hho_ctx hho_ctx;
@@ -125,9 +126,10 @@ hho_status hho_assemble(hho_ctx* ctx, const double* d_f, const double* d_gD, con
  * allocated per call.
  *  - No allocation of any kind is made on success (cudaMalloc, cudaFree,
  *    pools or host heap); on failure the message is stored in the context.
- *  - The first call on a device looks up the device address of the array with
- *    that device current; if you capture streams, make that first call before
- *    any capture begins.  The current device must be the context's device.
+ *  - The first call on a context looks up the device address of the array
+ *    with the context's device current and keeps it in the context; if you
+ *    capture streams, make that first call before any capture begins.  The
+ *    current device must be the context's device.
  *  - The work is only enqueued on the context's stream: the call returns
  *    before the right-hand side is ready (hho_assemble synchronises).
  *  - Every call on a device shares the one array.  The kernel clears what it
@@ -142,13 +144,18 @@ hho_status hho_assemble_noalloc(hho_ctx* ctx, const double* d_f, const double* d
 /* Build the p-hierarchy: levels of degrees degrees[0] = k > degrees[1] > ...
  * > degrees[n_levels-1] >= 0, coarse operators by Galerkin block extraction
  * from the fine condensed operator (Sec. 4.2), smoother data (face-block
- * Jacobi with element pressure pivot blocks), and the exact coarse solver
- * (dense inverse up to 10^4 coarse unknowns, two-level substructuring above).  prec: HHO_FP64 (every V-cycle operation in FP64) or
- * HHO_FP32 (mixed precision: level operators, smoother blocks and smoother
- * vectors stored and multiplied in FP32 with FP64 accumulation of every dot
- * product, FP64 Hessenberg algebra and FP64 coarse solve; the outer FGMRES and
- * its operator stay FP64).  smooth_its: GMRES iterations per pre/post
- * smoothing (the paper uses 2). */
+ * Jacobi with element pressure pivot blocks, or block ILU(0) with option
+ * "smoother" = HHO_SMOOTH_ILU), and the exact coarse solver (dense inverse up
+ * to "coarse_dense_max" coarse unknowns, nested-dissection multifrontal solver
+ * above).  prec: HHO_FP64 (every V-cycle operation in FP64) or HHO_FP32
+ * (mixed precision: the level operators, smoother blocks and smoother vectors
+ * of every level above the coarse one are stored and multiplied in FP32, and
+ * the smoother's arithmetic is FP32 too -- dot products are summed in FP32 per
+ * thread, warp and block, the block partials stored as FP64 and added in FP64,
+ * the Givens recurrence and basis scaling in FP32; the coarse solve stays FP64
+ * unless option "coarse_fp32" = 1; the outer FGMRES, its operator and its CGS2
+ * stay FP64).  smooth_its: GMRES iterations per pre/post smoothing (the paper
+ * uses 2). */
 hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, int smooth_its);
 
 /* Solver options.  "coarse_dense_max", "dd_elements", "coarse_fp32" and
@@ -266,6 +273,12 @@ hho_status hho_mlp_weights(hho_ctx* ctx, int set, double* W1, double* b1, double
  * nf x d_in floats holding the BF16-rounded normalised features) and d_s
  * (device, nf floats: the norms s_F). */
 hho_status hho_mlp_features(hho_ctx* ctx, const double* d_r, float* d_X, float* d_s);
+
+/* The learned correction as the finest-level post-smoother applies it (test
+ * hook): d_z[F's rows] += s_F y_F for every face F, y = the network's output
+ * on the normalised BF16 features of d_v (device, ndof(0) doubles each;
+ * element rows of d_z are left unchanged; d_v and d_z may not alias). */
+hho_status hho_mlp_apply(hho_ctx* ctx, const double* d_v, double* d_z);
 
 /* Training set from the FP64 V-cycle (pmg_setup with HHO_FP64, learned
  * smoother off) applied to r0 = S e0 for n_vec (1..4096) seeded white-noise

@@ -272,7 +272,7 @@ __global__ void k_rhs_gather(int64_t nf, int64_t ne, int b, int nP, const int32_
 
 int grid_for(int64_t n, int tpb) {
     int64_t g = (n + tpb - 1) / tpb;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152LL * 32));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sm_count() * 32));
 }
 
 }  // namespace

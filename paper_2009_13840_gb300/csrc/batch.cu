@@ -174,7 +174,7 @@ __global__ void k_zero(int64_t n, double* __restrict__ b) {
         b[i] = 0.0;
 }
 
-int grid1d(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152LL * 32)); }
+int grid1d(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 32)); }
 
 }  // namespace
 
@@ -508,15 +508,10 @@ hho_status batch_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double
 // every candidate runs `reps` V-cycles (and, for a batch, `reps` segmented
 // update kernels) on a fixed input; the fastest is kept.  choice (host, may be
 // NULL) receives {spmv_rows, spmv_grid, tile_rows}.
-hho_status autotune(hho_ctx* ctx, int reps, double* choice) {
+static hho_status autotune_run(hho_ctx* ctx, int reps, double* r, double* z, cudaEvent_t e0, cudaEvent_t e1,
+                               double* choice) {
     const int64_t n = ctx->levels[0].n;
-    double *r = nullptr, *z = nullptr;
-    HHO_TRY(dalloc(ctx, &r, (size_t)n));
-    HHO_TRY(dalloc(ctx, &z, (size_t)n));
     HHO_CUDA(cudaMemcpyAsync(r, ctx->rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    cudaEvent_t e0, e1;
-    HHO_CUDA(cudaEventCreate(&e0));
-    HHO_CUDA(cudaEventCreate(&e1));
     auto time_vcycles = [&](float* ms) -> hho_status {
         HHO_TRY(vcycle(ctx, r, z));  // capture / warm up
         HHO_CUDA(cudaEventRecord(e0, ctx->stream));
@@ -527,7 +522,7 @@ hho_status autotune(hho_ctx* ctx, int reps, double* choice) {
         return HHO_OK;
     };
     const int rows_c[] = {0, 2, 4};
-    const int grid_c[] = {0, 152 * 8, 152 * 16};
+    const int grid_c[] = {0, sm_count() * 8, sm_count() * 16};
     float best = 1e30f;
     int br = ctx->spmv_rows, bg = ctx->spmv_grid;
     for (int rr : rows_c)
@@ -572,16 +567,39 @@ hho_status autotune(hho_ctx* ctx, int reps, double* choice) {
         ctx->tile_rows = bt;
         HHO_TRY(batch_work(ctx, ctx->batch->restart));
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    dfree(r);
-    dfree(z);
     if (choice) {
         choice[0] = br;
         choice[1] = bg;
         choice[2] = bt;
     }
     return HHO_OK;
+}
+
+// The timing buffers and events are released on every path; a failed run
+// restores the kernel choices the context had before.
+hho_status autotune(hho_ctx* ctx, int reps, double* choice) {
+    const int64_t n = ctx->levels[0].n;
+    const int rows0 = ctx->spmv_rows, grid0 = ctx->spmv_grid, tile0 = ctx->tile_rows;
+    double *r = nullptr, *z = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    hho_status st = dalloc(ctx, &r, (size_t)n);
+    if (st == HHO_OK) st = dalloc(ctx, &z, (size_t)n);
+    if (st == HHO_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        ctx->err = "hho_autotune: cudaEventCreate failed";
+        st = HHO_ERR_CUDA;
+    }
+    if (st == HHO_OK) st = autotune_run(ctx, reps, r, z, e0, e1, choice);
+    if (st != HHO_OK) {
+        ctx->spmv_rows = rows0;
+        ctx->spmv_grid = grid0;
+        ctx->tile_rows = tile0;
+        invalidate_graphs(ctx);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dfree(r);
+    dfree(z);
+    return st;
 }
 
 }  // namespace hho

@@ -20,6 +20,19 @@ hho_status device_alloc(hho_ctx* ctx, void** p, size_t bytes) {
     return HHO_OK;
 }
 
+int sm_count() {
+    constexpr int kMaxDev = 64;
+    static int cache[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) dev = -1;
+    if (dev >= 0 && cache[dev] > 0) return cache[dev];
+    int s = 0;
+    if (dev < 0 || cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0)
+        return 1;  // no device answer: a one-SM grid cap is always valid
+    cache[dev] = s;
+    return s;
+}
+
 void dfree(void* p) {
     if (p) cudaFree(p);
 }
@@ -143,6 +156,21 @@ hho_status hho_mlp_weights(hho_ctx* ctx, int set, double* W1, double* b1, double
 hho_status hho_mlp_features(hho_ctx* ctx, const double* d_r, float* d_X, float* d_s) {
     if (!ctx || !d_r || !d_X || !d_s) return HHO_ERR_ARG;
     return mlp_features(ctx, d_r, d_X, d_s);
+}
+
+hho_status hho_mlp_apply(hho_ctx* ctx, const double* d_v, double* d_z) {
+    if (!ctx || !d_v || !d_z) return HHO_ERR_ARG;
+    if (d_v == d_z) {
+        ctx->err = "hho_mlp_apply: d_v and d_z may not alias";
+        return HHO_ERR_ARG;
+    }
+    if (!ctx->learned) {
+        ctx->err = "learned smoother: call hho_mlp_init first";
+        return HHO_ERR_STATE;
+    }
+    HHO_TRY(mlp_apply<double>(ctx, d_v, d_z));
+    HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    return HHO_OK;
 }
 
 hho_status hho_mlp_generate(hho_ctx* ctx, int n_vec, uint64_t seed, int kind, int64_t* n_samples) {

@@ -34,7 +34,7 @@ namespace {
 
 int grid1d(int64_t n, int tpb) {
     int64_t g = (n + tpb - 1) / tpb;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152LL * 64));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sm_count() * 64));
 }
 
 // ---------------------------------------------------------------------------

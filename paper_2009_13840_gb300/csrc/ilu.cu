@@ -42,7 +42,7 @@ struct IluLevel {
 
 namespace {
 
-int g1(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152LL * 32)); }
+int g1(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 32)); }
 
 // dst[p * nf + pos[F]] = src[p * nf + F] for every plane p (face-indexed arrays to colour order)
 __global__ void k_perm_faces(int64_t planes, int64_t nf, const int32_t* __restrict__ pos, const double* __restrict__ src,
@@ -534,10 +534,10 @@ hho_status ilu_setup(hho_ctx* ctx, int l, bool fp32) {
     for (int c = 0; c < ncol; ++c) {
         const int n = I->coff[c + 1] - I->coff[c];
         if (n == 0) continue;
-        k_ilu_face_rows<<<std::min(n, 152 * 16), IB, 0, ctx->stream>>>(v, I->coff[c], I->coff[c + 1], I->lff, I->lfp,
+        k_ilu_face_rows<<<std::min(n, sm_count() * 16), IB, 0, ctx->stream>>>(v, I->coff[c], I->coff[c + 1], I->lff, I->lfp,
                                                                        I->uf, ctx->d_flag);
     }
-    k_ilu_elem_rows<<<(int)std::min<int64_t>(ne, 152 * 16), IB, 0, ctx->stream>>>(v, I->lff, I->lfp, I->lpf, I->lpp,
+    k_ilu_elem_rows<<<(int)std::min<int64_t>(ne, (int64_t)sm_count() * 16), IB, 0, ctx->stream>>>(v, I->lff, I->lfp, I->lpf, I->lpp,
                                                                                  I->uf, I->ue, ctx->d_flag);
     HHO_CUDA(cudaGetLastError());
     int flag = 0;

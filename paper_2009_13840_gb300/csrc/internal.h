@@ -174,6 +174,8 @@ struct hho_ctx {
     int64_t coarse_its_total = 0;
     int* d_flag = nullptr;               // device status word for bounded waits / breakdowns
     int64_t launches = 0;                // kernels launched by the solver entry points
+    double* noalloc_scratch = nullptr;   // device address of the no-alloc assembly array, looked up
+                                         // on this context's first hho_assemble_noalloc call
     int64_t coarse_dense_max = 10000;    // options
     int64_t dd_elements = 0;             // 0 = default per dimension
     int coarse_fp32 = 0;                 // mixed precision: FP32 coarse solve operators
@@ -205,6 +207,8 @@ inline hho_status dalloc(hho_ctx* ctx, T** p, size_t count) {
     return device_alloc(ctx, reinterpret_cast<void**>(p), count * sizeof(T));
 }
 void dfree(void* p);
+// streaming multiprocessors of the current device (queried once per device)
+int sm_count();
 
 // setup.cu
 hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond);

@@ -345,7 +345,7 @@ __global__ void k_sum_losses(int nb, const float* __restrict__ lossp, float* __r
     }
 }
 
-int g1(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152LL * 32)); }
+int g1(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 32)); }
 
 Topo0 topo0(const hho_ctx* ctx, const Learned* M) {
     const LevelMat& L = ctx->levels[0];

@@ -10,8 +10,6 @@
 // the library's device image (every GPU that loads the library holds it until
 // the process exits).  The caller still passes the data arrays and the optional
 // output vector.
-#include <mutex>
-
 #include "internal.h"
 
 namespace {
@@ -19,13 +17,6 @@ namespace {
 // Working memory shared by every call on a device: 2^17 doubles = 1 MiB.
 constexpr int64_t kAssembleScratchDoubles = int64_t(1) << 17;
 static __device__ __align__(256) double g_assemble_scratch[kAssembleScratchDoubles];
-
-// Device address of g_assemble_scratch, looked up once per device with that
-// device current.  In host code the symbol names a host-side stand-in, so the
-// kernels must receive this address, never the symbol itself.
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
 
 }  // namespace
 
@@ -38,24 +29,24 @@ extern "C" hho_status hho_assemble_noalloc(hho_ctx* ctx, const double* d_f, cons
     }
     int dev = -1;
     HHO_CUDA(cudaGetDevice(&dev));
-    if (dev != ctx->device || dev < 0 || dev >= kMaxDevices) {
+    if (dev != ctx->device) {
         ctx->err = "hho_assemble_noalloc: the current device is not the context's device";
         return HHO_ERR_ARG;
     }
-    double* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_scratch_mutex);
-        if (!g_scratch_addr[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_assemble_scratch);
-            if (e != cudaSuccess || !p) {
-                ctx->err = std::string("hho_assemble_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-                return HHO_ERR_CUDA;
-            }
-            g_scratch_addr[dev] = static_cast<double*>(p);
+    // In host code the array's name is a host-side stand-in, so the kernels get
+    // its device address.  It is looked up with the context's device current on
+    // the context's first call and kept in the context: a context created after
+    // a device reset looks it up again in the reloaded module.
+    if (!ctx->noalloc_scratch) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_assemble_scratch);
+        if (e != cudaSuccess || !p) {
+            ctx->err = std::string("hho_assemble_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return HHO_ERR_CUDA;
         }
-        scratch = g_scratch_addr[dev];
+        ctx->noalloc_scratch = static_cast<double*>(p);
     }
+    double* scratch = ctx->noalloc_scratch;
     // The element kernel clears each element's slot of the array before use,
     // so nothing left over from an earlier call is read.
     HHO_TRY(hho::build_rhs_scratch(ctx, d_f, d_gD, d_gN, scratch, kAssembleScratchDoubles));

@@ -1425,9 +1425,7 @@ void gauss_legendre_tables(std::vector<double>& tab) {
 // Host drivers
 // ---------------------------------------------------------------------------
 static int element_grid(int64_t ne) {
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t g = (int64_t)sms * 4;
+    int64_t g = (int64_t)sm_count() * 4;
     return (int)std::min<int64_t>(g, std::max<int64_t>(ne, 1));
 }
 

@@ -59,13 +59,12 @@ namespace {
 constexpr int GMAX = 8192;  // largest grid of any reduction kernel
 constexpr int RT = 256;     // threads per block of the reduction kernels
 constexpr int NVMAX = 8;    // dot products per kernel
-constexpr int FP64_GRID = 2 * 152;  // blocks of the FP64 reduction kernels (two per SM)
 constexpr int EPT = 4;      // elements per thread of the streaming vector kernels (see vgrid)
 constexpr int NCCH = 4;     // combination vectors whose loads a streaming kernel issues together
 
 int grid1d(int64_t n, int tpb) {
     int64_t g = (n + tpb - 1) / tpb;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152LL * 64));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sm_count() * 64));
 }
 
 // grid of the streaming vector kernels: about 4 elements per thread
@@ -1320,7 +1319,8 @@ static void launch_update_dot(hho_ctx* ctx, int64_t n, T* w, const T* V, int64_t
     Workspace* W = ctx->ws;
     // FP64: fewer, longer threads, since every warp's share of the block
     // reductions costs FP64 additions on this part's narrow FP64 pipe
-    const int g = std::is_same<T, double>::value ? std::min(vgrid(n), FP64_GRID) : vgrid(n);
+    // (two blocks per SM)
+    const int g = std::is_same<T, double>::value ? std::min(vgrid(n), 2 * sm_count()) : vgrid(n);
 #define HHO_UPD(NVC)                                                                                               \
     k_update_dot<T, NVC><<<g, RT, 0, ctx->stream>>>(n, w, V, ld, ncomb, coef, sgn, Vd, self, W->partial, W->counter, \
                                                     out, hook, sc, gsl, j)

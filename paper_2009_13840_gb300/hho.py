@@ -28,7 +28,7 @@ SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "hho_assem
            "hho_solve", "hho_recover", "hho_errors", "hho_get_element_schur", "hho_get_level_coo",
            "hho_set_element_schur", "hho_launch_count", "hho_set_option", "hho_destroy",
            "hho_last_error", "hho_set_batch", "hho_solve_batch", "hho_autotune", "hho_mlp_init", "hho_mlp_dims",
-           "hho_mlp_weights", "hho_mlp_features", "hho_mlp_generate", "hho_mlp_train", "hho_mlp_grads",
+           "hho_mlp_weights", "hho_mlp_features", "hho_mlp_apply", "hho_mlp_generate", "hho_mlp_train", "hho_mlp_grads",
            "hho_ilu_apply"]
 
 
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
         "hho_mlp_dims": (C.c_int, [P, C.POINTER(C.c_int32)]),
         "hho_mlp_weights": (C.c_int, [P, C.c_int] + [C.POINTER(C.c_double)] * 4),
         "hho_mlp_features": (C.c_int, [P, P, P, P]),
+        "hho_mlp_apply": (C.c_int, [P, P, P]),
         "hho_mlp_generate": (C.c_int, [P, C.c_int, C.c_uint64, C.c_int, C.POINTER(C.c_int64)]),
         "hho_mlp_train": (C.c_int, [P, C.c_int, C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double)]),
         "hho_mlp_grads": (C.c_int, [P, P, P, C.c_int, C.POINTER(C.c_double)] + [C.POINTER(C.c_double)] * 4),
@@ -220,7 +221,20 @@ class Context:
         self._check(self.lib.hho_assemble(self.h, *self._data_ptrs(f, gD, gN, rhs_out)))
 
     def assemble_noalloc(self, f, gD, gN, rhs_out=None):
-        self._check(self.lib.hho_assemble_noalloc(self.h, *self._data_ptrs(f, gD, gN, rhs_out)))
+        """hho_assemble_noalloc: the library only enqueues the work on the
+        context's stream.  The tensors are marked as in use on that stream (so
+        torch's caching allocator keeps their memory until the kernels have
+        run, even if the caller drops them at once) and the caller's current
+        stream is ordered after the work, so that rhs_out is ready for it.
+        Neither step allocates device memory."""
+        ptrs = self._data_ptrs(f, gD, gN, rhs_out)
+        self._check(self.lib.hho_assemble_noalloc(self.h, *ptrs))
+        cur = self._torch.cuda.current_stream()
+        if cur != self.stream:
+            for t in (f, gD, gN, rhs_out):
+                if t is not None:
+                    t.record_stream(self.stream)
+            cur.wait_stream(self.stream)
 
     def pmg_setup(self, degrees, smooth_its: int = 2, prec="fp64"):
         prec = {"fp64": 0, "fp32": 1, 0: 0, 1: 1}[prec]
@@ -311,6 +325,12 @@ class Context:
         s = self._torch.empty(nf, dtype=self._torch.float32, device="cuda")
         self._check(self.lib.hho_mlp_features(self.h, _ptr(r), _ptr(X), _ptr(s)))
         return X, s
+
+    def mlp_apply(self, v, z):
+        """z[face rows] += the learned correction of v (hho_mlp_apply)."""
+        n, f64 = self.ndof(0), self._torch.float64
+        pv, pz = _vec(v, f64, n, "v"), _vec(z, f64, n, "z")
+        self._check(self.lib.hho_mlp_apply(self.h, pv, pz))
 
     def mlp_generate(self, n_vec, seed=0, kind=2):
         n = C.c_int64()

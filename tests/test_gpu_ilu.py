@@ -17,6 +17,7 @@ from oracle.hho import HHO  # noqa: E402
 from oracle.ilu import BlockILU  # noqa: E402
 from oracle.pmg import PMG, fgmres  # noqa: E402
 from synthetic import tri_mesh, quad_mesh, fields  # noqa: E402
+from parity_util import coarse_kappa, report, vcycle_tol  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -54,14 +55,17 @@ def test_ilu_apply_and_vcycle_match_oracle(hho_mod, name, mk, k, cond):
         z = torch.empty(lev.n, dtype=torch.float64, device="cuda")
         ctx.ilu_apply(l, torch.from_numpy(v).cuda(), z)
         ref = lev.ilu.apply(v)
-        err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
-        assert err < 1e-10, (l, err)
+        err = float(np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref))
+        report(f"ilu-apply {name} k={k} {cond} level={l}", err=err)
+        assert err < 1e-12, (l, err)
     b = rng.standard_normal(ctx.ndof(0))
     z = torch.empty(ctx.ndof(0), dtype=torch.float64, device="cuda")
     ctx.vcycle(torch.from_numpy(b).cuda(), z)
     ref = pmg.apply(b)
-    err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
-    assert err < 1e-9, err
+    err = float(np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref))
+    tol = vcycle_tol(pmg)
+    report(f"vcycle-ilu {name} k={k} {cond}", err=err, tol=tol, kappa_L=coarse_kappa(pmg))
+    assert err <= tol, (err, tol)
     ctx.close()
 
 

@@ -157,3 +157,39 @@ def test_learned_option_needs_a_network(hho_mod):
     with pytest.raises(hho_mod.HHOError):
         ctx.set_option("learned_smoother", 1)
     ctx.close()
+
+
+@pytest.mark.parametrize("cond,k", [("v", 3), ("vp", 2)])
+def test_inference_kernel_matches_oracle_forward(hho_mod, cond, k):
+    """The inference kernel of the finest-level post-smoother against the
+    oracle's forward pass, element by element: z_F += s_F y_F with y the
+    network's output.  The oracle takes the GPU's own BF16 features and norms
+    (which test_features_match_oracle pins against the oracle's gather) and the
+    BF16-rounded weights, so the two sides differ only by FP32 accumulation
+    order; element rows must be left untouched."""
+    mesh = tri_mesh(9, 7, jitter=0.2, seed=5, neumann_sides=(1,))
+    ctx = _ctx(hho_mod, mesh, k, cond)
+    d = ctx.mlp_init(hidden=128, seed=4)
+    W = ctx.mlp_weights()
+    n = ctx.ndof(0)
+    rng = np.random.default_rng(8)
+    v = torch.from_numpy(rng.standard_normal(n)).cuda()
+    z0 = torch.from_numpy(rng.standard_normal(n)).cuda()
+    z = z0.clone()
+    ctx.mlp_apply(v, z)
+    X, s = ctx.mlp_features(v)
+    from oracle.mlp import forward
+    Xg = X.cpu().numpy().astype(np.float64)
+    sg = s.cpu().numpy().astype(np.float64)
+    _, Y = forward(Xg, bf16_round(W["W1"]), np.float32(W["b1"]).astype(np.float64),
+                   bf16_round(W["W2"]), np.float32(W["b2"]).astype(np.float64))
+    nf = mesh.n_face
+    b = 2 * (k + 1)
+    ref = sg[:, None] * Y[:, :b]
+    got = (z - z0).cpu().numpy()
+    corr = got[:nf * b].reshape(nf, b)
+    err = np.abs(corr - ref).max() / np.abs(ref).max()
+    print(f"PARITY mlp_apply cond={cond} k={k} max_rel_err={err:.3e}")
+    assert err <= 1e-5, err
+    assert np.all(got[nf * b:] == 0.0)
+    ctx.close()

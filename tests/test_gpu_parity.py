@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 from oracle.hho import HHO  # noqa: E402
 from oracle.pmg import PMG, fgmres  # noqa: E402
 from synthetic import quad_mesh, tri_mesh, hex_mesh, fields  # noqa: E402
+from parity_util import coarse_kappa, report, vcycle_tol  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -115,13 +116,16 @@ def test_levels_spmv_vcycle(hho_mod, name, mk, cond):
         ctx.spmv(l, torch.from_numpy(x).cuda(), y)
         ref = pmg.levels[l].S @ x
         assert _rel(y.cpu().numpy(), ref) < 1e-13
+    tol = vcycle_tol(pmg)
+    worst = 0.0
     for trial in range(2):
         b = rng.standard_normal(ctx.ndof(0))
         z = torch.empty_like(torch.from_numpy(b)).cuda()
         ctx.vcycle(torch.from_numpy(b).cuda(), z)
         ref = pmg.apply(b)
-        err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
-        assert err < 1e-10, err
+        worst = max(worst, float(np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)))
+    report(f"vcycle2d {name} k=3 {cond}", err=worst, tol=tol, kappa_L=coarse_kappa(pmg))
+    assert worst <= tol, (worst, tol)
     ctx.close()
 
 
@@ -210,6 +214,8 @@ def test_substructured_coarse_solver(hho_mod, name, mk, cond):
     pmg = PMG(h, degrees, coarse="splu")
     rng = np.random.default_rng(1)
     null = h.null_vector()
+    tol = vcycle_tol(pmg)
+    worst = 0.0
     for trial in range(2):
         b = rng.standard_normal(ctx.ndof(0))
         if null is not None:
@@ -221,8 +227,9 @@ def test_substructured_coarse_solver(hho_mod, name, mk, cond):
         if null is not None:
             zz = zz - (null @ zz) * null
             ref = ref - (null @ ref) * null
-        err = np.linalg.norm(zz - ref) / np.linalg.norm(ref)
-        assert err < 1e-10, err
+        worst = max(worst, float(np.linalg.norm(zz - ref) / np.linalg.norm(ref)))
+    report(f"vcycle2d-multifrontal {name} k=3 {cond}", err=worst, tol=tol, kappa_L=coarse_kappa(pmg))
+    assert worst <= tol, (worst, tol)
     # single-level hierarchy: the V-cycle is the exact coarse solve itself
     ctx.pmg_setup([3])
     b = pmg.levels[0].S @ rng.standard_normal(ctx.ndof(0))

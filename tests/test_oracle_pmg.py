@@ -183,3 +183,66 @@ def test_vcycle_against_dense_brute_force(cond):
     ref = vcycle(0, b)
     z = pmg.apply(b)
     assert np.linalg.norm(z - ref) < 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("cond", ["vp", "v"])
+@pytest.mark.parametrize("mk", [lambda: tri_mesh(4, 3, jitter=0.2, seed=6, neumann_sides=(1,)),
+                                lambda: quad_mesh(3, 3, jitter=0.15, seed=2)])
+def test_jacobi_pivot_blocks_equal_ilu_pivots_without_face_coupling(cond, mk):
+    """The smoother's element pressure pivot M_T (reading of the ILU smoother of
+    Sec. 5.2.2) checked by a different algorithm: block ILU(0) (faces before
+    pressures, IKJ elimination) applied to S with every face-face block off the
+    diagonal set to zero performs exactly the eliminations that define M_T, so
+    its element pivot blocks must be M_T and its face pivots the face diagonal
+    blocks.  A sign slip or a dropped face in Level._jacobi fails this."""
+    import scipy.sparse as sps
+    from oracle.ilu import BlockILU
+    h = HHO(mk(), 2, cond)
+    pmg = PMG(h, [2, 1], coarse="lu")
+    for lev in pmg.levels:
+        S = lev.S.tolil(copy=True)
+        nfb = lev.nf * lev.b
+        A = S.toarray()
+        for F in range(lev.nf):
+            for G in range(lev.nf):
+                if F != G:
+                    A[F * lev.b:(F + 1) * lev.b, G * lev.b:(G + 1) * lev.b] = 0.0
+        ilu = BlockILU(sps.csr_matrix(A), h.mesh, lev.b, lev.nP)
+        scale = np.abs(A).max()
+        for F in range(lev.nf):
+            piv = ilu.blocks[(("f", F), ("f", F))]
+            assert np.abs(piv - A[F * lev.b:(F + 1) * lev.b, F * lev.b:(F + 1) * lev.b]).max() == 0.0
+            assert np.abs(np.linalg.inv(piv) - lev.Dinv[F]).max() <= 1e-12 * np.abs(lev.Dinv[F]).max()
+        for T in range(lev.ne):
+            piv = ilu.blocks[(("e", T), ("e", T))]
+            M = np.linalg.inv(lev.Minv[T])
+            assert np.abs(piv - M).max() <= 1e-12 * scale, (T, piv, M)
+        assert nfb + lev.ne * lev.nP == lev.n
+
+
+@pytest.mark.parametrize("cond", ["vp", "v"])
+def test_sparse_lu_coarse_branch_equals_dense_rank_one_lu(cond):
+    """The sparse direct coarse solve (alpha pin on one mean pressure, then
+    projection on the complement of the pressure kernel n) against the dense LU
+    with the rank-one term alpha n n^T, on an all-Dirichlet level: after
+    projecting both on the complement of n they agree, solve S c = d for every
+    d orthogonal to n, and are orthogonal to n themselves."""
+    h = HHO(quad_mesh(4, 3, jitter=0.15, seed=9), 2, cond)
+    degrees = [2, 1, 0]
+    dense = PMG(h, degrees, coarse="lu")
+    sparse = PMG(h, degrees, coarse="splu")
+    L = dense.levels[-1]
+    n = dense.null
+    assert n is not None and sparse.null is not None
+    S = L.S.toarray()
+    assert np.linalg.norm(S @ n) <= 1e-12 * np.abs(S).max()  # n spans the kernel
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        d = rng.standard_normal(L.n)
+        d -= (n @ d) * n
+        c_dense = dense.coarse_solve(d)
+        c_dense = c_dense - (n @ c_dense) * n
+        c_sparse = sparse.coarse_solve(d)
+        assert abs(n @ c_sparse) <= 1e-12 * np.linalg.norm(c_sparse)
+        assert np.linalg.norm(c_sparse - c_dense) <= 1e-10 * np.linalg.norm(c_dense)
+        assert np.linalg.norm(S @ c_sparse - d) <= 1e-11 * np.linalg.norm(d)
