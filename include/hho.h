@@ -158,14 +158,25 @@ hho_status hho_assemble_noalloc(hho_ctx* ctx, const double* d_f, const double* d
  * uses 2). */
 hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, int smooth_its);
 
-/* Solver options.  "coarse_dense_max", "dd_elements", "coarse_fp32" and
- * "smoother" take effect at the next pmg_setup.  Keys:
+/* Solver options.  "coarse_dense_max", "mf_leaf", "coarse_twolevel",
+ * "dd_elements", "coarse_fp32" and "smoother" take effect at the next
+ * pmg_setup.  Keys:
  *   "coarse_dense_max"  largest coarse level solved by the dense inverse
  *                       (default 10000 unknowns); larger coarse levels use
  *                       the substructured direct solver
+ *   "mf_leaf"           elements per leaf of the nested-dissection tree of
+ *                       the multifrontal coarse solver (default 16 in 2D, 8 in
+ *                       3D); pmg_setup returns HHO_ERR_UNSUPPORTED when one
+ *                       front exceeds the shared-memory staging of its solve
+ *                       kernels (about 28000 FP64 unknowns)
+ *   "coarse_twolevel"   1: coarse levels above "coarse_dense_max" use the
+ *                       two-level substructured solver (subdomain interiors
+ *                       eliminated, dense interface inverse; its setup grows
+ *                       with the cube of the interface size) instead of the
+ *                       multifrontal one; 0 (default): multifrontal
  *   "dd_elements"       target number of elements per subdomain of the
- *                       substructured coarse solver (default 128 in 2D, 64 in
- *                       3D; rounded so the subdomain count is a power of two);
+ *                       two-level solver (default 128 in 2D, 64 in 3D;
+ *                       rounded so the subdomain count is a power of two);
  *                       pmg_setup returns HHO_ERR_UNSUPPORTED when a subdomain
  *                       has more than 5632 interior unknowns (the interior
  *                       solve stages them in 48 KB of shared memory)

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhho.so")
-SOURCES = ["setup.cu", "assemble.cu", "solve.cu", "coarse.cu", "capi.cu", "noalloc.cu", "batch.cu", "learned.cu", "ilu.cu"]
+SOURCES = ["setup.cu", "assemble.cu", "solve.cu", "coarse.cu", "capi.cu", "noalloc.cu", "batch.cu", "learned.cu", "ilu.cu", "multifrontal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

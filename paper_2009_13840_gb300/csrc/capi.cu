@@ -331,12 +331,17 @@ hho_status hho_set_option(hho_ctx* ctx, const char* key, double value) {
         else ctx->spmv_grid = (int)value;
         return HHO_OK;
     }
+    if (k == "coarse_twolevel") {
+        ctx->coarse_twolevel = value != 0.0 ? 1 : 0;
+        return HHO_OK;
+    }
     if (!(value > 0.0) || value > 9.0e18) {
         ctx->err = "hho_set_option: value must be positive";
         return HHO_ERR_ARG;
     }
     if (k == "coarse_dense_max") ctx->coarse_dense_max = (int64_t)value;
     else if (k == "dd_elements") ctx->dd_elements = (int64_t)value;
+    else if (k == "mf_leaf") ctx->mf_leaf = (int64_t)value;
     else {
         ctx->err = "hho_set_option: unknown key " + k;
         return HHO_ERR_ARG;

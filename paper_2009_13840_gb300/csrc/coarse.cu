@@ -443,7 +443,8 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ src, float* __res
 }  // namespace
 
 struct CoarseSolver {
-    int kind = 0;  // 0 dense inverse, 1 substructuring
+    int kind = 0;  // 0 dense inverse, 1 two-level substructuring, 2 multifrontal (multifrontal.cu)
+    MFSolver* mf = nullptr;
     int64_t n = 0;
     double* Ainv = nullptr;   // dense path (n x n) or interface inverse (nG x nG)
     bool project = false;     // remove the pressure kernels of the problems that have one
@@ -477,6 +478,7 @@ void coarse_free(hho_ctx* ctx) {
                   C->Ainv32, C->AinvT32, C->XT32, C->AGI32, C->dI32, C->yI32, C->rG32, C->cG32,
                   C->g_prob0, C->g_off, C->g_n, C->g_row};
     for (void* p : ps) dfree(p);
+    mf_free(C->mf);
     delete C;
     ctx->coarse = nullptr;
 }
@@ -1092,10 +1094,23 @@ hho_status coarse_setup(hho_ctx* ctx) {
         }
         HHO_CUDA(cudaStreamSynchronize(ctx->stream));
     }
+    if (ctx->prec == HHO_FP32 && ctx->coarse_fp32 && ctx->levels.size() > 1 && C->kind == 2) {
+        HHO_TRY(mf_make_f32(ctx, C->mf));
+        HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
     return HHO_OK;
 }
 
-bool coarse_has_f32(const hho_ctx* ctx) { return ctx->coarse && ctx->coarse->Ainv32; }
+bool coarse_has_f32(const hho_ctx* ctx) {
+    return ctx->coarse && (ctx->coarse->Ainv32 || mf_has_f32(ctx->coarse->mf));
+}
+
+int64_t coarse_solve_bytes(const hho_ctx* ctx, int value_bytes) {
+    const CoarseSolver* C = ctx->coarse;
+    if (!C) return 0;
+    if (C->kind == 2) return mf_solve_bytes(C->mf, value_bytes);
+    return (C->nAinv + C->nAinvT + C->nXT + C->nAGI) * value_bytes;
+}
 
 static hho_status coarse_build(hho_ctx* ctx) {
     coarse_free(ctx);
@@ -1138,8 +1153,13 @@ static hho_status coarse_build(hho_ctx* ctx) {
         dfree(A);
         return st;
     }
-    C->kind = 1;
-    return build_dd(ctx, C);
+    if (ctx->coarse_twolevel) {
+        C->kind = 1;
+        return build_dd(ctx, C);
+    }
+    C->kind = 2;
+    const int64_t leaf = ctx->mf_leaf > 0 ? ctx->mf_leaf : (ctx->disc.d == 2 ? 16 : 8);
+    return mf_build(ctx, leaf, &C->mf);
 }
 
 template <typename T>
@@ -1148,6 +1168,12 @@ static hho_status coarse_apply_t(hho_ctx* ctx, CoarseSolver* C, const T* Ainv, c
     if (C->kind == 0) {
         k_gemv<T><<<grid1d(C->n * 32, 256), 256, 0, ctx->stream>>>(Ainv, C->n, d, c);
         ++ctx->launches;
+    } else if (C->kind == 2) {
+        HHO_TRY(mf_apply<T>(ctx, C->mf, d, c));
+        if (C->project) {
+            const LevelMat& L = ctx->levels.back();
+            HHO_TRY(null_project<T>(ctx, L.nf * L.b, L.nP, c));
+        }
     } else {
         k_dd_gather<T><<<grid1d(C->nIt, 256), 256, 0, ctx->stream>>>(C->nIt, C->flat_glob, d, dI);
         {
@@ -1185,7 +1211,7 @@ hho_status coarse_apply(hho_ctx* ctx, const double* d, double* c) {
 
 hho_status coarse_apply_f32(hho_ctx* ctx, const float* d, float* c) {
     CoarseSolver* C = ctx->coarse;
-    if (!C->Ainv32) {
+    if (!coarse_has_f32(ctx)) {
         ctx->err = "coarse solve: no FP32 copy of the coarse operators";
         return HHO_ERR_STATE;
     }

@@ -129,6 +129,7 @@ struct CoarseSolver;  // coarse-level solver (coarse.cu)
 struct BatchWork;     // segmented FGMRES state of a batch (batch.cu)
 struct Learned;       // learned block smoother (learned.cu)
 struct IluLevel;      // block ILU(0) factors of one level (ilu.cu)
+struct MFSolver;      // multifrontal coarse solver (multifrontal.cu)
 
 // Partition of the mesh into independent problems (a disjoint union): problem
 // p owns faces [face_off[p], face_off[p+1]) and elements [elem_off[p],
@@ -179,6 +180,9 @@ struct hho_ctx {
     int64_t coarse_dense_max = 10000;    // options
     int64_t dd_elements = 0;             // 0 = default per dimension
     int coarse_fp32 = 0;                 // mixed precision: FP32 coarse solve operators
+    int coarse_twolevel = 0;             // coarse levels above coarse_dense_max: 1 two-level substructuring,
+                                         // 0 multifrontal (default)
+    int64_t mf_leaf = 0;                 // elements per leaf of the multifrontal tree (0 = default per dimension)
     bool use_graphs = true;              // replay captured V-cycles
     int spmv_rows = 0;                   // rows per thread of the operator kernels (0 = automatic)
     int spmv_grid = 0;                   // blocks of the operator kernels (0 = automatic)
@@ -274,4 +278,14 @@ hho_status coarse_apply(hho_ctx* ctx, const double* d, double* c);
 bool coarse_has_f32(const hho_ctx* ctx);
 hho_status coarse_apply_f32(hho_ctx* ctx, const float* d, float* c);
 void coarse_free(hho_ctx* ctx);
+// bytes of the stored operators one coarse solve reads
+int64_t coarse_solve_bytes(const hho_ctx* ctx, int value_bytes);
+// multifrontal.cu
+hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out);
+hho_status mf_make_f32(hho_ctx* ctx, MFSolver* S);
+bool mf_has_f32(const MFSolver* S);
+int64_t mf_solve_bytes(const MFSolver* S, int value_bytes);
+template <typename T>
+hho_status mf_apply(hho_ctx* ctx, MFSolver* S, const T* d, T* c);
+void mf_free(MFSolver* S);
 }  // namespace hho

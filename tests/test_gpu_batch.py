@@ -64,11 +64,12 @@ def _solve_batch(hho_mod, ms, flds, k, cond, prec="fp64", options=(), rtol=1e-10
 
 
 @pytest.mark.parametrize("cond", ["v", "vp"])
-@pytest.mark.parametrize("coarse", ["dense", "substructured"])
+@pytest.mark.parametrize("coarse", ["dense", "multifrontal", "twolevel"])
 def test_batch_matches_oracle_per_problem(hho_mod, cond, coarse):
     ms, flds = _problems()
     k = 2
-    opts = () if coarse == "dense" else (("coarse_dense_max", 50), ("dd_elements", 16))
+    opts = {"dense": (), "multifrontal": (("coarse_dense_max", 50), ("mf_leaf", 4)),
+            "twolevel": (("coarse_dense_max", 50), ("coarse_twolevel", 1), ("dd_elements", 16))}[coarse]
     ctx, m, fo, eo, x, info, its, rr = _solve_batch(hho_mod, ms, flds, k, cond, options=opts)
     ref = _oracle_solutions(ms, flds, k, cond)
     b = 2 * (k + 1)
