@@ -2,20 +2,26 @@
 """Benchmark: FGMRES + p-multilevel V-cycle solve of the statically condensed
 HHO Stokes system on one GB300 (arXiv 2009.13840, Secs. 3-4).
 
-Workload (one "step" = one full solve to a 1e-8 relative residual with the
-assembled operator and RHS resident in HBM): 128 x 128 squares split into
-32768 triangles, interior vertices jittered by +-0.2h (SplitMix64 seed 0),
-Dirichlet on x=0, y=0, y=1 and Neumann on x=1, manufactured field
-u = (sin(pi x) cos(pi y), -cos(pi x) sin(pi y)), p = sin(2 pi x) sin(2 pi y),
-k = 3, v-cond static condensation, p-levels 3-2-1-0.  The headline solve uses
-the mixed-precision V-cycle (FP32 level operators, smoother vectors, dot
-products and coarse solve; FP64 only for stored scalars) inside FP64 FGMRES;
-the plain FP64 V-cycle is timed on the same problem for the speedup.
+Default workload (one "step" = one full solve to a 1e-8 relative residual with
+the assembled operator and right-hand side resident in HBM): the unit cube
+split into 32^3 hexahedra with planar faces, grid planes jittered by +-0.15h
+(SplitMix64 seed 0), all-Dirichlet, manufactured field
+u = curl(sin(pi x) sin(pi y) sin(pi z) (1,1,1)), p = cos(pi x) cos(pi y)
+cos(pi z), k = 3, velocity-pressure (v&p) static condensation, p-levels
+3-2-1-0 (3.07 M condensed unknowns).  The headline solve uses the
+mixed-precision V-cycle (FP32 level operators, smoother vectors and
+arithmetic) inside FP64 FGMRES; the plain FP64 V-cycle is timed on the same
+problem for the speedup.  Other workloads: --workload c2 (128 x 128 jittered
+triangles, mixed boundary conditions, k = 3, velocity-only condensation),
+c1 (16 x 16 quadrilaterals, all-Dirichlet, k = 3, v&p, FP64), sweep (the
+128 x 128 triangle mesh over k = 1..5, both condensations, FP64 and FP32
+V-cycles; one JSON line per case), batch, learned.
 
-Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
-bounded sample of the same workload family instead.  ``--probe-spmv`` only
-runs three FP32 and one FP64 level-0 operator launches on the workload (the
-small command for ncu captures of the roofline kernel) and prints nothing.
+Prints one JSON line (sweep: one per case).  ``--impl reference`` times the
+FP64 CPU oracle on a bounded sample of the same workload family instead.
+``--probe-spmv`` only runs three FP32 and one FP64 level-0 operator launches on
+the workload (the small command for ncu captures of the roofline kernel) and
+prints nothing.
 """
 from __future__ import annotations
 
@@ -34,10 +40,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FGMRES+p-MG time & DOFs/s to 1e-8 rel. residual; V-cycle GB/s vs HBM peak"
 UNIT = "DOF/s"
-# DRAM bytes (read + write) of one FP32 level-0 operator launch on the default
-# workload, from the ncu capture summarised in
-# profiles/k_spmv_level0_tri128_k3_vcond.md (kernel unchanged since)
+# DRAM bytes (read + write) of one FP32 level-0 operator launch, from the ncu
+# captures summarised under profiles/ (kernels unchanged since); keyed by
+# (mesh, n, k, condensation)
 SPMV_F32_TRAFFIC = {("tri", 128, 3, "v"): 144286208 + 3245056}
+
+# the named workloads (BASELINE configurations); command-line values override
+SPECS = {
+    "c3": dict(mesh="hex", n=32, k=3, cond="vp", prec="fp32", coarse_fp32=1, sample_n=4),
+    "c2": dict(mesh="tri", n=128, k=3, cond="v", prec="fp32", coarse_fp32=1, sample_n=24),
+    "c1": dict(mesh="quad", n=16, k=3, cond="vp", prec="fp64", coarse_fp32=0, sample_n=16),
+}
 
 
 def parse():
@@ -46,41 +59,56 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "sweep", "batch", "learned"],
+                    help="c3: 32^3 jittered hexahedra, k=3, v&p (default); c2: 128x128 jittered triangles, k=3, "
+                         "v-cond; c1: 16x16 quadrilaterals, k=3, v&p, FP64; sweep: the c2 mesh over k=1..5, both "
+                         "condensations, FP64 and FP32 V-cycles; batch: many independent small problems; learned: "
+                         "the learned smoother against the plain one")
+    ap.add_argument("--mesh", default=None, choices=["tri", "hex", "quad"],
+                    help="override the workload's mesh family (tri: n x n squares split into triangles; hex: n^3 "
+                         "jittered hexahedra; quad: n x n quadrilaterals)")
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--cond", default=None, choices=["v", "vp"])
+    ap.add_argument("--prec", default=None, choices=["fp32", "fp64"], help="V-cycle precision of the headline")
+    ap.add_argument("--coarse-fp32", type=int, default=None, choices=[0, 1],
+                    help="FP32 coarse solve inside the FP32 V-cycle")
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "ilu"],
                     help="preconditioner of the smoother's GMRES: block Jacobi or block ILU(0)")
-    ap.add_argument("--mesh", default="tri", choices=["tri", "hex"],
-                    help="tri: n x n squares split into triangles (2D); hex: n^3 jittered hexahedra (3D)")
-    ap.add_argument("--k", type=int, default=3)
-    ap.add_argument("--cond", default="v", choices=["v", "vp"])
     ap.add_argument("--rtol", type=float, default=1e-8)
-    ap.add_argument("--sample-n", type=int, default=24, help="mesh size of the CPU-oracle sample")
+    ap.add_argument("--sample-n", type=int, default=None, help="mesh size of the CPU-oracle sample")
+    ap.add_argument("--oracle-faces", type=int, default=12,
+                    help="faces of the full-size solution whose residual rows the oracle recomputes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of the headline")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--probe-spmv", action="store_true", help="three FP32 and one FP64 level-0 operator launches")
-    ap.add_argument("--coarse-fp32", type=int, default=1, choices=[0, 1],
-                    help="FP32 coarse solve inside the FP32 V-cycle (velocity-only condensation default)")
-    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "learned"],
-                    help="solve: the 128x128 triangle workload; batch: many independent small problems; "
-                         "learned: the learned smoother against the plain one")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed solves with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--learned-train-n", type=int, default=32, help="mesh size the learned smoother is trained on")
     ap.add_argument("--batch-n", type=int, default=256, help="problems in the batched workload")
     ap.add_argument("--batch-seed", type=int, default=12345)
     ap.add_argument("--batch-cond", default="v", choices=["v", "vp"])
     ap.add_argument("--batch-compare", type=int, default=16,
                     help="problems of the batch also solved one by one for the batching speedup (0: skip)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    spec = SPECS.get(args.workload, SPECS["c2"] if args.workload in ("sweep", "learned") else SPECS["c3"])
+    for key in ("mesh", "n", "k", "cond", "prec", "sample_n"):
+        if getattr(args, key) is None:
+            setattr(args, key, spec[key])
+    if args.coarse_fp32 is None:
+        args.coarse_fp32 = spec["coarse_fp32"]
+    return args
 
 
-MESH = "tri"
-
-
-def workload(n, k, cond, mesh_kind=None):
-    from synthetic import tri_mesh, hex_mesh, fields
-    if (mesh_kind or MESH) == "hex":
+def workload(n, k, cond, mesh_kind):
+    """(mesh, field, name) of a workload family member (seeded, synthetic)."""
+    from synthetic import tri_mesh, hex_mesh, quad_mesh, fields
+    if mesh_kind == "hex":
         mesh = hex_mesh(n, jitter=0.15, seed=0)
         return mesh, fields.CurlStokes3D(), f"hex{n}^3-jit0.15-seed0-allDirichlet k={k} {cond}-cond levels {k}..0"
+    if mesh_kind == "quad":
+        mesh = quad_mesh(n, jitter=0.0)
+        return mesh, fields.TrigStokes2D(), f"quad{n}x{n}-uniform-allDirichlet k={k} {cond}-cond levels {k}..0"
     mesh = tri_mesh(n, jitter=0.2, seed=0, neumann_sides=(1,))
     return mesh, fields.TrigStokes2D(), f"tri{n}x{n}-jit0.2-seed0-mixedBC k={k} {cond}-cond levels {k}..0"
 
@@ -163,68 +191,128 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def oracle_sample(n_s, k, cond, rtol):
-    """The oracle as it stands on a bounded sample: returns (DOF/s, ndof, its, seconds).
-    3D samples are capped at 5^3 hexahedra (a bounded CPU run)."""
-    from oracle.hho import HHO
-    from oracle.pmg import PMG, fgmres
-    if MESH == "hex":
-        n_s = min(n_s, 5)
-    mesh, fld, _ = workload(n_s, k, cond)
-    h = HHO(mesh, k, cond)
-    rhs = h.assemble_rhs(*h.data_values(fld))
-    pmg = PMG(h, list(range(k, -1, -1)))
-    t0 = time.perf_counter()
-    x, its, rr = fgmres(h.S, pmg.apply, rhs, rtol=rtol, null=h.null_vector())
-    dt = time.perf_counter() - t0
-    return h.ndof / dt, h.ndof, its, dt
-
-
-def cpu_threads():
+def one_thread():
+    """Context limiting the BLAS pools to one thread: the oracle's loops are
+    serial Python and its sparse products single-threaded, so the CPU baseline
+    is stated as what it is, a one-core run."""
     try:
         import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        return max([i.get("num_threads", 1) for i in info] + [1])
+        return threadpoolctl.threadpool_limits(1)
     except Exception:
-        return os.cpu_count() or 1
+        import contextlib
+        return contextlib.nullcontext()
+
+
+def oracle_sample(args, steps=1):
+    """The oracle as it stands on a bounded sample of the workload family: the
+    hierarchy is built once (timed as setup), then `steps` FGMRES solves are
+    timed.  Returns (DOF/s of the last solve, ndof, its, solve seconds, setup
+    seconds)."""
+    from oracle.hho import HHO
+    from oracle.pmg import PMG, fgmres
+    n_s = args.sample_n
+    mesh, fld, _ = workload(n_s, args.k, args.cond, args.mesh)
+    with one_thread():
+        t0 = time.perf_counter()
+        h = HHO(mesh, args.k, args.cond)
+        rhs = h.assemble_rhs(*h.data_values(fld))
+        pmg = PMG(h, list(range(args.k, -1, -1)))
+        t_setup = time.perf_counter() - t0
+        rates = []
+        for _ in range(max(1, steps)):
+            t0 = time.perf_counter()
+            x, its, rr = fgmres(h.S, pmg.apply, rhs, rtol=args.rtol, null=h.null_vector())
+            dt = time.perf_counter() - t0
+            rates.append((h.ndof / dt, dt))
+    return rates, h.ndof, its, t_setup
+
+
+def sample_name(args):
+    return {"hex": f"hex{args.sample_n}^3", "quad": f"quad{args.sample_n}x{args.sample_n}",
+            "tri": f"tri{args.sample_n}x{args.sample_n}"}[args.mesh]
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    vals = []
-    info = None
-    for i in range(args.warmup + args.steps):
-        v, ndof, its, dt = oracle_sample(args.sample_n, args.k, args.cond, args.rtol)
-        if i >= args.warmup:
-            vals.append(v)
-            info = (ndof, its, dt)
-    value = float(np.mean(vals))
-    ndof, its, dt = info
-    sample = (f"oracle FGMRES+p-MG solve on tri{args.sample_n}x{args.sample_n} (same family as the "
-              f"workload, {ndof} DOFs, {its} iterations, {dt:.2f} s per solve); setup excluded")
+    rates, ndof, its, t_setup = oracle_sample(args, steps=args.warmup + args.steps)
+    timed = rates[args.warmup:] or rates[-1:]
+    value = float(np.mean([r[0] for r in timed]))
+    dt = float(np.mean([r[1] for r in timed]))
+    full = workload(args.n, args.k, args.cond, args.mesh)
+    sample = (f"oracle FGMRES+p-MG solve on {sample_name(args)} (same family as the workload; {ndof} DOFs, "
+              f"{its} iterations, {dt:.2f} s per solve, {t_setup:.1f} s setup excluded), one thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload(args.n, args.k, args.cond)[2], "sample": f"tri{args.sample_n}"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+            "config": {"workload": full[2], "sample": sample_name(args)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def spmv_bytes(ctx, level=0, value_bytes=8):
-    """Algorithmic bytes of one level SpMV: stored values, column indices, x read, y written."""
-    r, c, v = ctx.level_coo(level)
-    n = ctx.ndof(level)
-    m = ctx.mesh
-    nf, ne = m.n_face, m.n_elem
-    N = np.diff(m.elem_face_ptr)
-    fe = m.face_elem
-    # face slots per face row: 1 + sum over its elements of (|F_T| - 1)
+def _dimP(nv, deg):
+    if deg < 0:
+        return 0
+    return {0: 1, 1: deg + 1, 2: (deg + 1) * (deg + 2) // 2, 3: (deg + 1) * (deg + 2) * (deg + 3) // 6}[nv]
+
+
+def level_counts(mesh, k_l, cond):
+    """(n, stored values z, index bytes, Jacobi values J, b, nP) of the level of
+    degree k_l: the face-block operator of the condensed system (stored blocks
+    of every face row and element row) and the block-Jacobi data."""
+    d = mesh.dim
+    b = d * _dimP(d - 1, k_l)
+    nP = 1 if cond == "vp" else _dimP(d, k_l)
+    nf, ne = mesh.n_face, mesh.n_elem
+    N = np.diff(mesh.elem_face_ptr)
+    fe = mesh.face_elem
     nsl = 1 + np.where(fe[:, 0] >= 0, N[fe[:, 0]] - 1, 0) + np.where(fe[:, 1] >= 0, N[np.maximum(fe[:, 1], 0)] - 1, 0)
-    idx_bytes = 4 * (int(nsl.sum()) + nf + 2 * nf + int(N.sum()) + ne)
-    return v.size * value_bytes + idx_bytes + 2 * n * value_bytes
+    z = b * b * int(nsl.sum()) + 2 * b * nP * int(N.sum()) + ne * nP * nP
+    idx = 4 * (int(nsl.sum()) + nf + 2 * nf + int(N.sum()) + ne)
+    J = nf * b * b + ne * nP * nP
+    return nf * b + ne * nP, z, idx, J, b, nP
+
+
+def spmv_bytes(mesh, k_l, cond, value_bytes):
+    """Algorithmic bytes of one level operator product: stored values, column
+    indices, x read, y written."""
+    n, z, idx, _, _, _ = level_counts(mesh, k_l, cond)
+    return z * value_bytes + idx + 2 * n * value_bytes
+
+
+def vcycle_bytes(mesh, degrees, cond, s, coarse_values, coarse_s, m=2):
+    """Algorithmic bytes of one V-cycle (Algorithm MG_V with m GMRES smoothing
+    steps): per level above the coarse one (2m+3) operator products (pre/post
+    Arnoldi steps, the post-smoother's initial residual, the fused defect),
+    2m block-Jacobi applies, 6m n_l vector passes of orthogonalisation and
+    updates, 3 n_l of transfers; the coarse solve reads its stored operators
+    once and two vectors."""
+    tot = 0
+    for kl in degrees[:-1]:
+        n, z, idx, J, b, nP = level_counts(mesh, kl, cond)
+        tot += (2 * m + 3) * (z * s + idx + 2 * n * s)
+        tot += 2 * m * (J * s + 2 * n * s)
+        tot += 6 * m * n * s + 3 * n * s
+    nL = level_counts(mesh, degrees[-1], cond)[0]
+    tot += coarse_values * coarse_s + 2 * nL * coarse_s
+    return int(tot)
+
+
+def oracle_check(mesh, k, cond, fld, x, faces, seed=0):
+    """Residual rows b - S x of the full-size solution at sampled faces (and the
+    kept pressures of their elements), recomputed by the oracle from its own
+    local systems (oracle/sampled.py), relative to the right-hand side on the
+    same rows."""
+    from oracle.sampled import residual_rows, sample_interior_faces
+    with one_thread():
+        t0 = time.perf_counter()
+        sf = sample_interior_faces(mesh, faces, seed)
+        rows, r, b = residual_rows(mesh, k, cond, fld, x, sf)
+        dt = time.perf_counter() - t0
+    return {"faces": int(len(sf)), "rows": int(len(rows)), "rel_residual_rows": float(np.linalg.norm(r) / np.linalg.norm(b)),
+            "max_abs_residual_over_max_abs_rhs": float(np.abs(r).max() / np.abs(b).max()), "seconds": dt}
 
 
 def run_ours(args):
@@ -236,13 +324,21 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2009_13840_gb300 import build, hho
     build.build()
-    mesh, fld, wname = workload(args.n, args.k, args.cond)
+    mesh, fld, wname = workload(args.n, args.k, args.cond, args.mesh)
+    degrees = list(range(args.k, -1, -1))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         ctx = hho.Context(mesh, args.k, args.cond, stream=stream)
-        f, gD, gN = hho.data_arrays(ctx, fld)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
+        f, gD, gN = hho.data_arrays(ctx, fld)  # input preparation (host evaluation of the data)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         ctx.assemble(f, gD, gN)
-        degrees = list(range(args.k, -1, -1))
+        torch.cuda.synchronize()
+        t_asm = time.perf_counter() - t0
         ndof = ctx.ndof(0)
         if args.probe_spmv:
             ctx.pmg_setup(degrees, smooth_its=2, prec="fp32")
@@ -258,7 +354,7 @@ def run_ours(args):
         x = torch.empty(ndof, dtype=torch.float64, device="cuda")
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-        def timed_solves(steps, tag, clocks=None):
+        def timed_solves(steps, tag):
             times, infos = [], []
             for _ in range(steps):
                 flush.fill_(1.0)
@@ -274,34 +370,7 @@ def run_ours(args):
                 infos.append(info)
             return float(np.mean(times)), infos
 
-        # plain FP64 V-cycle on the same problem (for the speedup of the mixed one)
-        fp64 = None
-        if args.prec == "fp32" and not args.no_fp64_compare:
-            ctx.set_option("smoother", 1 if args.smoother == "ilu" else 0)
-            ctx.pmg_setup(degrees, smooth_its=2, prec="fp64")
-            for _ in range(args.warmup):
-                ctx.solve(x, rtol=args.rtol)
-            ms64, inf64 = timed_solves(args.steps, "fp64_step")
-            fp64 = {"ms_per_solve": ms64, "fgmres_iterations": inf64[-1]["iterations"],
-                    "rel_residual": inf64[-1]["rel_residual"], "dof_per_s": ndof / (ms64 / 1e3)}
-        ctx.set_option("coarse_fp32", args.coarse_fp32 if args.prec == "fp32" else 0)
-        ctx.set_option("smoother", 1 if args.smoother == "ilu" else 0)
-        ctx.pmg_setup(degrees, smooth_its=2, prec=args.prec)
-        for _ in range(args.warmup):
-            info = ctx.solve(x, rtol=args.rtol)
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        l0 = ctx.launch_count()
-        with Clocks(local) as clk:
-            ms, infos = timed_solves(args.steps, "timed_step")
-            torch.cuda.synchronize()
-        launches = ctx.launch_count() - l0
-        ms = max_over_ranks(ms, ws, "cuda")
-        value = whole_job_rate(ndof, ws, ms / 1e3)
-
-        # dominant kernel: the level-0 operator of the V-cycle, timed live with CUDA events on its stream
-        def time_kernel(fn, reps=20):
+        def time_on_stream(fn, reps):
             kt = []
             for i in range(reps + 3):
                 flush.fill_(2.0)
@@ -315,15 +384,66 @@ def run_ours(args):
                     kt.append(e0.elapsed_time(e1))
             return float(np.mean(kt))
 
+        peak, peak_kind = peaks()
+        # plain FP64 V-cycle on the same problem (for the speedup of the mixed one)
+        fp64 = None
+        if args.prec == "fp32" and not args.no_fp64_compare:
+            ctx.set_option("smoother", 1 if args.smoother == "ilu" else 0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.pmg_setup(degrees, smooth_its=2, prec="fp64")
+            torch.cuda.synchronize()
+            t_pmg64 = time.perf_counter() - t0
+            for _ in range(args.warmup):
+                ctx.solve(x, rtol=args.rtol)
+            ms64, inf64 = timed_solves(args.steps, "fp64_step")
+            fp64 = {"ms_per_solve": ms64, "fgmres_iterations": inf64[-1]["iterations"],
+                    "rel_residual": inf64[-1]["rel_residual"], "dof_per_s": ndof / (ms64 / 1e3),
+                    "pmg_setup_s": t_pmg64}
+        ctx.set_option("coarse_fp32", args.coarse_fp32 if args.prec == "fp32" else 0)
+        ctx.set_option("smoother", 1 if args.smoother == "ilu" else 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.pmg_setup(degrees, smooth_its=2, prec=args.prec)
+        torch.cuda.synchronize()
+        t_pmg = time.perf_counter() - t0
+        coarse = ctx.coarse_info()
+        for _ in range(args.warmup):
+            info = ctx.solve(x, rtol=args.rtol)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        l0 = ctx.launch_count()
+        with Clocks(local) as clk:
+            if args.profile_region:
+                torch.cuda.profiler.start()
+            ms, infos = timed_solves(args.steps, "timed_step")
+            torch.cuda.synchronize()
+            if args.profile_region:
+                torch.cuda.profiler.stop()
+        launches = ctx.launch_count() - l0
+        ms = max_over_ranks(ms, ws, "cuda")
+        value = whole_job_rate(ndof, ws, ms / 1e3)
+        x_host = x.cpu().numpy()
+
+        # V-cycle: algorithmic bytes over its time (graph replay, inputs larger than L2 or L2 flushed)
+        s_val = 4 if args.prec == "fp32" else 8
+        cs = 4 if (args.prec == "fp32" and args.coarse_fp32) else 8
+        vbytes = vcycle_bytes(mesh, degrees, args.cond, s_val, coarse["values_per_solve"], cs)
+        rv = torch.randn(ndof, dtype=torch.float64, device="cuda")
+        zv = torch.empty_like(rv)
+        ms_v = time_on_stream(lambda: ctx.vcycle(rv, zv), 10)
+        vgbs = vbytes / (ms_v / 1e3) / 1e9
+
+        # dominant kernel: the level-0 operator of the V-cycle, timed live with CUDA events on its stream
         xs = torch.randn(ndof, dtype=torch.float64, device="cuda")
         ys = torch.empty_like(xs)
-        ms64_k = time_kernel(lambda: ctx.spmv(0, xs, ys))
-        nb64 = spmv_bytes(ctx, 0, 8)
-        peak, peak_kind = peaks()
+        ms64_k = time_on_stream(lambda: ctx.spmv(0, xs, ys), 20)
+        nb64 = spmv_bytes(mesh, args.k, args.cond, 8)
         if args.prec == "fp32":
             xs32, ys32 = xs.float(), torch.empty(ndof, dtype=torch.float32, device="cuda")
-            ms_k = time_kernel(lambda: ctx.spmv_f32(0, xs32, ys32))
-            nbytes = spmv_bytes(ctx, 0, 4)
+            ms_k = time_on_stream(lambda: ctx.spmv_f32(0, xs32, ys32), 20)
+            nbytes = spmv_bytes(mesh, args.k, args.cond, 4)
             kname = "k_spmv_v<float> (level 0, V-cycle operator, FP32, row-interleaved)"
         else:
             ms_k, nbytes, kname = ms64_k, nb64, "k_spmv_b<double> (level 0)"
@@ -347,12 +467,24 @@ def run_ours(args):
             if i >= args.warmup:
                 et.append(time.perf_counter() - t0)
         e2e_s = max_over_ranks(float(np.mean(et)), ws, "cuda")
-    cpu = None
+        # error norms of the discrete solution against the manufactured field (Sec. 5.2.2 columns)
+        loc = ctx.recover(x)
+        xe = ctx.quad_nodes("elem").cpu().numpy()
+        uex = torch.from_numpy(hho._chunked(fld.u, xe)).cuda()
+        gex = torch.from_numpy(hho._chunked(fld.grad_u, xe)).cuda()
+        pex = torch.from_numpy(hho._chunked(fld.p, xe)).cuda()
+        err = ctx.errors(loc, uex, gex, pex)
+        del loc, uex, gex, pex
+    cpu = check = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, nd, its, dt = oracle_sample(args.sample_n, args.k, args.cond, args.rtol)
-        cpu = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"oracle FGMRES+p-MG solve on {args.mesh}{args.sample_n if args.mesh == 'tri' else min(args.sample_n, 5)} of the same family "
-                         f"({nd} DOFs, {its} its, {dt:.2f} s); setup excluded"}
+        rates, nd, its, ts = oracle_sample(args)
+        v, dt = rates[-1]
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle FGMRES+p-MG solve on {sample_name(args)} of the same family ({nd} DOFs against "
+                         f"{ndof} in the workload, {its} its, {dt:.2f} s per solve, {ts:.1f} s setup excluded), "
+                         f"one thread"}
+        # the oracle recomputes residual rows of the full-size GPU solution at sampled faces
+        check = oracle_check(mesh, args.k, args.cond, fld, x_host, args.oracle_faces)
     if rank == 0:
         last = infos[-1]
         line = {
@@ -362,11 +494,18 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": wname, "vcycle_precision": args.prec, "smoother": args.smoother,
                        "coarse_precision": "fp32" if (args.prec == "fp32" and args.coarse_fp32) else "fp64",
-                       "dofs": ndof,
+                       "coarse_solver": coarse, "dofs": ndof, "coarse_dofs": ctx.ndof(len(degrees) - 1),
                        "fgmres_iterations": last["iterations"], "coarse_iterations": last["coarse_iterations"],
                        "rel_residual_fp64": last["rel_residual"], "fp64_vcycle": fp64,
                        "speedup_vs_fp64_vcycle": (fp64["ms_per_solve"] / ms) if fp64 else None,
-                       "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if ws > 1 else "single"},
+                       "setup_s": {"hho_setup": t_setup, "assemble": t_asm, "pmg_setup": t_pmg,
+                                   "total": t_setup + t_asm + t_pmg},
+                       "solve_s": ms / 1e3,
+                       "vcycle": {"ms": ms_v, "algorithmic_bytes": vbytes, "achieved_gbs": vgbs,
+                                  "frac_of_measured_hbm": vgbs / peak},
+                       "errors_vs_exact": err, "oracle_check": check,
+                       "l2": "flushed between steps (512 MiB write); operators larger than L2",
+                       "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": (SPMV_F32_TRAFFIC.get((args.mesh, args.n, args.k, args.cond))
@@ -385,6 +524,65 @@ def run_ours(args):
     ctx.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_sweep(args):
+    """The 128 x 128 triangle workload over k = 1..5, both condensations, FP64
+    and FP32 V-cycles: one JSON line per case (solve time, DOF/s, iterations,
+    true residual, setup times, V-cycle GB/s)."""
+    import torch
+    from paper_2009_13840_gb300 import build, hho
+    build.build()
+    peak, _ = peaks()
+    stream = torch.cuda.Stream()
+    for k in range(1, 6):
+        for cond in ("v", "vp"):
+            mesh, fld, wname = workload(args.n, k, cond, "tri")
+            degrees = list(range(k, -1, -1))
+            with torch.cuda.stream(stream):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ctx = hho.Context(mesh, k, cond, stream=stream)
+                ctx.assemble(*hho.data_arrays(ctx, fld))
+                torch.cuda.synchronize()
+                t_setup = time.perf_counter() - t0
+                ndof = ctx.ndof(0)
+                x = torch.empty(ndof, dtype=torch.float64, device="cuda")
+                for prec in ("fp64", "fp32"):
+                    ctx.set_option("coarse_fp32", 1 if (prec == "fp32" and cond == "v") else 0)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    ctx.pmg_setup(degrees, smooth_its=2, prec=prec)
+                    torch.cuda.synchronize()
+                    t_pmg = time.perf_counter() - t0
+                    for _ in range(args.warmup):
+                        ctx.solve(x, rtol=args.rtol, maxit=2000)
+                    ts, info = [], None
+                    for _ in range(args.steps):
+                        info = ctx.solve(x, rtol=args.rtol, maxit=2000)
+                        ts.append(info["solve_ms"])
+                    ms = float(np.mean(ts))
+                    coarse = ctx.coarse_info()
+                    rv = torch.randn(ndof, dtype=torch.float64, device="cuda")
+                    zv = torch.empty_like(rv)
+                    ctx.vcycle(rv, zv)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(10):
+                        ctx.vcycle(rv, zv)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms_v = e0.elapsed_time(e1) / 10
+                    s_val = 4 if prec == "fp32" else 8
+                    cs = 4 if (prec == "fp32" and cond == "v") else 8
+                    vb = vcycle_bytes(mesh, degrees, cond, s_val, coarse["values_per_solve"], cs)
+                    print(json.dumps({"workload": wname, "k": k, "cond": cond, "vcycle_precision": prec, "dofs": ndof,
+                                      "solve_ms": ms, "dof_per_s": ndof / (ms / 1e3),
+                                      "fgmres_iterations": info["iterations"], "rel_residual": info["rel_residual"],
+                                      "setup_s": t_setup, "pmg_setup_s": t_pmg, "vcycle_ms": ms_v,
+                                      "vcycle_gbs": vb / (ms_v / 1e3) / 1e9,
+                                      "vcycle_frac": vb / (ms_v / 1e3) / 1e9 / peak}), flush=True)
+                ctx.close()
 
 
 def oracle_batch_sample(probs, cond, rtol, budget_s=15.0):
@@ -564,7 +762,7 @@ def run_learned(args):
     stream = torch.cuda.Stream()
     degrees = list(range(k, -1, -1))
     with torch.cuda.stream(stream):
-        tmesh, fld, _ = workload(args.learned_train_n, k, cond)
+        tmesh, fld, _ = workload(args.learned_train_n, k, cond, args.mesh)
         tr = hho.Context(tmesh, k, cond, stream=stream)
         tr.assemble(*hho.data_arrays(tr, fld))
         tr.pmg_setup(degrees, smooth_its=2, prec="fp64")
@@ -577,7 +775,7 @@ def run_learned(args):
         train_s = time.perf_counter() - t0
         W = tr.mlp_weights()
         tr.close()
-        mesh, fld, wname = workload(args.n, k, cond)
+        mesh, fld, wname = workload(args.n, k, cond, args.mesh)
         ctx = hho.Context(mesh, k, cond, stream=stream)
         f, gD, gN = hho.data_arrays(ctx, fld)
         ctx.assemble(f, gD, gN)
@@ -643,15 +841,15 @@ def run_learned(args):
 
 
 def main():
-    global MESH
     args = parse()
-    MESH = args.mesh
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -353,6 +353,13 @@ hho_status hho_get_level_coo(hho_ctx* ctx, int level, int64_t* rows, int64_t* co
  * hierarchy must be rebuilt afterwards (hho_assemble is unaffected). */
 hho_status hho_set_element_schur(hho_ctx* ctx, const double* host_in);
 
+/* Coarse solver of the current hierarchy (after pmg_setup): info (host, 4)
+ * = {kind: 0 dense inverse, 1 two-level substructuring, 2 multifrontal;
+ * stored operator values one coarse solve reads; kernel launches per coarse
+ * solve (without the pressure-kernel projection); values of the dense
+ * factorisation workspace (multifrontal: freed after pmg_setup)}. */
+hho_status hho_coarse_info(hho_ctx* ctx, int64_t* info);
+
 /* Number of kernels the library has launched on this context since setup
  * (counts every launch of the solver, V-cycle and SpMV entry points). */
 hho_status hho_launch_count(const hho_ctx* ctx, int64_t* launches);

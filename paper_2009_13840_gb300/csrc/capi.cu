@@ -432,6 +432,15 @@ hho_status hho_get_level_coo(hho_ctx* ctx, int level, int64_t* rows, int64_t* co
     return level_coo(ctx, level, rows, cols, vals, nnz);
 }
 
+hho_status hho_coarse_info(hho_ctx* ctx, int64_t* info) {
+    if (!ctx || !info) return HHO_ERR_ARG;
+    if (!ctx->have_pmg) {
+        ctx->err = "hho_coarse_info: call pmg_setup first";
+        return HHO_ERR_STATE;
+    }
+    return coarse_info(ctx, info);
+}
+
 hho_status hho_launch_count(const hho_ctx* ctx, int64_t* launches) {
     if (!ctx || !launches) return HHO_ERR_ARG;
     *launches = ctx->launches;

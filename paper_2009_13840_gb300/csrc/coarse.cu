@@ -1105,6 +1105,16 @@ bool coarse_has_f32(const hho_ctx* ctx) {
     return ctx->coarse && (ctx->coarse->Ainv32 || mf_has_f32(ctx->coarse->mf));
 }
 
+hho_status coarse_info(const hho_ctx* ctx, int64_t out[4]) {
+    const CoarseSolver* C = ctx->coarse;
+    if (!C) return HHO_ERR_STATE;
+    out[0] = C->kind;
+    out[1] = coarse_solve_bytes(ctx, 1);
+    out[2] = C->kind == 0 ? 1 : C->kind == 1 ? 6 : mf_levels(C->mf) * 2;
+    out[3] = C->kind == 2 ? mf_factor_doubles(C->mf) : C->nAinv;
+    return HHO_OK;
+}
+
 int64_t coarse_solve_bytes(const hho_ctx* ctx, int value_bytes) {
     const CoarseSolver* C = ctx->coarse;
     if (!C) return 0;

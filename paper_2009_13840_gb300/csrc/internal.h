@@ -284,6 +284,9 @@ int64_t coarse_solve_bytes(const hho_ctx* ctx, int value_bytes);
 hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out);
 hho_status mf_make_f32(hho_ctx* ctx, MFSolver* S);
 bool mf_has_f32(const MFSolver* S);
+int mf_levels(const MFSolver* S);
+int64_t mf_factor_doubles(const MFSolver* S);
+hho_status coarse_info(const hho_ctx* ctx, int64_t out[4]);
 int64_t mf_solve_bytes(const MFSolver* S, int value_bytes);
 template <typename T>
 hho_status mf_apply(hho_ctx* ctx, MFSolver* S, const T* d, T* c);

@@ -1014,6 +1014,10 @@ hho_status mf_make_f32(hho_ctx* ctx, MFSolver* S) {
 
 bool mf_has_f32(const MFSolver* S) { return S && S->M1f; }
 
+int mf_levels(const MFSolver* S) { return (int)S->level_mmax.size(); }
+
+int64_t mf_factor_doubles(const MFSolver* S) { return S->factor_doubles; }
+
 int64_t mf_solve_bytes(const MFSolver* S, int value_bytes) { return (S->nM1 + S->nX) * value_bytes; }
 
 template <typename T>

@@ -26,7 +26,7 @@ NODES = {"elem": 0, "face": 1}
 # every entry point declared in include/hho.h
 SYMBOLS = ["hho_setup", "hho_ndof", "hho_quad_nodes", "hho_assemble", "hho_assemble_noalloc", "pmg_setup", "pmg_vcycle", "hho_spmv", "hho_spmv_f32",
            "hho_solve", "hho_recover", "hho_errors", "hho_get_element_schur", "hho_get_level_coo",
-           "hho_set_element_schur", "hho_launch_count", "hho_set_option", "hho_destroy",
+           "hho_set_element_schur", "hho_launch_count", "hho_coarse_info", "hho_set_option", "hho_destroy",
            "hho_last_error", "hho_set_batch", "hho_solve_batch", "hho_autotune", "hho_mlp_init", "hho_mlp_dims",
            "hho_mlp_weights", "hho_mlp_features", "hho_mlp_apply", "hho_mlp_generate", "hho_mlp_train", "hho_mlp_grads",
            "hho_ilu_apply"]
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         "hho_get_level_coo": (C.c_int, [P, C.c_int, P, P, P, C.POINTER(C.c_int64)]),
         "hho_set_element_schur": (C.c_int, [P, P]),
         "hho_launch_count": (C.c_int, [P, C.POINTER(C.c_int64)]),
+        "hho_coarse_info": (C.c_int, [P, C.POINTER(C.c_int64)]),
         "hho_set_option": (C.c_int, [P, C.c_char_p, C.c_double]),
         "hho_destroy": (C.c_int, [P]),
         "hho_last_error": (C.c_char_p, [P]),
@@ -373,6 +374,12 @@ class Context:
     def set_option(self, key: str, value: float):
         self._check(self.lib.hho_set_option(self.h, key.encode(), float(value)))
 
+    def coarse_info(self) -> dict:
+        a = (C.c_int64 * 4)()
+        self._check(self.lib.hho_coarse_info(self.h, a))
+        return {"kind": ["dense", "twolevel", "multifrontal"][a[0]], "values_per_solve": int(a[1]),
+                "launches_per_solve": int(a[2]), "factor_values": int(a[3])}
+
     def launch_count(self) -> int:
         n = C.c_int64()
         self._check(self.lib.hho_launch_count(self.h, C.byref(n)))
@@ -409,13 +416,27 @@ def _dimP(nv, deg):
     return (deg + 1) * (deg + 2) * (deg + 3) // 6
 
 
+def _chunked(fn, *arrays, chunk=1 << 20):
+    """fn over row chunks of the arrays on a thread pool (numpy releases the
+    GIL in its elementwise kernels), concatenated in order."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = arrays[0].shape[0]
+    if n <= chunk:
+        return np.ascontiguousarray(fn(*arrays))
+    parts = [(i, min(i + chunk, n)) for i in range(0, n, chunk)]
+    with ThreadPoolExecutor(max_workers=min(len(parts), os.cpu_count() or 1)) as ex:
+        res = list(ex.map(lambda ab: fn(*[a[ab[0]:ab[1]] for a in arrays]), parts))
+    return np.ascontiguousarray(np.concatenate(res))
+
+
 def data_arrays(ctx: Context, field):
-    """Evaluate a manufactured field at the library's data nodes; returns CUDA tensors (f, gD, gN)."""
+    """Evaluate a manufactured field at the library's data nodes; returns CUDA tensors (f, gD, gN).
+    (Input preparation on the host: the field is the caller's data, not part of the method.)"""
     import torch
     xe = ctx.quad_nodes("elem").cpu().numpy()
     xf, nf = ctx.quad_nodes("face")
     xf, nf = xf.cpu().numpy(), nf.cpu().numpy()
-    f = torch.from_numpy(np.ascontiguousarray(field.f(xe))).cuda()
-    gD = torch.from_numpy(np.ascontiguousarray(field.u(xf))).cuda()
-    gN = torch.from_numpy(np.ascontiguousarray(field.g_neumann(xf, nf))).cuda()
+    f = torch.from_numpy(_chunked(field.f, xe)).cuda()
+    gD = torch.from_numpy(_chunked(field.u, xf)).cuda()
+    gN = torch.from_numpy(_chunked(field.g_neumann, xf, nf)).cuda()
     return f, gD, gN

@@ -58,13 +58,13 @@ def test_single_rank_is_identity():
 def test_reference_arm_prints_on_rank_zero_only():
     env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1")
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
-                          "--warmup", "0", "--sample-n", "4", "--k", "1"], cwd=ROOT, env=env,
+                          "--warmup", "0", "--workload", "c2", "--sample-n", "4", "--k", "1"], cwd=ROOT, env=env,
                          capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     assert not [l for l in out.stdout.splitlines() if l.startswith("{")]
     env["RANK"], env["LOCAL_RANK"] = "0", "0"
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
-                          "--warmup", "0", "--sample-n", "4", "--k", "1"], cwd=ROOT, env=env,
+                          "--warmup", "0", "--workload", "c2", "--sample-n", "4", "--k", "1"], cwd=ROOT, env=env,
                          capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])

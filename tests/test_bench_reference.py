@@ -9,8 +9,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                          "--sample-n", "4", "--k", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "c2", "--steps", "1",
+                          "--warmup", "0", "--sample-n", "4", "--k", "1"], cwd=ROOT, capture_output=True, text=True,
+                         timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1, out.stdout
@@ -24,3 +25,12 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["cores"] >= 1 and "tri4" in d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_reference_arm_default_workload_is_the_3d_family():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1",
+                          "--sample-n", "2", "--k", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
+    assert "hex2^3" in d["cpu_baseline"]["sample"] and d["cpu_baseline"]["cores"] == 1
+    assert d["config"]["workload"].startswith("hex32^3")
