@@ -186,6 +186,8 @@ struct hho_ctx {
     bool use_graphs = true;              // replay captured V-cycles
     int spmv_rows = 0;                   // rows per thread of the operator kernels (0 = automatic)
     int spmv_grid = 0;                   // blocks of the operator kernels (0 = automatic)
+    int spmv_warp = 1;                   // FP32 operator of large 3D face blocks: warp per face (1) or
+                                         // a face's rows split over two threads (0)
 };
 
 // ---- helpers shared across units ----

@@ -749,6 +749,115 @@ __global__ void __launch_bounds__(RT, 4) k_spmv_v(LV<float> L, Items it, const f
     if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
 }
 
+// The same operator for large face blocks (3D, B = 18 and 30 unknowns): one
+// warp per face row block (P = 32 / B faces per warp for smaller blocks), lane
+// r of a face owns row r.  Per slot, lane c loads x's entry c of the slot's
+// column block once and the B values are broadcast by shuffles, while the
+// warp reads every column of the face's block as one contiguous span of B
+// floats (the row-interleaved layout keeps a face's rows contiguous per
+// column), so each slot issues B independent coalesced loads.  Element rows
+// stay one thread per element (their values are contiguous across elements).
+template <int B, int NP>
+__global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t etiles, const float* __restrict__ x,
+                                             const float* __restrict__ bv, float* __restrict__ y, int mode,
+                                             const float* __restrict__ V, int64_t ld, int nv, int self,
+                                             double* __restrict__ partial, unsigned* __restrict__ counter,
+                                             double* __restrict__ out, int hook, double* sc, GS gsl, int j,
+                                             Restr rs) {
+    constexpr int P = (B <= 32) ? (32 / B) : 1;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / B, r = lane - sub * B;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nf = L.nf, ne = L.ne;
+    float dacc[NVMAX + 1];
+#pragma unroll
+    for (int v = 0; v <= NVMAX; ++v) dacc[v] = 0.f;
+    for (int64_t w = warp; w < nfw + etiles; w += nwarps) {
+        if (w < nfw) {
+            const int64_t F = w * P + sub;
+            const bool act = sub < P && F < nf;
+            const int ns = act ? L.ff_nsl[F] : 0;
+            const int nsmax = __reduce_max_sync(0xffffffffu, ns);
+            float acc = 0.f;
+            for (int s = 0; s < nsmax; ++s) {
+                const bool has = s < ns;
+                const int64_t G = has ? L.ff_col[(int64_t)s * nf + F] : 0;
+                const float xl = has ? x[G * B + r] : 0.f;
+                const float* a = L.ff + ((int64_t)s * B * nf + F) * B + r;
+                float av[B];
+#pragma unroll
+                for (int c = 0; c < B; ++c) av[c] = has ? __ldg(a + (int64_t)c * nf * B) : 0.f;
+#pragma unroll
+                for (int c = 0; c < B; ++c) acc += av[c] * __shfl_sync(0xffffffffu, xl, sub * B + c);
+            }
+            if (act) {
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const int T = L.fp_col[p * nf + F];
+                    if (T < 0) continue;
+                    const float* xp = x + nf * B + (int64_t)T * NP;
+                    const float* a = L.fp + ((int64_t)p * NP * nf + F) * B + r;
+#pragma unroll
+                    for (int c = 0; c < NP; ++c) acc += __ldg(a + (int64_t)c * nf * B) * xp[c];
+                }
+                const int64_t o = F * B + r;
+                const float v = mode ? bv[o] - acc : acc;
+                if (mode == 2) {
+                    const int comp = r / rs.nFf, rr = r - comp * rs.nFf;
+                    if (rr < rs.nFc) {
+                        y[F * rs.bc + comp * rs.nFc + rr] = v;
+                        if (self) dacc[NVMAX] += v * v;
+                    }
+                } else {
+                    y[o] = v;
+                    accumulate_dots(dacc, V, ld, o, nv, self, v);
+                }
+            }
+        } else {
+            const int64_t E = (w - nfw) * 32 + lane;
+            if (E >= ne) continue;
+            float acc[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) acc[q] = 0.f;
+            const int N = L.pf_nsl[E];
+            for (int f = 0; f < N; ++f) {
+                const int64_t G = L.pf_col[(int64_t)f * ne + E];
+                const float* xv = x + G * B;
+                const float* a = L.pf + ((int64_t)f * B * ne + E) * NP;
+#pragma unroll 6
+                for (int c = 0; c < B; ++c) {
+                    const float xc = xv[c];
+                    float col[NP];
+                    load_run<NP>(a + (int64_t)c * ne * NP, col);
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) acc[q] += col[q] * xc;
+                }
+            }
+            {
+                float xp[NP];
+                load_run_plain<NP>(x + nf * B + E * NP, xp);
+                block_mv<NP, NP>(L.pp + E * NP, ne * NP, xp, acc);
+            }
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const int64_t o = nf * B + E * NP + q;
+                const float v = mode ? bv[o] - acc[q] : acc[q];
+                if (mode == 2) {
+                    if (q < rs.nPc) {
+                        y[nf * rs.bc + E * rs.nPc + q] = v;
+                        if (self) dacc[NVMAX] += v * v;
+                    }
+                } else {
+                    y[o] = v;
+                    accumulate_dots(dacc, V, ld, o, nv, self, v);
+                }
+            }
+        }
+    }
+    if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
+}
+
 // Block Jacobi on the interleaved FP32 layout, with the pending second
 // Gram-Schmidt pass of k_jacobi_b.
 template <int B, int NP>
@@ -1158,6 +1267,19 @@ template <int B, int NP>
 static void launch_spmv_v_BN(hho_ctx* ctx, const LevelMat& L, const float* x, const float* bv, float* y, int mode,
                              const float* V, int64_t ld, int nv, int self, double* partial, unsigned* counter,
                              double* out, int hook, double* sc, GS gsl, int j, Restr rs) {
+    if constexpr (B >= 18) {  // large 3D blocks: warp per face
+        if (ctx->spmv_warp) {
+            constexpr int P = (B <= 32) ? (32 / B) : 1;
+            Items it;
+            it.ftiles = (L.nf + P - 1) / P;
+            it.etiles = (L.ne + 31) / 32;
+            it.fgroups = it.egroups = 1;
+            const int g = op_grid(ctx, it);
+            k_spmv_w<B, NP><<<g, RT, 0, ctx->stream>>>(view<float>(L), it.ftiles, it.etiles, x, bv, y, mode, V, ld,
+                                                       nv, self, partial, counter, out, hook, sc, gsl, j, rs);
+            return;
+        }
+    }
     constexpr int RF = rf_v(B);
     Items it = items_v(L);
     it.fgroups = B / RF;
