@@ -98,7 +98,7 @@ hho_status hho_setup(const hho_mesh* mesh, int k, int cond, void* stream, hho_ct
  * at level 0 before it. */
 hho_status hho_ndof(const hho_ctx* ctx, int level, int64_t* ndof);
 
-/* Quadrature nodes where the data of hho_assemble are sampled (degree 2k+6
+/* Quadrature nodes where the data of hho_assemble are sampled (degree 2k+2
  * rules on the element and face simplex fans).  which = HHO_NODES_ELEM or
  * HHO_NODES_FACE.  *n_nodes receives the count.  If d_xyz (device,
  * n_nodes*dim) is not NULL the coordinates are written there; for the face

@@ -138,7 +138,7 @@ class LocalSystem:
         k, d = hho.k, hho.d
         eg, eb = hho.elems[self.t], hho.ebases[self.t]
         nE, nF = self.nE, self.nF
-        q_dat = 2 * k + 6
+        q_dat = 2 * k + 2
         b = np.zeros(self.nvec + nE)
         X, W = eg.rule(q_dat)
         ev = eb.eval(X, nE)
@@ -215,9 +215,10 @@ class HHO:
         self.ndof = self.n_face_dofs + mesh.n_elem * self.nP
         self._condense()
 
-    # --- quadrature nodes where the data are evaluated (degree 2k+6) ---
+    # --- quadrature nodes where the data are evaluated (degree 2k+2: exact for the
+    # polynomial data of the consistency pins; the paper does not fix it) ---
     def data_nodes(self):
-        q = 2 * self.k + 6
+        q = 2 * self.k + 2
         elem = [e.rule(q)[0] for e in self.elems]
         face = [f.rule(q)[0] for f in self.faces]
         return elem, face
@@ -350,7 +351,7 @@ class HHO:
         all-Dirichlet problem is compared after removing both means.
         """
         k, d, nE = self.k, self.d, self.nE
-        q = 2 * self.k + 6
+        q = 2 * self.k + 2
         eu = egu = ep = ediv = 0.0
         pm_h = pm_x = vol = 0.0
         cache = []

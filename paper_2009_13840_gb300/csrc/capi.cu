@@ -170,7 +170,7 @@ hho_status hho_mlp_apply(hho_ctx* ctx, const double* d_v, double* d_z) {
     }
     HHO_TRY(mlp_apply<double>(ctx, d_v, d_z));
     HHO_CUDA(cudaStreamSynchronize(ctx->stream));
-    return HHO_OK;
+    return mlp_status(ctx);
 }
 
 hho_status hho_mlp_generate(hho_ctx* ctx, int n_vec, uint64_t seed, int kind, int64_t* n_samples) {
@@ -392,7 +392,9 @@ hho_status hho_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double* 
         ctx->err = "hho_solve: call hho_assemble and pmg_setup first";
         return HHO_ERR_STATE;
     }
-    return fgmres(ctx, rtol, maxit, restart, d_x, info);
+    const hho_status st = fgmres(ctx, rtol, maxit, restart, d_x, info);
+    if (ctx->use_learned && ctx->learned) HHO_TRY(mlp_status(ctx));
+    return st;
 }
 
 hho_status hho_recover(hho_ctx* ctx, const double* d_x, double* d_local) {

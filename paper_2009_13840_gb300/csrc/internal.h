@@ -258,6 +258,7 @@ hho_status mlp_weights(hho_ctx* ctx, int set, double* W1, double* b1, double* W2
 hho_status mlp_features(hho_ctx* ctx, const double* r, float* X, float* s);
 template <typename T>
 hho_status mlp_apply(hho_ctx* ctx, const T* v, T* z);
+hho_status mlp_status(hho_ctx* ctx);
 hho_status mlp_generate(hho_ctx* ctx, int n_vec, uint64_t seed, int kind, int64_t* nsamp);
 hho_status mlp_train(hho_ctx* ctx, int steps, int batch, double lr, uint64_t seed, double* h_loss);
 hho_status mlp_grads(hho_ctx* ctx, const float* X, const float* T, int B, double* loss, double* gW1, double* gb1,

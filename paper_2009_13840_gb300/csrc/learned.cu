@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tc.cuh"
 
 namespace hho {
 
@@ -47,6 +48,8 @@ struct Learned {
     __nv_bfloat16* Xb = nullptr;
     float *Tb = nullptr, *H = nullptr, *dY = nullptr, *dH = nullptr, *lossp = nullptr, *losses = nullptr;
     int loss_cap = 0;
+    bool tc = false;              // first layer on the tensor cores (tc_ok)
+    int* d_status = nullptr;      // device status word of the tensor-core kernels (bounded waits)
 };
 
 namespace {
@@ -107,6 +110,17 @@ __device__ __forceinline__ float feature(const Topo0& t, const T* __restrict__ r
     return 0.f;
 }
 
+// s_F of face F: sequential FP32 sum of squares of its raw features in order
+template <typename T>
+__device__ __forceinline__ float feature_norm(const Topo0& t, const T* __restrict__ r, int64_t F) {
+    float a = 0.f;
+    for (int j = 0; j < t.raw; ++j) {
+        const float f = feature(t, r, F, j);
+        a += f * f;
+    }
+    return sqrtf(a);
+}
+
 // Stage FB faces' features in shared memory (sx[f][din], normalised) and their
 // norms (ss[f]).  Faces past nf get zero features.
 template <typename T>
@@ -117,12 +131,12 @@ __device__ void stage_features(const Topo0& t, const T* __restrict__ r, int64_t 
         sx[idx] = (F < t.nf) ? feature(t, r, F, j) : 0.f;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int f = wid; f < FB; f += blockDim.x >> 5) {
+    // s_F: sequential FP32 sum of squares in feature order (the same arithmetic
+    // as feature_norm, so every kernel sees identical normalised features)
+    for (int f = threadIdx.x; f < FB; f += blockDim.x) {
         float a = 0.f;
-        for (int j = lane; j < t.din; j += 32) a += sx[f * t.din + j] * sx[f * t.din + j];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) ss[f] = sqrtf(a);
+        for (int j = 0; j < t.din; ++j) a += sx[f * t.din + j] * sx[f * t.din + j];
+        ss[f] = sqrtf(a);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < FB * t.din; idx += blockDim.x) {
@@ -180,6 +194,219 @@ __global__ void __launch_bounds__(MT) k_mlp_apply(Topo0 t, int hid, int dout, co
         const float y = out_unit(hid, dout, sh, W2, b2, f, k);
         z[F * t.b + k] += (T)(ss[f] * y);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core first layer (tcgen05, BF16 x BF16 -> FP32 in TMEM).  A CTA of 128
+// threads holds W1^T (hid x din, BF16) in shared memory for the whole launch
+// and loops over tiles of 128 faces (samples): the tile's normalised BF16
+// features are staged as the A operand, one thread issues the din/16 MMAs of
+// the 128 x hid x din product, and every thread then reads its row of the
+// accumulator from TMEM in chunks of 32 columns, applies b1 and the ReLU and
+// runs the (small) second layer on the CUDA cores from W2 in shared memory.
+// Products of BF16 values are exact in FP32, so the layer computes what the
+// CUDA-core version computes up to the order of the FP32 additions.
+// Requirements: hid a multiple of 32 in 32..256, din a multiple of 16,
+// dout <= 32, and the shared-memory footprint of tc_smem.
+// ---------------------------------------------------------------------------
+constexpr int TC_ROWS = 128;
+constexpr int TC_WAIT = 1 << 22;  // bounded polls of the MMA-completion barrier
+
+__host__ __device__ inline uint32_t tc_cols(int hid) {
+    uint32_t c = 32;
+    while ((int)c < hid) c <<= 1;
+    return c;
+}
+
+size_t tc_smem(int din, int hid, int dout) {
+    return (size_t)(hid + TC_ROWS) * din * 2 + (size_t)(hid * dout + hid + dout + TC_ROWS) * 4;
+}
+
+bool tc_ok(int din, int hid, int dout) {
+    return hid % 32 == 0 && hid >= 32 && hid <= 256 && din % 16 == 0 && dout <= 32 &&
+           tc_smem(din, hid, dout) <= 227 * 1024;
+}
+
+struct TcSmem {
+    __nv_bfloat16 *B, *A;
+    float *W2, *b1, *b2, *ss;
+};
+
+__device__ TcSmem tc_carve(unsigned char* smem, int din, int hid, int dout) {
+    TcSmem m;
+    m.B = reinterpret_cast<__nv_bfloat16*>(smem);
+    m.A = m.B + (size_t)hid * din;
+    m.W2 = reinterpret_cast<float*>(m.A + (size_t)TC_ROWS * din);
+    m.b1 = m.W2 + hid * dout;
+    m.b2 = m.b1 + hid;
+    m.ss = m.b2 + dout;
+    return m;
+}
+
+// W1^T as the B operand (row n = hidden unit n over the din inputs), W2, biases
+__device__ void tc_load_weights(const TcSmem& m, int din, int hid, int dout, const __nv_bfloat16* __restrict__ W1,
+                                const float* __restrict__ b1, const __nv_bfloat16* __restrict__ W2,
+                                const float* __restrict__ b2) {
+    for (int idx = threadIdx.x; idx < din * hid; idx += blockDim.x) {
+        const int i = idx / hid, j = idx - i * hid;
+        m.B[tc::core_off(j, i, din)] = W1[idx];
+    }
+    for (int idx = threadIdx.x; idx < hid * dout; idx += blockDim.x) m.W2[idx] = __bfloat162float(W2[idx]);
+    for (int idx = threadIdx.x; idx < hid; idx += blockDim.x) m.b1[idx] = b1[idx];
+    for (int idx = threadIdx.x; idx < dout; idx += blockDim.x) m.b2[idx] = b2[idx];
+}
+
+// y[0..dout) = W2^T relu(acc + b1) + b2 for this thread's accumulator row
+__device__ __forceinline__ void tc_second_layer(const TcSmem& m, uint32_t tmem, int hid, int dout, float (&y)[32],
+                                                float* __restrict__ Hrow) {
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) y[k] = k < dout ? m.b2[k] : 0.f;
+    for (int c0 = 0; c0 < hid; c0 += 32) {
+        float h[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, h);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const float hq = fmaxf(h[q] + m.b1[c0 + q], 0.f);
+            if (Hrow) Hrow[c0 + q] = hq;
+            const float* w = m.W2 + (c0 + q) * dout;
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+                if (k < dout) y[k] += hq * w[k];
+        }
+    }
+}
+
+// Finest-level smoother correction z_F += s_F y_F[:b] with the first layer on
+// the tensor cores (persistent: grid-stride over tiles of 128 faces).
+template <typename T>
+__global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_apply_tc(Topo0 t, int hid, int dout, const T* __restrict__ v,
+                                                            T* __restrict__ z, const __nv_bfloat16* __restrict__ W1,
+                                                            const float* __restrict__ b1,
+                                                            const __nv_bfloat16* __restrict__ W2,
+                                                            const float* __restrict__ b2, int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar;
+    const int din = t.din;
+    const TcSmem m = tc_carve(tc_smem_raw, din, hid, dout);
+    const uint32_t ncols = tc_cols(hid);
+    tc_load_weights(m, din, hid, dout, W1, b1, W2, b2);
+    if (threadIdx.x < 32) tc::tmem_alloc(&s_tmem, ncols);
+    if (threadIdx.x == 0) tc::mbar_init(&s_bar);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    uint32_t parity = 0;
+    const int64_t ntiles = (t.nf + TC_ROWS - 1) / TC_ROWS;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t F = tile * TC_ROWS + threadIdx.x;
+        const bool act = F < t.nf;
+        const float sF = act ? feature_norm(t, v, F) : 0.f;
+        m.ss[threadIdx.x] = sF;
+        for (int j = 0; j < din; ++j) {
+            const float x = (act && sF > 0.f) ? feature(t, v, F, j) / sF : 0.f;
+            m.A[tc::core_off(threadIdx.x, j, din)] = __float2bfloat16_rn(x);
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (threadIdx.x == 0) tc::mma_tile(tmem, m.A, m.B, din, hid, &s_bar);
+        const bool ok = tc::mbar_wait(&s_bar, parity, TC_WAIT);
+        parity ^= 1u;
+        if (!ok) {
+            if (threadIdx.x == 0) atomicExch(status, (int)HHO_ERR_TIMEOUT);
+            break;  // uniform: every thread polls the same barrier
+        }
+        tc::fence_after_sync();
+        float y[32];
+        tc_second_layer(m, tmem, hid, dout, y, nullptr);
+        if (act && sF > 0.f)
+            for (int k = 0; k < t.b; ++k) z[F * t.b + k] += (T)(sF * y[k]);
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_free(tmem, ncols);
+}
+
+// Training forward over a minibatch with the first layer on the tensor cores:
+// H (B x hid, FP32 after relu), dY = 2 (Y - T) / B and one partial loss per
+// tile of 128 samples.
+template <typename XT>
+__global__ void __launch_bounds__(TC_ROWS, 1) k_train_fwd_tc(int B, int din, int hid, int dout,
+                                                            const XT* __restrict__ X, const float* __restrict__ Tt,
+                                                            const __nv_bfloat16* __restrict__ W1,
+                                                            const float* __restrict__ b1,
+                                                            const __nv_bfloat16* __restrict__ W2,
+                                                            const float* __restrict__ b2, float* __restrict__ H,
+                                                            float* __restrict__ dY, float* __restrict__ lossp,
+                                                            int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ float red[TC_ROWS];
+    const TcSmem m = tc_carve(tc_smem_raw, din, hid, dout);
+    const uint32_t ncols = tc_cols(hid);
+    tc_load_weights(m, din, hid, dout, W1, b1, W2, b2);
+    if (threadIdx.x < 32) tc::tmem_alloc(&s_tmem, ncols);
+    if (threadIdx.x == 0) tc::mbar_init(&s_bar);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    uint32_t parity = 0;
+    const int ntiles = (B + TC_ROWS - 1) / TC_ROWS;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i0 = tile * TC_ROWS;
+        for (int idx = threadIdx.x; idx < TC_ROWS * din; idx += blockDim.x) {
+            const int r = idx / din, j = idx - r * din;
+            const float x = (i0 + r < B) ? (float)X[(int64_t)(i0 + r) * din + j] : 0.f;
+            m.A[tc::core_off(r, j, din)] = __float2bfloat16_rn(x);
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (threadIdx.x == 0) tc::mma_tile(tmem, m.A, m.B, din, hid, &s_bar);
+        const bool ok = tc::mbar_wait(&s_bar, parity, TC_WAIT);
+        parity ^= 1u;
+        if (!ok) {
+            if (threadIdx.x == 0) atomicExch(status, (int)HHO_ERR_TIMEOUT);
+            break;
+        }
+        tc::fence_after_sync();
+        const int i = i0 + threadIdx.x;
+        float y[32];
+        tc_second_layer(m, tmem, hid, dout, y, i < B ? H + (int64_t)i * hid : nullptr);
+        float l = 0.f;
+        if (i < B) {
+            for (int k = 0; k < dout; ++k) {
+                const float d = y[k] - Tt[(int64_t)i * dout + k];
+                dY[(int64_t)i * dout + k] = 2.f * d / (float)B;
+                l += d * d;
+            }
+        }
+        red[threadIdx.x] = l;
+        __syncthreads();
+        for (int o = TC_ROWS / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) lossp[tile] = red[0] / (float)B;
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_free(tmem, ncols);
 }
 
 // Training samples of one generated pair: X rows (BF16, normalised features),
@@ -361,7 +588,7 @@ void mlp_free(hho_ctx* ctx) {
     if (!M) return;
     void* ps[] = {M->W1, M->b1, M->W2, M->b2, M->mW1, M->mb1, M->mW2, M->mb2, M->vW1, M->vb1, M->vW2, M->vb2,
                   M->gW1, M->gb1, M->gW2, M->gb2, M->W1h, M->W2h, M->X, M->T, M->Xb, M->Tb, M->H, M->dY, M->dH,
-                  M->lossp, M->losses};
+                  M->lossp, M->losses, M->d_status};
     for (void* p : ps) dfree(p);
     delete M;
     ctx->learned = nullptr;
@@ -388,10 +615,34 @@ hho_status mlp_init(hho_ctx* ctx, int hidden, uint64_t seed) {
     M->din = (M->raw + 15) / 16 * 16;
     M->hid = hidden;
     M->dout = (M->b + 7) / 8 * 8;
-    if (M->din > 256) {
-        ctx->err = "hho_mlp_init: neighbourhood features exceed 256 values";
+    M->tc = tc_ok(M->din, M->hid, M->dout);
+    if (M->din > (M->tc ? 512 : 256)) {
+        ctx->err = "hho_mlp_init: neighbourhood features exceed the kernels' limit (256 values, 512 with the "
+                   "tensor-core first layer: hidden width a multiple of 32)";
         mlp_free(ctx);
         return HHO_ERR_UNSUPPORTED;
+    }
+    HHO_TRY(dalloc(ctx, &M->d_status, 1));
+    HHO_CUDA(cudaMemset(M->d_status, 0, sizeof(int)));
+    {
+        // dynamic shared memory above the default 48 KB where a kernel needs it
+        const int fs = (int)feat_smem(M->din, M->hid), ss = (FB * M->din + FB) * 4;
+        HHO_CUDA(cudaFuncSetAttribute(k_mlp_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs));
+        HHO_CUDA(cudaFuncSetAttribute(k_mlp_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs));
+        HHO_CUDA(cudaFuncSetAttribute(k_train_fwd<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((FB * M->din + FB * M->hid) * 4)));
+        HHO_CUDA(cudaFuncSetAttribute(k_train_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((FB * M->din + FB * M->hid) * 4)));
+        HHO_CUDA(cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, ss));
+        HHO_CUDA(cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, ss));
+        if (M->tc) {
+            const int ts = (int)tc_smem(M->din, M->hid, M->dout);
+            HHO_CUDA(cudaFuncSetAttribute(k_mlp_apply_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts));
+            HHO_CUDA(cudaFuncSetAttribute(k_mlp_apply_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts));
+            HHO_CUDA(cudaFuncSetAttribute(k_train_fwd_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          ts));
+            HHO_CUDA(cudaFuncSetAttribute(k_train_fwd_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts));
+        }
     }
     const int64_t n1 = (int64_t)M->din * M->hid, n2 = (int64_t)M->hid * M->dout;
     float** fp[] = {&M->W1, &M->mW1, &M->vW1, &M->gW1};
@@ -494,15 +745,54 @@ template <typename T>
 hho_status mlp_apply(hho_ctx* ctx, const T* v, T* z) {
     Learned* M = ctx->learned;
     const Topo0 t = topo0(ctx, M);
-    const int nb = (int)((M->nf + FB - 1) / FB);
-    k_mlp_apply<T><<<nb, MT, feat_smem(M->din, M->hid), ctx->stream>>>(t, M->hid, M->dout, v, z, M->W1h, M->b1,
-                                                                        M->W2h, M->b2);
+    if (M->tc) {
+        const int64_t ntiles = (M->nf + TC_ROWS - 1) / TC_ROWS;
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, sm_count()));
+        k_mlp_apply_tc<T><<<g, TC_ROWS, tc_smem(M->din, M->hid, M->dout), ctx->stream>>>(
+            t, M->hid, M->dout, v, z, M->W1h, M->b1, M->W2h, M->b2, M->d_status);
+    } else {
+        const int nb = (int)((M->nf + FB - 1) / FB);
+        k_mlp_apply<T><<<nb, MT, feat_smem(M->din, M->hid), ctx->stream>>>(t, M->hid, M->dout, v, z, M->W1h, M->b1,
+                                                                            M->W2h, M->b2);
+    }
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());
     return HHO_OK;
 }
+
+// Status word of the tensor-core kernels (a bounded wait that expired), read
+// after the synchronising entry points that ran them; cleared when read.
+hho_status mlp_status(hho_ctx* ctx) {
+    Learned* M = ctx->learned;
+    if (!M || !M->tc) return HHO_OK;
+    int st = 0;
+    HHO_CUDA(cudaMemcpyAsync(&st, M->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (st != 0) {
+        HHO_CUDA(cudaMemsetAsync(M->d_status, 0, sizeof(int), ctx->stream));
+        ctx->err = "learned smoother: a tensor-core kernel gave up waiting for its MMAs";
+        return (hho_status)st;
+    }
+    return HHO_OK;
+}
 template hho_status mlp_apply<double>(hho_ctx*, const double*, double*);
 template hho_status mlp_apply<float>(hho_ctx*, const float*, float*);
+
+// Forward pass of a minibatch (H, dY, partial losses): tensor-core first layer
+// when available, else the CUDA-core kernel.
+template <typename XT>
+static void train_forward(hho_ctx* ctx, Learned* M, int B, const XT* X, const float* Tt, size_t sm) {
+    if (M->tc) {
+        const int ntiles = (B + TC_ROWS - 1) / TC_ROWS;
+        const int g = std::max(1, std::min(ntiles, sm_count()));
+        k_train_fwd_tc<XT><<<g, TC_ROWS, tc_smem(M->din, M->hid, M->dout), ctx->stream>>>(
+            B, M->din, M->hid, M->dout, X, Tt, M->W1h, M->b1, M->W2h, M->b2, M->H, M->dY, M->lossp, M->d_status);
+    } else {
+        const int nbk = (B + FB - 1) / FB;
+        k_train_fwd<XT><<<nbk, MT, sm, ctx->stream>>>(B, M->din, M->hid, M->dout, X, Tt, M->W1h, M->b1, M->W2h,
+                                                      M->b2, M->H, M->dY, M->lossp);
+    }
+}
 
 static hho_status ensure_batch(hho_ctx* ctx, Learned* M, int B) {
     if (B <= M->bcap) return HHO_OK;
@@ -614,14 +904,13 @@ hho_status mlp_train(hho_ctx* ctx, int steps, int B, double lr, uint64_t seed, d
         M->loss_cap = steps;
     }
     const int64_t n1 = (int64_t)M->din * M->hid, n2 = (int64_t)M->hid * M->dout;
-    const int nbk = (B + FB - 1) / FB;
+    const int nbk = M->tc ? (B + TC_ROWS - 1) / TC_ROWS : (B + FB - 1) / FB;
     const size_t sm = (size_t)(FB * M->din + FB * M->hid) * 4;
     for (int s = 0; s < steps; ++s) {
         k_gather<<<std::min(B, 4096), 64, 0, ctx->stream>>>(M->nsamp, M->din, M->dout, B,
                                                             seed * 0x9E3779B97F4A7C15ull + (uint64_t)s, M->X, M->T,
                                                             M->Xb, M->Tb);
-        k_train_fwd<__nv_bfloat16><<<nbk, MT, sm, ctx->stream>>>(B, M->din, M->hid, M->dout, M->Xb, M->Tb, M->W1h,
-                                                                 M->b1, M->W2h, M->b2, M->H, M->dY, M->lossp);
+        train_forward<__nv_bfloat16>(ctx, M, B, M->Xb, M->Tb, sm);
         k_sum_losses<<<1, 32, 0, ctx->stream>>>(nbk, M->lossp, M->losses + s);
         k_train_dh<<<g1((int64_t)B * M->hid), 256, 0, ctx->stream>>>(B, M->hid, M->dout, M->dY, M->W2h, M->H,
                                                                      M->dH);
@@ -640,6 +929,7 @@ hho_status mlp_train(hho_ctx* ctx, int steps, int B, double lr, uint64_t seed, d
     std::vector<float> l(steps);
     HHO_CUDA(cudaMemcpyAsync(l.data(), M->losses, steps * 4, cudaMemcpyDeviceToHost, ctx->stream));
     HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    HHO_TRY(mlp_status(ctx));
     if (h_loss)
         for (int s = 0; s < steps; ++s) h_loss[s] = l[s];
     invalidate_graphs(ctx);
@@ -658,15 +948,14 @@ hho_status mlp_grads(hho_ctx* ctx, const float* X, const float* Tt, int B, doubl
     }
     if (B < 1 || B > (1 << 20)) return HHO_ERR_ARG;
     HHO_TRY(ensure_batch(ctx, M, B));
-    const int nbk = (B + FB - 1) / FB;
+    const int nbk = M->tc ? (B + TC_ROWS - 1) / TC_ROWS : (B + FB - 1) / FB;
     const size_t sm = (size_t)(FB * M->din + FB * M->hid) * 4;
     const int64_t n1 = (int64_t)M->din * M->hid, n2 = (int64_t)M->hid * M->dout;
     if (M->loss_cap < 1) {
         HHO_TRY(dalloc(ctx, &M->losses, 1));
         M->loss_cap = 1;
     }
-    k_train_fwd<float><<<nbk, MT, sm, ctx->stream>>>(B, M->din, M->hid, M->dout, X, Tt, M->W1h, M->b1, M->W2h, M->b2,
-                                                     M->H, M->dY, M->lossp);
+    train_forward<float>(ctx, M, B, X, Tt, sm);
     k_sum_losses<<<1, 32, 0, ctx->stream>>>(nbk, M->lossp, M->losses);
     k_train_dh<<<g1((int64_t)B * M->hid), 256, 0, ctx->stream>>>(B, M->hid, M->dout, M->dY, M->W2h, M->H, M->dH);
     k_train_gw<float><<<g1(n1 + n2 + M->hid + M->dout), 256, 0, ctx->stream>>>(
@@ -675,6 +964,7 @@ hho_status mlp_grads(hho_ctx* ctx, const float* X, const float* Tt, int B, doubl
     float lf = 0.f;
     HHO_CUDA(cudaMemcpyAsync(&lf, M->losses, 4, cudaMemcpyDeviceToHost, ctx->stream));
     HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    HHO_TRY(mlp_status(ctx));
     *loss = lf;
     double* hp[] = {gW1, gb1, gW2, gb2};
     float* dp[] = {M->gW1, M->gb1, M->gW2, M->gb2};

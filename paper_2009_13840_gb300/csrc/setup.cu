@@ -13,7 +13,8 @@
 // vertex average) and each simplex gets a collapsed-coordinate tensor
 // Gauss-Legendre rule (segment n=ceil((p+1)/2), triangle n=ceil((p+2)/2),
 // tetrahedron n=ceil((p+3)/2) points per direction).  Operator integrals use
-// degree 2k+2, data integrals degree 2k+6.
+// degree 2k+2, data integrals degree 2k+2 (exact for the polynomial data the
+// scheme reproduces; the paper does not fix the data quadrature).
 //
 // Starting functions before orthonormalisation: collapsed-coordinate (Dubiner)
 // polynomials on triangles, Legendre products on the bounding box otherwise;
@@ -1048,7 +1049,7 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
 }
 
 // ---------------------------------------------------------------------------
-// Right-hand side kernel (data integrals of degree 2k+6) and local condensation.
+// Right-hand side kernel (data integrals of degree 2k+2) and local condensation.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne, const double* __restrict__ xyz,
                                              const int32_t* __restrict__ ef_ptr, const int32_t* __restrict__ ef,
@@ -1069,7 +1070,7 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
     __shared__ RecTab tab;
     rec_tab_fill(tab);
     const int nR = dimP(d, k + 1), nE = dimP(d, k), nF = dimP(d - 1, k);
-    const int pd = 2 * k + 6;
+    const int pd = 2 * k + 2;
     double* ws = scratch + (int64_t)blockIdx.x * scratch_per;
     for (int64_t t = blockIdx.x; t < ne; t += gridDim.x) {
         load_element(E, d, (int)t, ef_ptr, ef, fv_ptr, fv, xyz, fgeo, fbc);
@@ -1213,7 +1214,7 @@ __global__ void k_nodes(int d, int k, int which, int64_t n_items, const double* 
                         const FaceGeo* __restrict__ fgeo, const int32_t* __restrict__ fe, const double* __restrict__ gl,
                         const int64_t* __restrict__ node_off, double* __restrict__ out, double* __restrict__ normals) {
     __shared__ ElemSh E;
-    const int pd = 2 * k + 6;
+    const int pd = 2 * k + 2;
     for (int64_t t = blockIdx.x; t < n_items; t += gridDim.x) {
         if (which == HHO_NODES_ELEM) {
             load_element(E, d, (int)t, ef_ptr, ef, fv_ptr, fv, xyz, fgeo, fbc);
@@ -1306,7 +1307,7 @@ __global__ void k_errors(int d, int k, int cond, int64_t ne, const double* __res
     __shared__ double s_coef[3][36];
     __shared__ double red[6][TPB];
     const int nR = dimP(d, k + 1), nE = dimP(d, k);
-    const int pd = 2 * k + 6;
+    const int pd = 2 * k + 2;
     for (int64_t t = blockIdx.x; t < ne; t += gridDim.x) {
         load_element(E, d, (int)t, ef_ptr, ef, fv_ptr, fv, xyz, fgeo, fbc);
         LocalDims D = local_dims(d, k, E.N, cond);
@@ -1504,7 +1505,7 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
     // data-node offsets
     D.h_enode_off.resize(D.ne + 1);
     D.h_fnode_off.resize(D.nf + 1);
-    const int pd = 2 * k + 6;
+    const int pd = 2 * k + 2;
     int64_t on = 0;
     for (int64_t t = 0; t < D.ne; ++t) {
         D.h_enode_off[t] = on;
