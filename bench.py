@@ -50,6 +50,7 @@ SPECS = {
     "c3": dict(mesh="hex", n=32, k=3, cond="vp", prec="fp32", coarse_fp32=1, sample_n=4),
     "c2": dict(mesh="tri", n=128, k=3, cond="v", prec="fp32", coarse_fp32=1, sample_n=24),
     "c1": dict(mesh="quad", n=16, k=3, cond="vp", prec="fp64", coarse_fp32=0, sample_n=16),
+    "learned": dict(mesh="hex", n=48, k=3, cond="vp", prec="fp32", coarse_fp32=1, sample_n=4),
 }
 
 
@@ -84,14 +85,18 @@ def parse():
     ap.add_argument("--probe-spmv", action="store_true", help="three FP32 and one FP64 level-0 operator launches")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed solves with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
-    ap.add_argument("--learned-train-n", type=int, default=32, help="mesh size the learned smoother is trained on")
+    ap.add_argument("--learned-train-n", type=int, default=None,
+                    help="mesh size the learned smoother is trained on (default 24 for hexahedra, 32 for triangles)")
+    ap.add_argument("--learned-samples", type=int, default=100000, help="training pairs (one per face and vector)")
     ap.add_argument("--batch-n", type=int, default=256, help="problems in the batched workload")
     ap.add_argument("--batch-seed", type=int, default=12345)
     ap.add_argument("--batch-cond", default="v", choices=["v", "vp"])
     ap.add_argument("--batch-compare", type=int, default=16,
                     help="problems of the batch also solved one by one for the batching speedup (0: skip)")
     args = ap.parse_args()
-    spec = SPECS.get(args.workload, SPECS["c2"] if args.workload in ("sweep", "learned") else SPECS["c3"])
+    spec = SPECS.get(args.workload, SPECS["c2"] if args.workload == "sweep" else SPECS["c3"])
+    if args.workload == "learned" and args.mesh == "tri":  # the 2D variant of the learned workload
+        spec = dict(SPECS["c2"], n=128)
     for key in ("mesh", "n", "k", "cond", "prec", "sample_n"):
         if getattr(args, key) is None:
             setattr(args, key, spec[key])
@@ -300,19 +305,27 @@ def vcycle_bytes(mesh, degrees, cond, s, coarse_values, coarse_s, m=2):
     return int(tot)
 
 
-def oracle_check(mesh, k, cond, fld, x, faces, seed=0):
-    """Residual rows b - S x of the full-size solution at sampled faces (and the
-    kept pressures of their elements), recomputed by the oracle from its own
-    local systems (oracle/sampled.py), relative to the right-hand side on the
-    same rows."""
+def oracle_check(mesh, k, cond, fld, x, b_gpu, Sx_gpu, faces, seed=0):
+    """Rows of the full-size system recomputed by the oracle from its own local
+    systems (oracle/sampled.py) at sampled faces and their elements' kept
+    pressures: the oracle's residual b - S x of the GPU solution x on those
+    rows against the GPU's own residual there (equal up to rounding when both
+    sides build the same system), and the oracle's residual on the rows scaled
+    to the global right-hand side (||r_S|| / ||b|| * sqrt(n / |S|), an estimate
+    of the global relative residual)."""
     from oracle.sampled import residual_rows, sample_interior_faces
     with one_thread():
         t0 = time.perf_counter()
         sf = sample_interior_faces(mesh, faces, seed)
         rows, r, b = residual_rows(mesh, k, cond, fld, x, sf)
         dt = time.perf_counter() - t0
-    return {"faces": int(len(sf)), "rows": int(len(rows)), "rel_residual_rows": float(np.linalg.norm(r) / np.linalg.norm(b)),
-            "max_abs_residual_over_max_abs_rhs": float(np.abs(r).max() / np.abs(b).max()), "seconds": dt}
+    r_gpu = b_gpu[rows] - Sx_gpu[rows]
+    scale = max(np.abs(b_gpu[rows]).max(), np.abs(Sx_gpu[rows]).max())
+    return {"faces": int(len(sf)), "rows": int(len(rows)),
+            "system_rows_max_diff_rel": float(np.abs(r - r_gpu).max() / scale),
+            "rhs_rows_max_diff_rel": float(np.abs(b - b_gpu[rows]).max() / np.abs(b_gpu[rows]).max()),
+            "residual_rows_scaled": float(np.linalg.norm(r) / np.linalg.norm(b_gpu) * np.sqrt(len(b_gpu) / len(rows))),
+            "seconds": dt}
 
 
 def run_ours(args):
@@ -425,6 +438,13 @@ def run_ours(args):
         ms = max_over_ranks(ms, ws, "cuda")
         value = whole_job_rate(ndof, ws, ms / 1e3)
         x_host = x.cpu().numpy()
+        # the GPU's right-hand side and S x of the benched solution (for the oracle's row check)
+        b_dev = torch.empty(ndof, dtype=torch.float64, device="cuda")
+        ctx.assemble(f, gD, gN, b_dev)
+        sx_dev = torch.empty(ndof, dtype=torch.float64, device="cuda")
+        ctx.spmv(0, x, sx_dev)
+        b_host, sx_host = b_dev.cpu().numpy(), sx_dev.cpu().numpy()
+        del b_dev, sx_dev
 
         # V-cycle: algorithmic bytes over its time (graph replay, inputs larger than L2 or L2 flushed)
         s_val = 4 if args.prec == "fp32" else 8
@@ -484,7 +504,7 @@ def run_ours(args):
                          f"{ndof} in the workload, {its} its, {dt:.2f} s per solve, {ts:.1f} s setup excluded), "
                          f"one thread"}
         # the oracle recomputes residual rows of the full-size GPU solution at sampled faces
-        check = oracle_check(mesh, args.k, args.cond, fld, x_host, args.oracle_faces)
+        check = oracle_check(mesh, args.k, args.cond, fld, x_host, b_host, sx_host, args.oracle_faces)
     if rank == 0:
         last = infos[-1]
         line = {
@@ -749,36 +769,52 @@ def run_batch(args):
 
 
 def run_learned(args):
-    """Learned smoother: a two-layer MLP (hidden 128, BF16) trained on the GPU on
-    the finest-level post-smoother pairs of the FP64 V-cycle on a smaller mesh of
-    the family, then used in the 128x128 triangle workload under
-    velocity-pressure condensation (where block-Jacobi smoothing is weak);
-    one step = one solve to 1e-8 with the learned smoother, timed against the
-    plain smoother on the same problem."""
+    """Learned smoother: a two-layer MLP (hidden 128, BF16, first layer on the
+    tensor cores) trained on the GPU on the finest-level post-smoother pairs of
+    the FP64 V-cycle, taken on a smaller mesh of the workload family (default:
+    24^3 jittered hexahedra, seed 1, k = 3, v&p condensation, about 10^5
+    pairs), then used in the FP32 V-cycle of the evaluation mesh (default
+    48^3 hexahedra, seed 0); one step = one solve to 1e-8 with the learned
+    smoother, timed against the plain block-Jacobi smoother on the same
+    problem.  --mesh tri gives the 2D variant (32x32 -> 128x128 triangles)."""
     import torch
     from paper_2009_13840_gb300 import build, hho
     build.build()
     cond, k = "vp", args.k
+    train_n = args.learned_train_n or (24 if args.mesh == "hex" else 32)
     stream = torch.cuda.Stream()
     degrees = list(range(k, -1, -1))
     with torch.cuda.stream(stream):
-        tmesh, fld, _ = workload(args.learned_train_n, k, cond, args.mesh)
+        from synthetic import hex_mesh, tri_mesh
+        if args.mesh == "hex":
+            from synthetic import fields as F_
+            tmesh, fld = hex_mesh(train_n, jitter=0.15, seed=1), F_.CurlStokes3D()
+        else:
+            tmesh, fld, _ = workload(train_n, k, cond, args.mesh)
         tr = hho.Context(tmesh, k, cond, stream=stream)
         tr.assemble(*hho.data_arrays(tr, fld))
         tr.pmg_setup(degrees, smooth_its=2, prec="fp64")
         tr.mlp_init(hidden=128, seed=11)
+        n_vec = max(1, -(-args.learned_samples // tmesh.n_face))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        nsamp = tr.mlp_generate(n_vec=16, seed=3, kind=2)
+        nsamp = tr.mlp_generate(n_vec=n_vec, seed=3, kind=2)
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
         loss = tr.mlp_train(steps=1500, batch=4096, lr=1e-3, seed=5)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
         W = tr.mlp_weights()
+        dims = tr.mlp_dims()
         tr.close()
+        del tr
+        torch.cuda.empty_cache()
         mesh, fld, wname = workload(args.n, k, cond, args.mesh)
         ctx = hho.Context(mesh, k, cond, stream=stream)
         f, gD, gN = hho.data_arrays(ctx, fld)
         ctx.assemble(f, gD, gN)
+        ctx.set_option("coarse_fp32", args.coarse_fp32 if args.prec == "fp32" else 0)
         ctx.pmg_setup(degrees, smooth_its=2, prec=args.prec)
         ctx.mlp_init(hidden=128, seed=0)
         ctx.mlp_weights(W)
@@ -786,7 +822,7 @@ def run_learned(args):
         x = torch.empty(ndof, dtype=torch.float64, device="cuda")
         flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device="cuda")
 
-        def timed(learned, steps, clk=None):
+        def timed(learned, steps):
             ctx.set_option("learned_smoother", learned)
             for _ in range(args.warmup):
                 ctx.solve(x, rtol=args.rtol, maxit=2000)
@@ -799,6 +835,18 @@ def run_learned(args):
             return float(np.mean(times)), info
 
         ms_plain, inf_plain = timed(0, max(1, args.steps // 2))
+        # the learned correction alone (tensor-core inference kernel) on a finest-level vector
+        rv = torch.randn(ndof, dtype=torch.float64, device="cuda")
+        zv = torch.zeros_like(rv)
+        ctx.mlp_apply(rv, zv)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            ctx.mlp_apply(rv, zv)
+        e1.record(stream)
+        e1.synchronize()
+        ms_apply = e0.elapsed_time(e1) / 10
+        flops_apply = 2.0 * mesh.n_face * dims["din"] * dims["hid"] + 2.0 * mesh.n_face * dims["hid"] * dims["dout"]
         launches0 = ctx.launch_count()
         with Clocks(torch.cuda.current_device()) as clk:
             ms, inf = timed(1, args.steps)
@@ -827,12 +875,16 @@ def run_learned(args):
                    "plain_smoother": {"ms_per_solve": ms_plain, "fgmres_iterations": inf_plain["iterations"],
                                       "dof_per_s": ndof / (ms_plain / 1e3)},
                    "speedup_vs_plain": ms_plain / ms,
-                   "training": {"mesh": f"tri{args.learned_train_n}x{args.learned_train_n}", "samples": int(nsamp),
-                                "steps": 1500, "batch": 4096, "hidden": 128, "seconds": train_s,
-                                "loss_first": float(loss[:10].mean()), "loss_last": float(loss[-50:].mean())},
+                   "mlp_apply": {"ms": ms_apply, "tflops": flops_apply / (ms_apply / 1e3) / 1e12,
+                                 "din": dims["din"], "hidden": dims["hid"], "dout": dims["dout"]},
+                   "training": {"mesh": f"{args.mesh}{train_n}", "samples": int(nsamp), "vectors": n_vec,
+                                "steps": 1500, "batch": 4096, "hidden": 128, "generate_s": gen_s,
+                                "seconds": train_s, "loss_first": float(loss[:10].mean()),
+                                "loss_last": float(loss[-50:].mean())},
                    "l2": "flushed between steps (512 MiB write)", "parallelism": "single"},
         "cpu_baseline": None,
-        "e2e": {"value": ndof / float(np.mean(et)), "unit": UNIT, "h2d_bytes_per_step": int((f.numel() + gD.numel() + gN.numel()) * 8),
+        "e2e": {"value": ndof / float(np.mean(et)), "unit": UNIT,
+                "h2d_bytes_per_step": int((f.numel() + gD.numel() + gN.numel()) * 8),
                 "d2h_bytes_per_step": int(ndof * 8)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

@@ -749,14 +749,51 @@ __global__ void __launch_bounds__(RT, 4) k_spmv_v(LV<float> L, Items it, const f
     if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
 }
 
-// The same operator for large face blocks (3D, B = 18 and 30 unknowns): one
-// warp per face row block (P = 32 / B faces per warp for smaller blocks), lane
-// r of a face owns row r.  Per slot, lane c loads x's entry c of the slot's
-// column block once and the B values are broadcast by shuffles, while the
-// warp reads every column of the face's block as one contiguous span of B
-// floats (the row-interleaved layout keeps a face's rows contiguous per
-// column), so each slot issues B independent coalesced loads.  Element rows
-// stay one thread per element (their values are contiguous across elements).
+// Lane layout of the warp-per-face kernels for the 3D face blocks (B = 9, 18,
+// 30 unknowns): a lane loads VW consecutive rows of one column with one
+// VW * 4-byte load; RL = B / VW lanes cover a column and GC = 32 / RL columns
+// are read by one warp instruction (lane = g * RL + rr: column group g, rows
+// rr * VW ..); each lane accumulates its rows over the columns c = g (mod GC)
+// and the GC partial sums of a row are added across the lane groups in group
+// order (deterministic).
+constexpr int wv_vw(int B) { return (B % 2 == 0 && B / 2 <= 16) ? 2 : 1; }
+constexpr int wv_rl(int B) { return B / wv_vw(B); }
+constexpr int wv_gc(int B) { return 32 / wv_rl(B); }
+constexpr int wv_nk(int B) { return (B + wv_gc(B) - 1) / wv_gc(B); }
+static_assert(wv_rl(30) == 15 && wv_gc(30) == 2 && wv_rl(18) == 9 && wv_gc(18) == 3 && wv_rl(9) == 9 &&
+                  wv_gc(9) == 3 && wv_nk(30) * wv_gc(30) == 30 && wv_nk(18) * wv_gc(18) == 18,
+              "warp lane layout");
+
+template <int VW>
+__device__ __forceinline__ void load_vw(const float* __restrict__ p, float (&v)[VW]) {
+    if constexpr (VW == 2) {
+        const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < VW; ++q) v[q] = __ldg(p + q);
+    }
+}
+
+// sum over the GC column groups of acc (every lane gets the total of its rows)
+template <int B, int VW>
+__device__ __forceinline__ void wv_group_sum(float (&acc)[VW], int rr) {
+    constexpr int RL = wv_rl(B), GC = wv_gc(B);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) {
+        float t = 0.f;
+#pragma unroll
+        for (int g2 = 0; g2 < GC; ++g2) t += __shfl_sync(0xffffffffu, acc[q], g2 * RL + rr);
+        acc[q] = t;
+    }
+}
+
+// The level operator for the 3D face blocks: one warp per face row block
+// (lane layout above).  Per slot, lane c < B loads x's entry c of the slot's
+// column block once and the values are broadcast by shuffles; the face's
+// block is read as NK wide coalesced loads per slot.  Element rows stay one
+// thread per element (their values are contiguous across elements).
 template <int B, int NP>
 __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t etiles, const float* __restrict__ x,
                                              const float* __restrict__ bv, float* __restrict__ y, int mode,
@@ -764,9 +801,10 @@ __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t
                                              double* __restrict__ partial, unsigned* __restrict__ counter,
                                              double* __restrict__ out, int hook, double* sc, GS gsl, int j,
                                              Restr rs) {
-    constexpr int P = (B <= 32) ? (32 / B) : 1;
+    constexpr int VW = wv_vw(B), RL = wv_rl(B), GC = wv_gc(B), NK = wv_nk(B);
     const int lane = threadIdx.x & 31;
-    const int sub = lane / B, r = lane - sub * B;
+    const int g = lane / RL, rr = lane - g * RL;
+    const bool lane_ok = g < GC;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nf = L.nf, ne = L.ne;
@@ -775,43 +813,63 @@ __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t
     for (int v = 0; v <= NVMAX; ++v) dacc[v] = 0.f;
     for (int64_t w = warp; w < nfw + etiles; w += nwarps) {
         if (w < nfw) {
-            const int64_t F = w * P + sub;
-            const bool act = sub < P && F < nf;
-            const int ns = act ? L.ff_nsl[F] : 0;
-            const int nsmax = __reduce_max_sync(0xffffffffu, ns);
-            float acc = 0.f;
-            for (int s = 0; s < nsmax; ++s) {
-                const bool has = s < ns;
-                const int64_t G = has ? L.ff_col[(int64_t)s * nf + F] : 0;
-                const float xl = has ? x[G * B + r] : 0.f;
-                const float* a = L.ff + ((int64_t)s * B * nf + F) * B + r;
-                float av[B];
+            const int64_t F = w;
+            const int ns = L.ff_nsl[F];
+            float acc[VW];
 #pragma unroll
-                for (int c = 0; c < B; ++c) av[c] = has ? __ldg(a + (int64_t)c * nf * B) : 0.f;
+            for (int q = 0; q < VW; ++q) acc[q] = 0.f;
+            for (int s = 0; s < ns; ++s) {
+                const int64_t G = L.ff_col[(int64_t)s * nf + F];
+                const float xl = lane < B ? x[G * B + lane] : 0.f;
+                const float* a = L.ff + ((int64_t)s * B * nf + F) * B + rr * VW;
+                float av[NK][VW];
 #pragma unroll
-                for (int c = 0; c < B; ++c) acc += av[c] * __shfl_sync(0xffffffffu, xl, sub * B + c);
-            }
-            if (act) {
+                for (int k = 0; k < NK; ++k) {
+                    const int c = k * GC + g;
+                    if (lane_ok && c < B) load_vw<VW>(a + (int64_t)c * nf * B, av[k]);
+                    else
 #pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    const int T = L.fp_col[p * nf + F];
-                    if (T < 0) continue;
-                    const float* xp = x + nf * B + (int64_t)T * NP;
-                    const float* a = L.fp + ((int64_t)p * NP * nf + F) * B + r;
-#pragma unroll
-                    for (int c = 0; c < NP; ++c) acc += __ldg(a + (int64_t)c * nf * B) * xp[c];
+                        for (int q = 0; q < VW; ++q) av[k][q] = 0.f;
                 }
-                const int64_t o = F * B + r;
-                const float v = mode ? bv[o] - acc : acc;
-                if (mode == 2) {
-                    const int comp = r / rs.nFf, rr = r - comp * rs.nFf;
-                    if (rr < rs.nFc) {
-                        y[F * rs.bc + comp * rs.nFc + rr] = v;
-                        if (self) dacc[NVMAX] += v * v;
+#pragma unroll
+                for (int k = 0; k < NK; ++k) {
+                    const float xc = __shfl_sync(0xffffffffu, xl, (k * GC + g) & 31);
+#pragma unroll
+                    for (int q = 0; q < VW; ++q) acc[q] += av[k][q] * xc;
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const int T = L.fp_col[p * nf + F];
+                if (T < 0) continue;
+                const float* xp = x + nf * B + (int64_t)T * NP;
+                const float* a = L.fp + ((int64_t)p * NP * nf + F) * B + rr * VW;
+                for (int c = g; c < NP; c += GC) {
+                    if (!lane_ok) break;
+                    float av[VW];
+                    load_vw<VW>(a + (int64_t)c * nf * B, av);
+                    const float xc = xp[c];
+#pragma unroll
+                    for (int q = 0; q < VW; ++q) acc[q] += av[q] * xc;
+                }
+            }
+            wv_group_sum<B, VW>(acc, rr);
+            if (g == 0) {
+#pragma unroll
+                for (int q = 0; q < VW; ++q) {
+                    const int r = rr * VW + q;
+                    const int64_t o = F * B + r;
+                    const float v = mode ? bv[o] - acc[q] : acc[q];
+                    if (mode == 2) {
+                        const int comp = r / rs.nFf, rq = r - comp * rs.nFf;
+                        if (rq < rs.nFc) {
+                            y[F * rs.bc + comp * rs.nFc + rq] = v;
+                            if (self) dacc[NVMAX] += v * v;
+                        }
+                    } else {
+                        y[o] = v;
+                        accumulate_dots(dacc, V, ld, o, nv, self, v);
                     }
-                } else {
-                    y[o] = v;
-                    accumulate_dots(dacc, V, ld, o, nv, self, v);
                 }
             }
         } else {
@@ -856,6 +914,71 @@ __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t
         }
     }
     if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
+}
+
+// Block Jacobi for the 3D face blocks with the lane layout above (one warp per
+// face), element blocks one thread per element; the pending second
+// Gram-Schmidt pass as in k_jacobi_v.
+template <int B, int NP>
+__global__ void __launch_bounds__(RT) k_jacobi_w(LV<float> L, int64_t etiles, const float* __restrict__ w,
+                                               const double* __restrict__ den, float* __restrict__ v,
+                                               float* __restrict__ z, const float* __restrict__ Vp, int64_t ld,
+                                               int npend, const double* __restrict__ pc) {
+    constexpr int VW = wv_vw(B), RL = wv_rl(B), GC = wv_gc(B), NK = wv_nk(B);
+    const float inv = block_inverse<float>(den);
+    const float* s_pc = stage_pending<float>(pc, npend);
+    const int lane = threadIdx.x & 31;
+    const int g = lane / RL, rr = lane - g * RL;
+    const bool lane_ok = g < GC;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nf = L.nf, ne = L.ne;
+    for (int64_t wi = warp; wi < nf + etiles; wi += nwarps) {
+        if (wi < nf) {
+            const int64_t F = wi;
+            const float ul = lane < B ? pending(w, Vp, ld, npend, s_pc, F * B + lane) : 0.f;
+            const float* a = L.dinv + F * B + rr * VW;
+            float av[NK][VW];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const int c = k * GC + g;
+                if (lane_ok && c < B) load_vw<VW>(a + (int64_t)c * nf * B, av[k]);
+                else
+#pragma unroll
+                    for (int q = 0; q < VW; ++q) av[k][q] = 0.f;
+            }
+            float acc[VW];
+#pragma unroll
+            for (int q = 0; q < VW; ++q) acc[q] = 0.f;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const float uc = __shfl_sync(0xffffffffu, ul, (k * GC + g) & 31);
+#pragma unroll
+                for (int q = 0; q < VW; ++q) acc[q] += av[k][q] * uc;
+            }
+            wv_group_sum<B, VW>(acc, rr);
+            if (g == 0)
+#pragma unroll
+                for (int q = 0; q < VW; ++q) z[F * B + rr * VW + q] = acc[q] * inv;
+            if (lane < B) v[F * B + lane] = ul * inv;
+        } else {
+            const int64_t E = (wi - nf) * 32 + lane;
+            if (E >= ne) continue;
+            const int64_t ob = nf * B + E * NP;
+            float u[NP], acc[NP];
+#pragma unroll
+            for (int c = 0; c < NP; ++c) {
+                u[c] = pending(w, Vp, ld, npend, s_pc, ob + c);
+                acc[c] = 0.f;
+            }
+            block_mv<NP, NP>(L.minv + E * NP, ne * NP, u, acc);
+#pragma unroll
+            for (int r = 0; r < NP; ++r) {
+                z[ob + r] = acc[r] * inv;
+                v[ob + r] = u[r] * inv;
+            }
+        }
+    }
 }
 
 // Block Jacobi on the interleaved FP32 layout, with the pending second
@@ -1267,11 +1390,10 @@ template <int B, int NP>
 static void launch_spmv_v_BN(hho_ctx* ctx, const LevelMat& L, const float* x, const float* bv, float* y, int mode,
                              const float* V, int64_t ld, int nv, int self, double* partial, unsigned* counter,
                              double* out, int hook, double* sc, GS gsl, int j, Restr rs) {
-    if constexpr (B >= 18) {  // large 3D blocks: warp per face
+    if constexpr (B == 9 || B == 18 || B == 30) {  // 3D face blocks: warp per face
         if (ctx->spmv_warp) {
-            constexpr int P = (B <= 32) ? (32 / B) : 1;
             Items it;
-            it.ftiles = (L.nf + P - 1) / P;
+            it.ftiles = L.nf;
             it.etiles = (L.ne + 31) / 32;
             it.fgroups = it.egroups = 1;
             const int g = op_grid(ctx, it);
@@ -1291,6 +1413,15 @@ static void launch_spmv_v_BN(hho_ctx* ctx, const LevelMat& L, const float* x, co
 template <int B, int NP>
 static void launch_jacobi_v_BN(hho_ctx* ctx, const LevelMat& L, const float* w, const double* den, float* v,
                                float* z, const float* Vp, int64_t ld, int npend, const double* pc) {
+    if constexpr (B == 9 || B == 18 || B == 30) {
+        if (ctx->spmv_warp) {
+            const int64_t etiles = (L.ne + 31) / 32;
+            const int64_t g = std::max<int64_t>(1, std::min<int64_t>((L.nf + etiles + RT / 32 - 1) / (RT / 32), GMAX));
+            k_jacobi_w<B, NP><<<(int)g, RT, 0, ctx->stream>>>(view<float>(L), etiles, w, den, v, z, Vp, ld, npend,
+                                                              pc);
+            return;
+        }
+    }
     const Items it = items_v(L);
     const int64_t g = std::max<int64_t>(1, std::min<int64_t>((it.total() + RT / 32 - 1) / (RT / 32), GMAX));
     k_jacobi_v<B, NP><<<(int)g, RT, 0, ctx->stream>>>(view<float>(L), it, w, den, v, z, Vp, ld, npend, pc);

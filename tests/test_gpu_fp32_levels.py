@@ -7,7 +7,7 @@ against the FP64 operator (itself pinned to the oracle at 1e-13) for the block
 sizes of 2D triangles (k = 1..5: face blocks of 4..12 unknowns, pressure
 blocks of 3..21) and 3D hexahedra (k = 1..3: face blocks of 9, 18 and 30),
 under both condensations; for the large 3D blocks the warp-per-face kernel is
-also compared with the two-threads-per-face one.  One FP32 V-cycle is compared
+also compared with the one-thread-per-face one.  One FP32 V-cycle is compared
 with the oracle's FP64 V-cycle: FP32 rounding amplified by the coarse
 conditioning, 1e-3 relative.
 """
@@ -58,7 +58,7 @@ def test_fp32_levels_match_fp64(hho_mod, shape, k, cond):
         err = (torch.linalg.norm(y32.double() - y64) / torch.linalg.norm(y64)).item()
         worst = max(worst, err)
         assert err < 1e-5, (l, err)
-        if shape == "hex" and k >= 2:
+        if shape == "hex":
             ctx.set_option("spmv_warp", 0)
             y32b = torch.empty(n, dtype=torch.float32, device="cuda")
             ctx.spmv_f32(l, x.float(), y32b)
