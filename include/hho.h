@@ -202,6 +202,15 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
  *                       block-Jacobi output in the finest-level post-smoother;
  *                       0 (default): plain smoother.  HHO_ERR_STATE without
  *                       hho_mlp_init.
+ *   "spmv_warp"         1 (default): the FP32 operator and block-Jacobi
+ *                       kernels of face blocks of 18 and 30 unknowns (3D, k =
+ *                       2, 3) use one warp per face; 0: one thread per face
+ *   "solve_graph"       1 (default): hho_solve_batch on a non-default stream
+ *                       runs as one CUDA graph captured on first use for each
+ *                       (x, rtol, maxit, restart): restart cycles in a WHILE
+ *                       node, Arnoldi steps in IF nodes, every convergence
+ *                       test on the device; 0: host-driven loop (one 16-byte
+ *                       read per problem and iteration)
  *   "coarse_fp32"       with HHO_FP32: 1 keeps FP32 copies of the coarse
  *                       solver's inverse blocks and runs the coarse solve in
  *                       FP32 (FP32 multiply-adds, no FP64 round trip);
@@ -210,8 +219,8 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
  *                       operator is badly conditioned (velocity-pressure
  *                       condensation).  Copies are made at pmg_setup;
  *                       setting 0 afterwards switches back at once.
- * "graphs", "spmv_rows", "spmv_grid" and a later "coarse_fp32" = 0 act at the
- * next V-cycle.  Returns HHO_ERR_ARG for an unknown key or an invalid value. */
+ * "graphs", "spmv_rows", "spmv_grid", "spmv_warp", "solve_graph" and a later
+ * "coarse_fp32" = 0 act at the next V-cycle or solve.  Returns HHO_ERR_ARG for an unknown key or an invalid value. */
 hho_status hho_set_option(hho_ctx* ctx, const char* key, double value);
 
 /* One V-cycle MG_V(0, r, 0) of the Algorithm of Sec. 3.3: d_z = MG(d_r).
@@ -247,7 +256,10 @@ hho_status hho_set_batch(hho_ctx* ctx, int n_prob, const int64_t* face_off, cons
 /* One FGMRES per problem of a declared batch (Sec. 3.3: one V-cycle per
  * iteration, CGS2, x0 = 0), all advanced in lockstep with per-problem
  * (segmented) dot products, each stopping at ||rhs_p - S_p x_p|| <=
- * rtol ||rhs_p||; a converged problem is frozen while the others go on.  The
+ * rtol ||rhs_p||; a converged problem is frozen while the others go on.
+ * With option "solve_graph" (default) and a non-default stream the whole
+ * solve is one graph launch with device-side control; the results are read
+ * back once it has finished.  The
  * V-cycle is the union's (its smoother's Krylov coefficients are shared by the
  * batch, which flexible GMRES admits).  d_x: device, ndof(0).  h_iters
  * (host, n_prob, may be NULL): iteration at which each problem converged;

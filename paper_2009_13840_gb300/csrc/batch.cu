@@ -178,6 +178,13 @@ int grid1d(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 
 
 }  // namespace
 
+// Device state of the graph-captured batch solve (one FGMRES per problem, all
+// control on the device).
+struct BGState {
+    int it;      // FGMRES iterations so far
+    int cycles;  // restart cycles so far
+};
+
 struct BatchWork {
     int restart = 0, tile_rows = 0;
     int nt = 0;
@@ -187,13 +194,40 @@ struct BatchWork {
            *stat = nullptr;
     double* h_stat = nullptr;  // pinned
     int32_t* h_frz = nullptr;  // pinned
+    // graph-captured solve: the captured graph, what it was captured for, and its device state
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    double* g_x = nullptr;
+    double g_rtol = 0.0;
+    int g_maxit = -1, g_restart = 0;
+    int64_t g_launch_fixed = 0, g_launch_cycle = 0, g_launch_iter = 0;  // kernels per part of the graph
+    double *d_bnorm = nullptr, *d_relres = nullptr;
+    int32_t *d_conv = nullptr, *d_convit = nullptr, *d_its = nullptr;
+    BGState* d_state = nullptr;
+    cudaGraphConditionalHandle* d_handles = nullptr;  // the restart cycle's IF nodes
+    cudaStream_t s_body = nullptr;                    // streams that capture the nested bodies
+    int gP = 0;
 };
+
+void batch_graph_free(hho_ctx* ctx) {
+    BatchWork* B = ctx->batch;
+    if (!B) return;
+    if (B->gexec) cudaGraphExecDestroy(B->gexec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    B->gexec = nullptr;
+    B->graph = nullptr;
+    B->g_x = nullptr;
+    B->g_maxit = -1;
+}
 
 void batch_free(hho_ctx* ctx) {
     BatchWork* B = ctx->batch;
     if (!B) return;
+    batch_graph_free(ctx);
+    if (B->s_body) cudaStreamDestroy(B->s_body);
     void* ps[] = {B->tile_prob, B->tile_len, B->prob_t0, B->frz, B->tile_r0, B->V, B->Z, B->w, B->b, B->fsc,
-                  B->partial, B->stat};
+                  B->partial, B->stat, B->d_bnorm, B->d_relres, B->d_conv, B->d_convit, B->d_its, B->d_state,
+                  B->d_handles};
     for (void* p : ps) dfree(p);
     if (B->h_stat) cudaFreeHost(B->h_stat);
     if (B->h_frz) cudaFreeHost(B->h_frz);
@@ -369,6 +403,328 @@ struct Seg {
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Graph-captured batch solve.  The whole solve (every restart cycle and every
+// Arnoldi step of every problem's FGMRES) is one CUDA graph: a WHILE node runs
+// the restart cycles and, inside it, one IF node per Arnoldi step skips the
+// rest of a cycle once every problem has met its tolerance.  The tests that
+// the host-driven loop does on copied scalars run in the single-block kernels
+// below, which set the graph's conditions; nothing is read on the host until
+// the graph has finished.
+// ---------------------------------------------------------------------------
+constexpr int BG_T = 256;
+
+__device__ __forceinline__ void bg_freeze(double* fsc, int64_t GT, int p) {
+    fsc[p * GT + 4] = 1.0;
+    fsc[p * GT + 5] = 0.0;
+}
+
+// after ||b_p|| (START statistics in stat): tolerances and the first condition
+__global__ void __launch_bounds__(BG_T) k_bg_init(int P, const double* __restrict__ stat, double* __restrict__ bnorm,
+                                                  int32_t* __restrict__ conv, int32_t* __restrict__ convit,
+                                                  BGState* st, int maxit, cudaGraphConditionalHandle h_outer) {
+    int open = 0;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const double bn = stat[2 * p];
+        bnorm[p] = bn;
+        const int c = bn > 0.0 ? 0 : 1;
+        conv[p] = c;
+        convit[p] = c ? 0 : -1;
+        open |= !c;
+    }
+    open = __syncthreads_or(open);
+    if (threadIdx.x == 0) {
+        st->it = 0;
+        st->cycles = 0;
+        cudaGraphSetConditional(h_outer, (open && maxit > 0) ? 1u : 0u);
+    }
+}
+
+// start of a restart cycle: freeze the problems that have converged, open the
+// first Arnoldi step and close the others
+__global__ void __launch_bounds__(BG_T) k_bg_cycle_start(int P, const int32_t* __restrict__ conv,
+                                                         double* __restrict__ fsc, int64_t GT,
+                                                         const cudaGraphConditionalHandle* __restrict__ hs, int m) {
+    for (int p = threadIdx.x; p < P; p += blockDim.x)
+        if (conv[p]) bg_freeze(fsc, GT, p);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) cudaGraphSetConditional(hs[j], j == 0 ? 1u : 0u);
+}
+
+// after Arnoldi step j: problems whose residual estimate meets the tolerance
+// are frozen for the rest of the cycle; step j + 1 runs unless every problem
+// is frozen or broken down, maxit is reached or the cycle is full
+__global__ void __launch_bounds__(BG_T) k_bg_iter(int P, const double* __restrict__ stat,
+                                                  const double* __restrict__ bnorm, const int32_t* __restrict__ conv,
+                                                  int32_t* __restrict__ convit, BGState* st, double rtol, int maxit,
+                                                  int j, int m, double* __restrict__ fsc, int64_t GT,
+                                                  const cudaGraphConditionalHandle* __restrict__ hs) {
+    __shared__ int s_it;
+    if (threadIdx.x == 0) s_it = ++st->it;
+    __syncthreads();
+    const int it = s_it;
+    int open = 0;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        if (conv[p]) continue;
+        const double est = stat[2 * p];
+        const bool brk = stat[2 * p + 1] != 0.0;
+        if (est <= rtol * bnorm[p]) {
+            if (convit[p] < 0) convit[p] = it;
+            bg_freeze(fsc, GT, p);
+        } else if (!brk) {
+            open = 1;
+        }
+    }
+    open = __syncthreads_or(open);
+    if (threadIdx.x == 0 && j + 1 < m) cudaGraphSetConditional(hs[j + 1], (open && it < maxit) ? 1u : 0u);
+}
+
+// end of a cycle (START statistics of the true residuals in stat): converged
+// problems, and whether another cycle runs
+__global__ void __launch_bounds__(BG_T) k_bg_cycle_end(int P, const double* __restrict__ stat,
+                                                       const double* __restrict__ bnorm, int32_t* __restrict__ conv,
+                                                       int32_t* __restrict__ convit, BGState* st, double rtol,
+                                                       int maxit, cudaGraphConditionalHandle h_outer) {
+    const int it = st->it;
+    int open = 0;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const double beta = stat[2 * p];
+        if (beta <= rtol * bnorm[p] || !(bnorm[p] > 0.0)) {
+            if (!conv[p] && convit[p] < 0) convit[p] = it;
+            conv[p] = 1;
+        } else {
+            conv[p] = 0;  // the estimate was optimistic: iterate again
+            convit[p] = -1;
+            open = 1;
+        }
+    }
+    open = __syncthreads_or(open);
+    if (threadIdx.x == 0) {
+        ++st->cycles;
+        cudaGraphSetConditional(h_outer, (open && it < maxit) ? 1u : 0u);
+    }
+}
+
+// per-problem results from the final START statistics
+__global__ void __launch_bounds__(BG_T) k_bg_final(int P, const double* __restrict__ stat,
+                                                   const double* __restrict__ bnorm,
+                                                   const int32_t* __restrict__ convit, const BGState* st,
+                                                   int32_t* __restrict__ its, double* __restrict__ relres) {
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        relres[p] = bnorm[p] > 0.0 ? stat[2 * p] / bnorm[p] : 0.0;
+        its[p] = convit[p] >= 0 ? convit[p] : st->it;
+    }
+}
+
+// a conditional node appended to the graph the stream is capturing; returns its body
+hho_status add_conditional(hho_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType ty,
+                           cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraph_t cg = nullptr;
+    HHO_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = ty;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    HHO_CUDA(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    HHO_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return HHO_OK;
+}
+
+}  // namespace
+
+// Capture the graph of a batch solve (x, restart, rtol and maxit are baked in).
+// The library's kernels are launched on ctx->stream, which is pointed at the
+// stream capturing each part in turn; the V-cycle is captured by its direct
+// launches.
+static hho_status batch_graph_build(hho_ctx* ctx, BatchWork* B, double rtol, int maxit, int restart, double* x) {
+    const LevelMat& L0 = ctx->levels[0];
+    const int P = ctx->probs.P;
+    const int64_t n = L0.n;
+    Seg S{ctx, B, TileView{B->nt, B->tile_prob, B->tile_r0, B->tile_len}, n, (gs_layout(restart).total + 7) / 8 * 8,
+          gs_layout(restart), P};
+    const GS& G = S.G;
+    if (B->gP != P || !B->d_bnorm) {
+        void* ps[] = {B->d_bnorm, B->d_relres, B->d_conv, B->d_convit, B->d_its, B->d_state, B->d_handles};
+        for (void* q : ps) dfree(q);
+        B->d_bnorm = B->d_relres = nullptr;
+        B->d_conv = B->d_convit = B->d_its = nullptr;
+        B->d_state = nullptr;
+        B->d_handles = nullptr;
+        B->gP = 0;
+        HHO_TRY(dalloc(ctx, &B->d_bnorm, (size_t)P));
+        HHO_TRY(dalloc(ctx, &B->d_relres, (size_t)P));
+        HHO_TRY(dalloc(ctx, &B->d_conv, (size_t)P));
+        HHO_TRY(dalloc(ctx, &B->d_convit, (size_t)P));
+        HHO_TRY(dalloc(ctx, &B->d_its, (size_t)P));
+        HHO_TRY(dalloc(ctx, &B->d_state, 1));
+        HHO_TRY(dalloc(ctx, &B->d_handles, (size_t)MMAX));
+        B->gP = P;
+    }
+    if (!B->s_body) HHO_CUDA(cudaStreamCreateWithFlags(&B->s_body, cudaStreamNonBlocking));
+    batch_graph_free(ctx);
+    cudaStream_t main = ctx->stream;
+    const bool saved_graphs = ctx->use_graphs;
+    const int64_t saved_launches = ctx->launches;
+    ctx->use_graphs = false;  // the V-cycle's own kernels go into this graph
+    cudaGraph_t g = nullptr;
+    hho_status st = HHO_OK;
+    auto fail = [&](hho_status e) {
+        st = e;
+        return e;
+    };
+    do {
+        if (cudaGraphCreate(&g, 0) != cudaSuccess) { fail(HHO_ERR_CUDA); break; }
+        cudaGraphConditionalHandle h_outer;
+        if (cudaGraphConditionalHandleCreate(&h_outer, g, 0, 0) != cudaSuccess) { fail(HHO_ERR_CUDA); break; }
+        // prologue: b, x = 0, ||b_p||, w = b, tolerances
+        if (cudaStreamBeginCaptureToGraph(main, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            fail(HHO_ERR_CUDA);
+            break;
+        }
+        int64_t l0 = ctx->launches;
+        k_copy<<<grid1d(n), 256, 0, main>>>(n, ctx->rhs, B->b);
+        k_zero<<<grid1d(n), 256, 0, main>>>(n, x);
+        ctx->launches += 2;
+        hho_status e = null_project<double>(ctx, L0.nf * L0.b, L0.nP, B->b);
+        if (e == HHO_OK) e = S.upd_dot(B->b, nullptr, 0, 0, 0.0, B->b, 1, 0, 0, HOOK_START, 0, true);
+        k_copy<<<grid1d(n), 256, 0, main>>>(n, B->b, B->w);
+        k_bg_init<<<1, BG_T, 0, main>>>(P, B->stat, B->d_bnorm, B->d_conv, B->d_convit, B->d_state, maxit, h_outer);
+        ctx->launches += 2;
+        cudaGraph_t body = nullptr;
+        if (e == HHO_OK) e = add_conditional(ctx, main, h_outer, cudaGraphCondTypeWhile, &body);
+        if (e != HHO_OK) { fail(e); cudaGraph_t t; cudaStreamEndCapture(main, &t); break; }
+        // epilogue: the pressure kernels' projection and the final statistics
+        if (ctx->has_null) {
+            e = null_project<double>(ctx, L0.nf * L0.b, L0.nP, x);
+            if (e == HHO_OK) e = residual(ctx, 0, x, B->b, B->w);
+            if (e == HHO_OK) e = S.upd_dot(B->w, nullptr, 0, 0, 0.0, B->w, 1, 0, 0, HOOK_START, 0, true);
+        }
+        k_bg_final<<<1, BG_T, 0, main>>>(P, B->stat, B->d_bnorm, B->d_convit, B->d_state, B->d_its, B->d_relres);
+        ++ctx->launches;
+        cudaGraph_t tmp = nullptr;
+        if (cudaStreamEndCapture(main, &tmp) != cudaSuccess || e != HHO_OK) { fail(e != HHO_OK ? e : HHO_ERR_CUDA); break; }
+        B->g_launch_fixed = ctx->launches - l0;
+        // the restart cycle (WHILE body)
+        std::vector<cudaGraphConditionalHandle> hs(restart);
+        bool ok = true;
+        for (int j = 0; j < restart && ok; ++j) ok = cudaGraphConditionalHandleCreate(&hs[j], body, 0, 0) == cudaSuccess;
+        if (!ok || cudaMemcpy(B->d_handles, hs.data(), restart * sizeof(cudaGraphConditionalHandle),
+                              cudaMemcpyHostToDevice) != cudaSuccess) { fail(HHO_ERR_CUDA); break; }
+        ctx->stream = B->s_body;
+        if (cudaStreamBeginCaptureToGraph(B->s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+            cudaSuccess) { fail(HHO_ERR_CUDA); break; }
+        l0 = ctx->launches;
+        k_bg_cycle_start<<<1, BG_T, 0, B->s_body>>>(P, B->d_conv, B->fsc, S.GT, B->d_handles, restart);
+        k_seg_scale<<<B->nt, BT, 0, B->s_body>>>(S.tv, B->w, B->V, B->fsc, S.GT);
+        ctx->launches += 2;
+        std::vector<cudaGraph_t> ifb(restart, nullptr);
+        for (int j = 0; j < restart && e == HHO_OK; ++j) e = add_conditional(ctx, B->s_body, hs[j], cudaGraphCondTypeIf, &ifb[j]);
+        k_seg_update_x<<<B->nt, BT, (size_t)((G.m + 1) * G.m + G.m) * sizeof(double), B->s_body>>>(S.tv, x, B->Z, n,
+                                                                                                 B->fsc, S.GT, G);
+        ++ctx->launches;
+        if (e == HHO_OK) e = residual(ctx, 0, x, B->b, B->w);
+        if (e == HHO_OK) e = S.upd_dot(B->w, nullptr, 0, 0, 0.0, B->w, 1, 0, 0, HOOK_START, 0, true);
+        k_bg_cycle_end<<<1, BG_T, 0, B->s_body>>>(P, B->stat, B->d_bnorm, B->d_conv, B->d_convit, B->d_state, rtol,
+                                                  maxit, h_outer);
+        ++ctx->launches;
+        if (cudaStreamEndCapture(B->s_body, &tmp) != cudaSuccess || e != HHO_OK) { fail(e != HHO_OK ? e : HHO_ERR_CUDA); break; }
+        B->g_launch_cycle = ctx->launches - l0;
+        // the Arnoldi steps (IF bodies)
+        for (int j = 0; j < restart && e == HHO_OK; ++j) {
+            if (cudaStreamBeginCaptureToGraph(B->s_body, ifb[j], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+                cudaSuccess) { e = HHO_ERR_CUDA; break; }
+            l0 = ctx->launches;
+            double* vj = B->V + (int64_t)j * n;
+            double* zj = B->Z + (int64_t)j * n;
+            if (j > 0) {
+                k_seg_scale<<<B->nt, BT, 0, B->s_body>>>(S.tv, B->w, vj, B->fsc, S.GT);
+                ++ctx->launches;
+            }
+            e = vcycle(ctx, vj, zj);
+            if (e == HHO_OK) e = spmv(ctx, 0, zj, B->w);
+            const int nv = j + 1;
+            if (e == HHO_OK) e = S.upd_dot(B->w, nullptr, 0, 0, 0.0, B->V, nv, 0, G.t1, HOOK_NONE, j, false);
+            if (e == HHO_OK) e = S.upd_dot(B->w, B->V, nv, G.t1, -1.0, B->V, nv, 0, G.t2, HOOK_NONE, j, false);
+            if (e == HHO_OK) e = S.upd_dot(B->w, B->V, nv, G.t2, -1.0, nullptr, 0, 1, G.nrm, HOOK_COLUMN, j, true);
+            // the step's test: freezes the problems that met the tolerance and opens step j + 1
+            k_bg_iter<<<1, BG_T, 0, B->s_body>>>(P, B->stat, B->d_bnorm, B->d_conv, B->d_convit, B->d_state, rtol,
+                                                 maxit, j, restart, B->fsc, S.GT, B->d_handles);
+            ++ctx->launches;
+            if (cudaStreamEndCapture(B->s_body, &tmp) != cudaSuccess && e == HHO_OK) e = HHO_ERR_CUDA;
+            if (j == 0) B->g_launch_iter = ctx->launches - l0 + 1;  // + the scaling of the later steps
+        }
+        if (e != HHO_OK) { fail(e); break; }
+        if (cudaGraphInstantiate(&B->gexec, g, 0) != cudaSuccess) { fail(HHO_ERR_CUDA); break; }
+        B->graph = g;
+        g = nullptr;
+        B->g_x = x;
+        B->g_rtol = rtol;
+        B->g_maxit = maxit;
+        B->g_restart = restart;
+    } while (false);
+    ctx->stream = main;
+    ctx->use_graphs = saved_graphs;
+    ctx->launches = saved_launches;
+    if (g) cudaGraphDestroy(g);
+    if (st != HHO_OK) {
+        cudaGetLastError();
+        if (ctx->err.empty() || st == HHO_ERR_CUDA) ctx->err = "hho_solve_batch: capturing the solve graph failed";
+    }
+    return st;
+}
+
+static hho_status batch_solve_graph(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, int32_t* its,
+                                    double* relres, hho_solve_info* info) {
+    BatchWork* B = ctx->batch;
+    const int P = ctx->probs.P;
+    if (!B->gexec || B->g_x != x || B->g_rtol != rtol || B->g_maxit != maxit || B->g_restart != restart)
+        HHO_TRY(batch_graph_build(ctx, B, rtol, maxit, restart, x));
+    cudaEvent_t e0, e1;
+    HHO_CUDA(cudaEventCreate(&e0));
+    HHO_CUDA(cudaEventCreate(&e1));
+    HHO_CUDA(cudaEventRecord(e0, ctx->stream));
+    HHO_CUDA(cudaGraphLaunch(B->gexec, ctx->stream));
+    HHO_CUDA(cudaEventRecord(e1, ctx->stream));
+    std::vector<int32_t> hits(P);
+    std::vector<double> hrr(P);
+    BGState hst{};
+    HHO_CUDA(cudaMemcpyAsync(hits.data(), B->d_its, P * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    HHO_CUDA(cudaMemcpyAsync(hrr.data(), B->d_relres, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    HHO_CUDA(cudaMemcpyAsync(&hst, B->d_state, sizeof(BGState), cudaMemcpyDeviceToHost, ctx->stream));
+    HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->launches += B->g_launch_fixed + (int64_t)hst.cycles * B->g_launch_cycle + (int64_t)hst.it * B->g_launch_iter;
+    ctx->coarse_its_total = hst.it;
+    double worst = 0.0;
+    bool ok = true;
+    for (int p = 0; p < P; ++p) {
+        if (relres) relres[p] = hrr[p];
+        if (its) its[p] = hits[p];
+        worst = std::max(worst, hrr[p]);
+        ok &= hrr[p] <= rtol;
+    }
+    const hho_status st = ok ? HHO_OK : HHO_ERR_NOT_CONVERGED;
+    if (info) {
+        info->iterations = hst.it;
+        info->coarse_iterations = hst.it;
+        info->rel_residual = worst;
+        info->solve_ms = ms;
+        info->status = st;
+    }
+    if (st != HHO_OK) ctx->err = "hho_solve_batch: some problem reached maxit above the tolerance";
+    return st;
+}
+
 hho_status batch_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, int32_t* its, double* relres,
                        hho_solve_info* info) {
     if (restart < 1 || restart > MMAX || maxit < 0 || !(rtol > 0.0)) {
@@ -376,6 +732,7 @@ hho_status batch_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double
         return HHO_ERR_ARG;
     }
     HHO_TRY(batch_work(ctx, restart));
+    if (ctx->solve_graph && ctx->stream != nullptr) return batch_solve_graph(ctx, rtol, maxit, restart, x, its, relres, info);
     BatchWork* B = ctx->batch;
     const LevelMat& L0 = ctx->levels[0];
     const int P = ctx->probs.P;

@@ -331,6 +331,10 @@ hho_status hho_set_option(hho_ctx* ctx, const char* key, double value) {
         else ctx->spmv_grid = (int)value;
         return HHO_OK;
     }
+    if (k == "solve_graph") {
+        ctx->solve_graph = value != 0.0 ? 1 : 0;
+        return HHO_OK;
+    }
     if (k == "spmv_warp") {
         ctx->spmv_warp = value != 0.0 ? 1 : 0;
         return HHO_OK;

@@ -186,6 +186,7 @@ struct hho_ctx {
     bool use_graphs = true;              // replay captured V-cycles
     int spmv_rows = 0;                   // rows per thread of the operator kernels (0 = automatic)
     int spmv_grid = 0;                   // blocks of the operator kernels (0 = automatic)
+    int solve_graph = 1;                 // hho_solve_batch as one captured CUDA graph (device-side control)
     int spmv_warp = 1;                   // FP32 operator of large 3D face blocks: warp per face (1) or
                                          // a face's rows split over two threads (0)
 };
@@ -274,6 +275,7 @@ hho_status batch_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double
                        double* relres, hho_solve_info* info);
 hho_status autotune(hho_ctx* ctx, int reps, double* choice);
 void batch_free(hho_ctx* ctx);
+void batch_graph_free(hho_ctx* ctx);
 // coarse.cu
 hho_status coarse_setup(hho_ctx* ctx);
 hho_status coarse_apply(hho_ctx* ctx, const double* d, double* c);

@@ -749,8 +749,9 @@ __global__ void __launch_bounds__(RT, 4) k_spmv_v(LV<float> L, Items it, const f
     if (nv + self > 0) finish_dots(dacc, nv, self, partial, counter, out, hook, sc, gsl, j);
 }
 
-// Lane layout of the warp-per-face kernels for the 3D face blocks (B = 9, 18,
-// 30 unknowns): a lane loads VW consecutive rows of one column with one
+// Lane layout of the warp-per-face kernels for the large 3D face blocks (B = 18
+// and 30 unknowns; smaller blocks keep one thread per face, which measured
+// faster for B = 9): a lane loads VW consecutive rows of one column with one
 // VW * 4-byte load; RL = B / VW lanes cover a column and GC = 32 / RL columns
 // are read by one warp instruction (lane = g * RL + rr: column group g, rows
 // rr * VW ..); each lane accumulates its rows over the columns c = g (mod GC)
@@ -802,6 +803,7 @@ __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t
                                              double* __restrict__ out, int hook, double* sc, GS gsl, int j,
                                              Restr rs) {
     constexpr int VW = wv_vw(B), RL = wv_rl(B), GC = wv_gc(B), NK = wv_nk(B);
+    constexpr int SU = (NK * VW <= 12) ? 2 : 1;  // slots in flight per warp
     const int lane = threadIdx.x & 31;
     const int g = lane / RL, rr = lane - g * RL;
     const bool lane_ok = g < GC;
@@ -818,25 +820,35 @@ __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t
             float acc[VW];
 #pragma unroll
             for (int q = 0; q < VW; ++q) acc[q] = 0.f;
-            for (int s = 0; s < ns; ++s) {
-                const int64_t G = L.ff_col[(int64_t)s * nf + F];
-                const float xl = lane < B ? x[G * B + lane] : 0.f;
-                const float* a = L.ff + ((int64_t)s * B * nf + F) * B + rr * VW;
-                float av[NK][VW];
+            // SU slots per iteration: their column-index -> x chains and their
+            // value loads are all issued before the first multiply
+            for (int s0 = 0; s0 < ns; s0 += SU) {
+                float xl[SU];
+                float av[SU][NK][VW];
 #pragma unroll
-                for (int k = 0; k < NK; ++k) {
-                    const int c = k * GC + g;
-                    if (lane_ok && c < B) load_vw<VW>(a + (int64_t)c * nf * B, av[k]);
-                    else
+                for (int u = 0; u < SU; ++u) {
+                    const int s = s0 + u;
+                    const bool has = s < ns;
+                    const int64_t G = has ? L.ff_col[(int64_t)s * nf + F] : 0;
+                    xl[u] = (has && lane < B) ? x[G * B + lane] : 0.f;
+                    const float* a = L.ff + ((int64_t)s * B * nf + F) * B + rr * VW;
 #pragma unroll
-                        for (int q = 0; q < VW; ++q) av[k][q] = 0.f;
+                    for (int k = 0; k < NK; ++k) {
+                        const int c = k * GC + g;
+                        if (has && lane_ok && c < B) load_vw<VW>(a + (int64_t)c * nf * B, av[u][k]);
+                        else
+#pragma unroll
+                            for (int q = 0; q < VW; ++q) av[u][k][q] = 0.f;
+                    }
                 }
 #pragma unroll
-                for (int k = 0; k < NK; ++k) {
-                    const float xc = __shfl_sync(0xffffffffu, xl, (k * GC + g) & 31);
+                for (int u = 0; u < SU; ++u)
 #pragma unroll
-                    for (int q = 0; q < VW; ++q) acc[q] += av[k][q] * xc;
-                }
+                    for (int k = 0; k < NK; ++k) {
+                        const float xc = __shfl_sync(0xffffffffu, xl[u], (k * GC + g) & 31);
+#pragma unroll
+                        for (int q = 0; q < VW; ++q) acc[q] += av[u][k][q] * xc;
+                    }
             }
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
@@ -1237,6 +1249,7 @@ static void free_graphs(Workspace* W) {
 
 void invalidate_graphs(hho_ctx* ctx) {
     if (ctx->ws) free_graphs(ctx->ws);
+    batch_graph_free(ctx);
 }
 
 void free_workspace(hho_ctx* ctx) {
@@ -1390,7 +1403,7 @@ template <int B, int NP>
 static void launch_spmv_v_BN(hho_ctx* ctx, const LevelMat& L, const float* x, const float* bv, float* y, int mode,
                              const float* V, int64_t ld, int nv, int self, double* partial, unsigned* counter,
                              double* out, int hook, double* sc, GS gsl, int j, Restr rs) {
-    if constexpr (B == 9 || B == 18 || B == 30) {  // 3D face blocks: warp per face
+    if constexpr (B == 18 || B == 30) {  // large 3D face blocks: warp per face
         if (ctx->spmv_warp) {
             Items it;
             it.ftiles = L.nf;
@@ -1413,7 +1426,7 @@ static void launch_spmv_v_BN(hho_ctx* ctx, const LevelMat& L, const float* x, co
 template <int B, int NP>
 static void launch_jacobi_v_BN(hho_ctx* ctx, const LevelMat& L, const float* w, const double* den, float* v,
                                float* z, const float* Vp, int64_t ld, int npend, const double* pc) {
-    if constexpr (B == 9 || B == 18 || B == 30) {
+    if constexpr (B == 18 || B == 30) {
         if (ctx->spmv_warp) {
             const int64_t etiles = (L.ne + 31) / 32;
             const int64_t g = std::max<int64_t>(1, std::min<int64_t>((L.nf + etiles + RT / 32 - 1) / (RT / 32), GMAX));

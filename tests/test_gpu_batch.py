@@ -154,3 +154,39 @@ def test_batch_declaration_errors(hho_mod):
     with pytest.raises(hho_mod.HHOError):
         ctx.set_batch(fo, eo)  # after pmg_setup
     ctx.close()
+
+
+@pytest.mark.parametrize("cond", ["v", "vp"])
+def test_graph_captured_solve_equals_host_driven(hho_mod, cond):
+    """hho_solve_batch as one captured CUDA graph (restart cycles in a WHILE
+    node, Arnoldi steps in IF nodes, every convergence test on the device)
+    takes the same decisions as the host-driven loop: identical iteration
+    counts per problem and bitwise-identical solutions; replaying it gives the
+    same result again, and a restart shorter than the iteration count (several
+    cycles) still converges every problem."""
+    ms, flds = _problems()
+    k = 2
+    m, fo, eo, sh = union_mesh(ms, per_row=4)
+    ctx = hho_mod.Context(m, k, cond, stream=torch.cuda.Stream())
+    ctx.set_batch(fo, eo)
+    ctx.assemble(*hho_mod.data_arrays(ctx, BatchField(flds, sh, per_row=4)))
+    ctx.pmg_setup(list(range(k, -1, -1)))
+    n = ctx.ndof(0)
+    res = {}
+    for graph in (0, 1):
+        ctx.set_option("solve_graph", graph)
+        for restart in (50, 4):
+            x = torch.empty(n, dtype=torch.float64, device="cuda")
+            info, its, rr = ctx.solve_batch(x, rtol=1e-9, restart=restart)
+            res[(graph, restart)] = (x.cpu().numpy(), its.copy(), rr.copy(), info["iterations"])
+    for restart in (50, 4):
+        xh, ith, rrh, ih = res[(0, restart)]
+        xg, itg, rrg, ig = res[(1, restart)]
+        assert np.all(rrg <= 1e-9) and ig == ih
+        assert np.array_equal(ith, itg), (ith, itg)
+        assert np.array_equal(xh, xg)
+    ctx.set_option("solve_graph", 1)
+    x2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.solve_batch(x2, rtol=1e-9, restart=4)
+    assert np.array_equal(x2.cpu().numpy(), res[(1, 4)][0])
+    ctx.close()
