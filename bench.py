@@ -91,6 +91,9 @@ def parse():
     ap.add_argument("--batch-n", type=int, default=256, help="problems in the batched workload")
     ap.add_argument("--batch-seed", type=int, default=12345)
     ap.add_argument("--batch-cond", default="v", choices=["v", "vp"])
+    ap.add_argument("--batch-graph", type=int, default=1, choices=[0, 1],
+                    help="1: each group's batched solve is one captured CUDA graph with device-side control; "
+                         "0: host-driven FGMRES loop")
     ap.add_argument("--batch-compare", type=int, default=16,
                     help="problems of the batch also solved one by one for the batching speedup (0: skip)")
     args = ap.parse_args()
@@ -646,6 +649,7 @@ def run_batch(args):
         data = hho.data_arrays(ctx, BatchField([probs[i].field for i in idx], sh))
         ctx.assemble(*data)
         ctx.set_option("coarse_fp32", cf)
+        ctx.set_option("solve_graph", args.batch_graph)
         ctx.pmg_setup(list(range(k, -1, -1)), smooth_its=2, prec=args.prec)
         return ctx, data
 

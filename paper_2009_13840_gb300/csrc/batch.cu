@@ -525,6 +525,10 @@ hho_status add_conditional(hho_ctx* ctx, cudaStream_t s, cudaGraphConditionalHan
     size_t nd = 0;
     cudaGraph_t cg = nullptr;
     HHO_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive || !cg) {
+        ctx->err = "hho_solve_batch: the solve graph's capture was invalidated";
+        return HHO_ERR_CUDA;
+    }
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
@@ -569,6 +573,17 @@ static hho_status batch_graph_build(hho_ctx* ctx, BatchWork* B, double rtol, int
     }
     if (!B->s_body) HHO_CUDA(cudaStreamCreateWithFlags(&B->s_body, cudaStreamNonBlocking));
     batch_graph_free(ctx);
+    {
+        // one direct V-cycle first: a kernel that cannot run is reported here as
+        // an error instead of invalidating the capture
+        const bool g0 = ctx->use_graphs;
+        ctx->use_graphs = false;
+        hho_status e = vcycle(ctx, B->V, B->Z);
+        ctx->use_graphs = g0;
+        HHO_TRY(e);
+        HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+        HHO_CUDA(cudaGetLastError());
+    }
     cudaStream_t main = ctx->stream;
     const bool saved_graphs = ctx->use_graphs;
     const int64_t saved_launches = ctx->launches;

@@ -33,6 +33,19 @@ int sm_count() {
     return s;
 }
 
+int smem_optin() {
+    constexpr int kMaxDev = 64;
+    static int cache[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) dev = -1;
+    if (dev >= 0 && cache[dev] > 0) return cache[dev];
+    int s = 0;
+    if (dev < 0 || cudaDeviceGetAttribute(&s, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || s <= 0)
+        return 48 * 1024;
+    cache[dev] = s;
+    return s;
+}
+
 void dfree(void* p) {
     if (p) cudaFree(p);
 }

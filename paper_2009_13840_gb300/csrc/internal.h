@@ -216,6 +216,29 @@ inline hho_status dalloc(hho_ctx* ctx, T** p, size_t count) {
 void dfree(void* p);
 // streaming multiprocessors of the current device (queried once per device)
 int sm_count();
+// largest dynamic shared memory a block may opt in to on the current device
+int smem_optin();
+// Allow `fn` the device's largest dynamic shared memory.  The limit is a
+// process-wide attribute of the kernel, not of a context, so every context
+// raises it to the maximum rather than to its own need (a later context with
+// smaller fronts must not lower it below an earlier one's); occupancy follows
+// the shared memory a launch actually requests.  HHO_ERR_UNSUPPORTED when
+// `need` exceeds the device's limit.
+template <class F>
+inline hho_status allow_smem(hho_ctx* ctx, F* fn, size_t need) {
+    const int mx = smem_optin();
+    if ((int64_t)need > (int64_t)mx) {
+        ctx->err = "a kernel needs " + std::to_string(need) + " bytes of shared memory, more than the device's " +
+                   std::to_string(mx);
+        return HHO_ERR_UNSUPPORTED;
+    }
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+        return HHO_ERR_CUDA;
+    }
+    return HHO_OK;
+}
 
 // setup.cu
 hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond);

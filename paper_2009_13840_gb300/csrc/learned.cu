@@ -626,22 +626,20 @@ hho_status mlp_init(hho_ctx* ctx, int hidden, uint64_t seed) {
     HHO_CUDA(cudaMemset(M->d_status, 0, sizeof(int)));
     {
         // dynamic shared memory above the default 48 KB where a kernel needs it
-        const int fs = (int)feat_smem(M->din, M->hid), ss = (FB * M->din + FB) * 4;
-        HHO_CUDA(cudaFuncSetAttribute(k_mlp_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs));
-        HHO_CUDA(cudaFuncSetAttribute(k_mlp_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs));
-        HHO_CUDA(cudaFuncSetAttribute(k_train_fwd<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)((FB * M->din + FB * M->hid) * 4)));
-        HHO_CUDA(cudaFuncSetAttribute(k_train_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)((FB * M->din + FB * M->hid) * 4)));
-        HHO_CUDA(cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, ss));
-        HHO_CUDA(cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, ss));
+        const size_t fs = feat_smem(M->din, M->hid), ss = (size_t)(FB * M->din + FB) * 4;
+        const size_t fw = (size_t)(FB * M->din + FB * M->hid) * 4;
+        HHO_TRY(allow_smem(ctx, k_mlp_apply<double>, fs));
+        HHO_TRY(allow_smem(ctx, k_mlp_apply<float>, fs));
+        HHO_TRY(allow_smem(ctx, k_train_fwd<__nv_bfloat16>, fw));
+        HHO_TRY(allow_smem(ctx, k_train_fwd<float>, fw));
+        HHO_TRY(allow_smem(ctx, k_samples, ss));
+        HHO_TRY(allow_smem(ctx, k_features, ss));
         if (M->tc) {
-            const int ts = (int)tc_smem(M->din, M->hid, M->dout);
-            HHO_CUDA(cudaFuncSetAttribute(k_mlp_apply_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts));
-            HHO_CUDA(cudaFuncSetAttribute(k_mlp_apply_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts));
-            HHO_CUDA(cudaFuncSetAttribute(k_train_fwd_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          ts));
-            HHO_CUDA(cudaFuncSetAttribute(k_train_fwd_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, ts));
+            const size_t ts = tc_smem(M->din, M->hid, M->dout);
+            HHO_TRY(allow_smem(ctx, k_mlp_apply_tc<double>, ts));
+            HHO_TRY(allow_smem(ctx, k_mlp_apply_tc<float>, ts));
+            HHO_TRY(allow_smem(ctx, k_train_fwd_tc<__nv_bfloat16>, ts));
+            HHO_TRY(allow_smem(ctx, k_train_fwd_tc<float>, ts));
         }
     }
     const int64_t n1 = (int64_t)M->din * M->hid, n2 = (int64_t)M->hid * M->dout;

@@ -884,7 +884,7 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
         S->smem_bwd64 = std::max(S->smem_bwd64, (size_t)((MF_WARPS + 1) * 64 + nBmax) * 8);
         S->smem_bwd32 = std::max(S->smem_bwd32, (size_t)((MF_WARPS + 1) * 128 + nBmax) * 4);
     }
-    const size_t smem_cap = 227 * 1024;
+    const size_t smem_cap = (size_t)smem_optin();
     if (S->smem_fwd64 > smem_cap || S->smem_bwd64 > smem_cap) {
         delete S;
         ctx->err = "pmg_setup: multifrontal coarse solver: a front exceeds the shared-memory staging of the solve";
@@ -993,10 +993,10 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
         ctx->err = "pmg_setup: multifrontal coarse solver: singular front";
         return HHO_ERR_SINGULAR;
     }
-    HHO_CUDA(cudaFuncSetAttribute(k_mf_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem_fwd64));
-    HHO_CUDA(cudaFuncSetAttribute(k_mf_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem_bwd64));
-    HHO_CUDA(cudaFuncSetAttribute(k_mf_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem_fwd32));
-    HHO_CUDA(cudaFuncSetAttribute(k_mf_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem_bwd32));
+    HHO_TRY(allow_smem(ctx, k_mf_fwd<double>, S->smem_fwd64));
+    HHO_TRY(allow_smem(ctx, k_mf_bwd<double>, S->smem_bwd64));
+    HHO_TRY(allow_smem(ctx, k_mf_fwd<float>, S->smem_fwd32));
+    HHO_TRY(allow_smem(ctx, k_mf_bwd<float>, S->smem_bwd32));
     return HHO_OK;
 }
 

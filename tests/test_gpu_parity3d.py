@@ -207,3 +207,37 @@ def test_multifrontal_coarse_3d(hho_mod, cond, leaf):
     assert worst <= 1e-12, worst
     assert res <= 1e-11, res
     ctx.close()
+
+
+def test_two_contexts_keep_their_coarse_kernels_runnable(hho_mod):
+    """A context created after another with smaller multifrontal fronts must not
+    leave the first one's coarse-solve kernels unable to launch (the kernels'
+    shared-memory limit is a process-wide attribute): the first context's FP32
+    V-cycle, replayed from a captured graph on a side stream, still equals its
+    result from before the second context existed."""
+    stream = torch.cuda.Stream()
+    mesh, fld, h, rhs_o = _oracle(4, 3, "vp")
+    with torch.cuda.stream(stream):
+        a = hho_mod.Context(mesh, 3, "vp", stream=stream)
+        a.assemble(*hho_mod.data_arrays(a, fld))
+        a.set_option("coarse_dense_max", 100)
+        a.set_option("coarse_fp32", 1)
+        a.pmg_setup([3, 2, 1, 0], prec="fp32")
+        r = torch.from_numpy(np.random.default_rng(1).standard_normal(a.ndof(0))).cuda()
+        z0 = torch.empty_like(r)
+        a.vcycle(r, z0)
+        stream.synchronize()
+        from synthetic import tri_mesh
+        from synthetic import fields as F2
+        b = hho_mod.Context(tri_mesh(6, 5, jitter=0.2, seed=2, neumann_sides=(1,)), 1, "v", stream=stream)
+        b.assemble(*hho_mod.data_arrays(b, F2.TrigStokes2D()))
+        b.set_option("coarse_dense_max", 20)
+        b.set_option("coarse_fp32", 1)
+        b.pmg_setup([1, 0], prec="fp32")
+        z1 = torch.empty_like(r)
+        for _ in range(2):  # capture, then replay
+            a.vcycle(r, z1)
+        stream.synchronize()
+        assert torch.equal(z0, z1)
+        b.close()
+        a.close()
