@@ -51,11 +51,13 @@ def _submesh(mesh, elems):
     return sub, elems, faces
 
 
-def residual_rows(mesh, k, cond, field, x, sample_faces):
+def residual_rows(mesh, k, cond, field, x, sample_faces, with_scale=False):
     """(rows, r, b): global indices of the condensed rows of the sampled faces
     and of the kept pressures of their elements, the residual b - S x and the
     right-hand side b on those rows, from the oracle's local systems.  x is the
-    condensed vector of the full mesh (faces then elements)."""
+    condensed vector of the full mesh (faces then elements).  With with_scale,
+    also the scale |b| + |S| |x| of every row (the size of the terms whose
+    difference r is; two evaluations of r in FP64 differ by about eps times it)."""
     sample_faces = np.unique(np.asarray(sample_faces, dtype=np.int64))
     elems = np.unique([int(t) for F in sample_faces for t in mesh.face_elem[int(F)] if t >= 0])
     sub, elems, faces = _submesh(mesh, elems)
@@ -71,19 +73,23 @@ def residual_rows(mesh, k, cond, field, x, sample_faces):
         xs[h.n_face_dofs + i * nP:h.n_face_dofs + (i + 1) * nP] = x[nF_glob * bb + int(t) * nP:
                                                                    nF_glob * bb + (int(t) + 1) * nP]
     r_loc = b_loc - h.S @ xs
-    rows, r, b = [], [], []
+    sc_loc = np.abs(b_loc) + abs(h.S) @ np.abs(xs)
+    rows, r, b, sc = [], [], [], []
     fpos = {int(F): i for i, F in enumerate(faces)}
     for F in sample_faces:
         i = fpos[int(F)]
         rows.extend(int(F) * bb + np.arange(bb))
         r.extend(r_loc[i * bb:(i + 1) * bb])
         b.extend(b_loc[i * bb:(i + 1) * bb])
+        sc.extend(sc_loc[i * bb:(i + 1) * bb])
     for i, t in enumerate(elems):
         o = h.n_face_dofs + i * nP
         rows.extend(nF_glob * bb + int(t) * nP + np.arange(nP))
         r.extend(r_loc[o:o + nP])
         b.extend(b_loc[o:o + nP])
-    return np.asarray(rows), np.asarray(r), np.asarray(b)
+        sc.extend(sc_loc[o:o + nP])
+    out = (np.asarray(rows), np.asarray(r), np.asarray(b))
+    return out + (np.asarray(sc),) if with_scale else out
 
 
 def sample_interior_faces(mesh, count, seed):

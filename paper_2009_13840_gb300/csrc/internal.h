@@ -232,7 +232,16 @@ inline hho_status allow_smem(hho_ctx* ctx, F* fn, size_t need) {
                    std::to_string(mx);
         return HHO_ERR_UNSUPPORTED;
     }
-    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    // the limit covers static and dynamic shared memory together
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e == cudaSuccess && need + fa.sharedSizeBytes > (size_t)mx) {
+        ctx->err = "a kernel needs " + std::to_string(need + fa.sharedSizeBytes) +
+                   " bytes of shared memory, more than the device's " + std::to_string(mx);
+        return HHO_ERR_UNSUPPORTED;
+    }
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess) {
         ctx->err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return HHO_ERR_CUDA;

@@ -399,18 +399,19 @@ __global__ void k_mf_mean_abs_diag(int64_t nf, int64_t ne, int b, int nP, const 
 // ---------------------------------------------------------------------------
 // solve kernels (FP64, or FP32 copies of M1 / X)
 // ---------------------------------------------------------------------------
-template <typename T> struct MFVec;
-template <> struct MFVec<double> {
+// W consecutive rows per lane: the widest 16-byte vector (2 FP64, 4 FP32) on
+// levels with enough row blocks to fill the GPU, one row per lane (32 rows
+// per CTA, 4x / 2x more CTAs) on the few large fronts near the roots
+template <typename T, int W> struct MFVec;
+template <> struct MFVec<double, 2> {
     using V = double2;
-    static constexpr int W = 2;
     __device__ static void fma(double* a, const double2& q, double x) {
         a[0] += q.x * x;
         a[1] += q.y * x;
     }
 };
-template <> struct MFVec<float> {
+template <> struct MFVec<float, 4> {
     using V = float4;
-    static constexpr int W = 4;
     __device__ static void fma(float* a, const float4& q, float x) {
         a[0] += q.x * x;
         a[1] += q.y * x;
@@ -418,18 +419,23 @@ template <> struct MFVec<float> {
         a[3] += q.w * x;
     }
 };
+template <typename T> struct MFVec<T, 1> {
+    using V = T;
+    __device__ static void fma(T* a, const T& q, T x) { a[0] += q * x; }
+};
+template <typename T> constexpr int mf_wide() { return std::is_same<T, float>::value ? 4 : 2; }
 constexpr int MF_UNROLL = 4;
 
 // rows [rb*RB, rb*RB + RB) of the column-major matrix A (ld, ncol columns)
 // times the vector xs (shared memory); lane l of every warp owns W consecutive
 // rows (one 16-byte load per column), warp w takes columns w, w + 8, ...; the
 // warp partials are added in warp order (deterministic).  Results in sred[0..RB).
-template <typename T>
+template <typename T, int W>
 __device__ void block_colmajor_gemv(const T* __restrict__ A, int64_t ld, int nrow, int ncol, const T* xs, int rb,
                                     T* sred) {
-    using DV = MFVec<T>;
+    using DV = MFVec<T, W>;
     using V = typename DV::V;
-    constexpr int W = DV::W, RB = 32 * W;
+    constexpr int RB = 32 * W;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = rb * RB + lane * W;
     T acc[W];
@@ -460,11 +466,11 @@ __device__ void block_colmajor_gemv(const T* __restrict__ A, int64_t ld, int nro
 }
 
 // Forward step of one tree level: one CTA per (node, block of RB front rows).
-template <typename T>
+template <typename T, int W>
 __global__ void __launch_bounds__(MF_T) k_mf_fwd(MFView V, const int32_t* __restrict__ nodes, int rb_max,
                                                 const T* __restrict__ M1all, const T* __restrict__ d,
                                                 T* __restrict__ Y, T* __restrict__ U) {
-    constexpr int RB = 32 * MFVec<T>::W;
+    constexpr int RB = 32 * W;
     extern __shared__ unsigned char mf_smem[];
     T* sred = reinterpret_cast<T*>(mf_smem);           // (MF_WARPS + 1) * RB
     T* f = sred + (MF_WARPS + 1) * RB;                 // m
@@ -482,7 +488,7 @@ __global__ void __launch_bounds__(MF_T) k_mf_fwd(MFView V, const int32_t* __rest
         f[i] = s;
     }
     __syncthreads();
-    block_colmajor_gemv<T>(M1all + V.offM1[v], mf_ld(m), m, nI, f, rb, sred);
+    block_colmajor_gemv<T, W>(M1all + V.offM1[v], mf_ld(m), m, nI, f, rb, sred);
     const T* res = sred + MF_WARPS * RB;
     for (int r = threadIdx.x; r < RB; r += blockDim.x) {
         const int i = rb * RB + r;
@@ -494,11 +500,11 @@ __global__ void __launch_bounds__(MF_T) k_mf_fwd(MFView V, const int32_t* __rest
 
 // Backward step of one tree level: x_I = y - X x_B, written to the global
 // solution (one CTA per (node, block of RB eliminated rows)).
-template <typename T>
+template <typename T, int W>
 __global__ void __launch_bounds__(MF_T) k_mf_bwd(MFView V, const int32_t* __restrict__ nodes, int rb_max,
                                                 const T* __restrict__ Xall, const T* __restrict__ Y,
                                                 T* __restrict__ c) {
-    constexpr int RB = 32 * MFVec<T>::W;
+    constexpr int RB = 32 * W;
     extern __shared__ unsigned char mf_smem[];
     T* sred = reinterpret_cast<T*>(mf_smem);
     T* xb = sred + (MF_WARPS + 1) * RB;
@@ -509,7 +515,7 @@ __global__ void __launch_bounds__(MF_T) k_mf_bwd(MFView V, const int32_t* __rest
     const int32_t* gl = V.glob + V.offP[v];
     for (int j = threadIdx.x; j < nB; j += blockDim.x) xb[j] = c[gl[nI + j]];
     __syncthreads();
-    block_colmajor_gemv<T>(Xall + V.offX[v], mf_ld(nI), nI, nB, xb, rb, sred);
+    block_colmajor_gemv<T, W>(Xall + V.offX[v], mf_ld(nI), nI, nB, xb, rb, sred);
     const T* res = sred + MF_WARPS * RB;
     for (int r = threadIdx.x; r < RB; r += blockDim.x) {
         const int i = rb * RB + r;
@@ -535,7 +541,7 @@ struct MFSolver {
     int nnodes = 0;
     std::vector<int32_t> h_level_ptr, h_level_nodes;  // nodes grouped by height (leaves first)
     std::vector<int> level_rbf64, level_rbf32, level_rbb64, level_rbb32;  // row blocks per node per level
-    std::vector<int> level_mmax, level_nBmax;
+    std::vector<int> level_mmax, level_nBmax, level_nImax;
     int32_t *m = nullptr, *nI = nullptr, *child = nullptr, *pin = nullptr, *glob = nullptr, *cpos = nullptr,
             *level_nodes = nullptr, *leaf_elem_ptr = nullptr, *leaf_elem = nullptr, *elem_loc = nullptr;
     int64_t *offW = nullptr, *offM1 = nullptr, *offX = nullptr, *offP = nullptr, *offY = nullptr, *offU = nullptr,
@@ -875,6 +881,7 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
         S->h_level_ptr.push_back((int32_t)S->h_level_nodes.size());
         S->level_mmax.push_back(mmax);
         S->level_nBmax.push_back(nBmax);
+        S->level_nImax.push_back(nImax);
         S->level_rbf64.push_back((mmax + 63) / 64);
         S->level_rbf32.push_back((mmax + 127) / 128);
         S->level_rbb64.push_back((nImax + 63) / 64);
@@ -993,10 +1000,14 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
         ctx->err = "pmg_setup: multifrontal coarse solver: singular front";
         return HHO_ERR_SINGULAR;
     }
-    HHO_TRY(allow_smem(ctx, k_mf_fwd<double>, S->smem_fwd64));
-    HHO_TRY(allow_smem(ctx, k_mf_bwd<double>, S->smem_bwd64));
-    HHO_TRY(allow_smem(ctx, k_mf_fwd<float>, S->smem_fwd32));
-    HHO_TRY(allow_smem(ctx, k_mf_bwd<float>, S->smem_bwd32));
+    HHO_TRY(allow_smem(ctx, k_mf_fwd<double, 2>, S->smem_fwd64));
+    HHO_TRY(allow_smem(ctx, k_mf_bwd<double, 2>, S->smem_bwd64));
+    HHO_TRY(allow_smem(ctx, k_mf_fwd<float, 4>, S->smem_fwd32));
+    HHO_TRY(allow_smem(ctx, k_mf_bwd<float, 4>, S->smem_bwd32));
+    HHO_TRY(allow_smem(ctx, k_mf_fwd<double, 1>, S->smem_fwd64));
+    HHO_TRY(allow_smem(ctx, k_mf_bwd<double, 1>, S->smem_bwd64));
+    HHO_TRY(allow_smem(ctx, k_mf_fwd<float, 1>, S->smem_fwd32));
+    HHO_TRY(allow_smem(ctx, k_mf_bwd<float, 1>, S->smem_bwd32));
     return HHO_OK;
 }
 
@@ -1023,26 +1034,39 @@ int64_t mf_solve_bytes(const MFSolver* S, int value_bytes) { return (S->nM1 + S-
 template <typename T>
 hho_status mf_apply(hho_ctx* ctx, MFSolver* S, const T* d, T* c) {
     constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int WW = mf_wide<T>();
     const T* M1 = F32 ? (const T*)S->M1f : (const T*)S->M1;
     const T* X = F32 ? (const T*)S->Xf : (const T*)S->X;
     T* Y = F32 ? (T*)S->Yf : (T*)S->Y;
     T* U = F32 ? (T*)S->Uf : (T*)S->U;
     const MFView V = S->view();
     const int H = (int)S->level_mmax.size();
+    const int64_t fill = 2LL * sm_count();  // CTAs below which a level uses one row per lane
+    const size_t red1 = (size_t)(MF_WARPS + 1) * 32 * sizeof(T), redw = (size_t)(MF_WARPS + 1) * 32 * WW * sizeof(T);
     for (int h = 0; h < H; ++h) {
         const int l0 = S->h_level_ptr[h], cnt = S->h_level_ptr[h + 1] - l0;
-        const int rb = F32 ? S->level_rbf32[h] : S->level_rbf64[h];
-        const size_t shm = F32 ? ((size_t)(MF_WARPS + 1) * 128 + S->level_mmax[h]) * 4
-                               : ((size_t)(MF_WARPS + 1) * 64 + S->level_mmax[h]) * 8;
-        k_mf_fwd<T><<<(unsigned)((int64_t)cnt * rb), MF_T, shm, ctx->stream>>>(V, S->level_nodes + l0, rb, M1, d, Y, U);
+        const int mm = S->level_mmax[h];
+        const int rbw = (mm + 32 * WW - 1) / (32 * WW), rb1 = (mm + 31) / 32;
+        const size_t vec = (size_t)mm * sizeof(T);
+        if ((int64_t)cnt * rbw >= fill)
+            k_mf_fwd<T, WW><<<(unsigned)((int64_t)cnt * rbw), MF_T, redw + vec, ctx->stream>>>(V, S->level_nodes + l0,
+                                                                                           rbw, M1, d, Y, U);
+        else
+            k_mf_fwd<T, 1><<<(unsigned)((int64_t)cnt * rb1), MF_T, red1 + vec, ctx->stream>>>(V, S->level_nodes + l0,
+                                                                                          rb1, M1, d, Y, U);
     }
     for (int h = H - 1; h >= 0; --h) {
         const int l0 = S->h_level_ptr[h], cnt = S->h_level_ptr[h + 1] - l0;
-        const int rb = F32 ? S->level_rbb32[h] : S->level_rbb64[h];
-        if (rb == 0) continue;
-        const size_t shm = F32 ? ((size_t)(MF_WARPS + 1) * 128 + S->level_nBmax[h]) * 4
-                               : ((size_t)(MF_WARPS + 1) * 64 + S->level_nBmax[h]) * 8;
-        k_mf_bwd<T><<<(unsigned)((int64_t)cnt * rb), MF_T, shm, ctx->stream>>>(V, S->level_nodes + l0, rb, X, Y, c);
+        const int nImax = S->level_nImax[h];
+        if (nImax == 0) continue;
+        const int rbw = (nImax + 32 * WW - 1) / (32 * WW), rb1 = (nImax + 31) / 32;
+        const size_t vec = (size_t)S->level_nBmax[h] * sizeof(T);
+        if ((int64_t)cnt * rbw >= fill)
+            k_mf_bwd<T, WW><<<(unsigned)((int64_t)cnt * rbw), MF_T, redw + vec, ctx->stream>>>(V, S->level_nodes + l0,
+                                                                                           rbw, X, Y, c);
+        else
+            k_mf_bwd<T, 1><<<(unsigned)((int64_t)cnt * rb1), MF_T, red1 + vec, ctx->stream>>>(V, S->level_nodes + l0,
+                                                                                          rb1, X, Y, c);
     }
     ctx->launches += 2 * H;
     HHO_CUDA(cudaGetLastError());

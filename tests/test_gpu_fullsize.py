@@ -11,7 +11,7 @@ Sec. 4.1.2), so it recomputes them on the submesh around sampled faces
   small parity meshes never exercise);
 * the residual b - S x of the GPU's FGMRES solution (FP32 V-cycle, 1e-8) on
   the sampled rows, recomputed by the oracle: equal to the GPU's own residual
-  on those rows up to rounding (1e-11 of the larger of b and S x there), and,
+  on those rows up to rounding (1e-11 of each row's |b| + |S| |x|), and,
   scaled to the global right-hand side (||r_S|| / ||b|| sqrt(n / |S|)),
   within 1e-6 (the global relative residual is 1e-8; the sampled rows are a
   random subset).  The rows of one face are not compared with the right-hand
@@ -82,9 +82,9 @@ def test_sampled_elements_rhs_and_residual(hho_mod, name, mk, fld, k, cond, schu
     sx = torch.empty_like(x)
     ctx.spmv(0, x, sx)
     bg, sxg = rhs.cpu().numpy(), sx.cpu().numpy()
-    rows, r, b = residual_rows(mesh, k, cond, fld, xs, faces)
+    rows, r, b, sc = residual_rows(mesh, k, cond, fld, xs, faces, with_scale=True)
     e_b = float(np.abs(bg[rows] - b).max() / np.abs(b).max())
-    e_sys = float(np.abs(r - (bg[rows] - sxg[rows])).max() / max(np.abs(bg[rows]).max(), np.abs(sxg[rows]).max()))
+    e_sys = float(np.max(np.abs(r - (bg[rows] - sxg[rows])) / sc))
     e_r = float(np.linalg.norm(r) / np.linalg.norm(bg) * np.sqrt(len(bg) / len(rows)))
     report(f"fullsize-residual {name}", rhs_rows=e_b, system_rows=e_sys, residual_rows_scaled=e_r,
            relres=info["rel_residual"], its=info["iterations"], rows=len(rows))
