@@ -211,6 +211,9 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
  *                       node, Arnoldi steps in IF nodes, every convergence
  *                       test on the device; 0: host-driven loop (one 16-byte
  *                       read per problem and iteration)
+ *   "solve_graph_single" 1: hho_solve (no declared batch, non-default stream)
+ *                       runs the same graph-captured FGMRES with one problem;
+ *                       0 (default): the host-driven FGMRES of hho_solve
  *   "coarse_fp32"       with HHO_FP32: 1 keeps FP32 copies of the coarse
  *                       solver's inverse blocks and runs the coarse solve in
  *                       FP32 (FP32 multiply-adds, no FP64 round trip);

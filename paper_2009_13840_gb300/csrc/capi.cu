@@ -348,6 +348,10 @@ hho_status hho_set_option(hho_ctx* ctx, const char* key, double value) {
         ctx->solve_graph = value != 0.0 ? 1 : 0;
         return HHO_OK;
     }
+    if (k == "solve_graph_single") {
+        ctx->solve_graph_single = value != 0.0 ? 1 : 0;
+        return HHO_OK;
+    }
     if (k == "spmv_warp") {
         ctx->spmv_warp = value != 0.0 ? 1 : 0;
         return HHO_OK;
@@ -409,7 +413,9 @@ hho_status hho_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double* 
         ctx->err = "hho_solve: call hho_assemble and pmg_setup first";
         return HHO_ERR_STATE;
     }
-    const hho_status st = fgmres(ctx, rtol, maxit, restart, d_x, info);
+    const hho_status st = (ctx->solve_graph_single && ctx->stream != nullptr && !ctx->probs.declared)
+                              ? batch_solve(ctx, rtol, maxit, restart, d_x, nullptr, nullptr, info)
+                              : fgmres(ctx, rtol, maxit, restart, d_x, info);
     if (ctx->use_learned && ctx->learned) HHO_TRY(mlp_status(ctx));
     return st;
 }

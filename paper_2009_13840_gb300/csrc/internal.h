@@ -187,6 +187,8 @@ struct hho_ctx {
     int spmv_rows = 0;                   // rows per thread of the operator kernels (0 = automatic)
     int spmv_grid = 0;                   // blocks of the operator kernels (0 = automatic)
     int solve_graph = 1;                 // hho_solve_batch as one captured CUDA graph (device-side control)
+    int solve_graph_single = 0;          // hho_solve through the same graph (one problem) instead of the
+                                         // host-driven FGMRES
     int spmv_warp = 1;                   // FP32 operator of large 3D face blocks: warp per face (1) or
                                          // a face's rows split over two threads (0)
 };

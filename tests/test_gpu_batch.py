@@ -190,3 +190,32 @@ def test_graph_captured_solve_equals_host_driven(hho_mod, cond):
     ctx.solve_batch(x2, rtol=1e-9, restart=4)
     assert np.array_equal(x2.cpu().numpy(), res[(1, 4)][0])
     ctx.close()
+
+
+@pytest.mark.parametrize("cond", ["v", "vp"])
+def test_single_solve_through_the_graph(hho_mod, cond):
+    """hho_solve with option solve_graph_single runs the graph-captured FGMRES
+    on one problem: same tolerance reached, solution within 1e-8 of the
+    host-driven FGMRES's (both solve to 1e-10), and replays give the same
+    iterate bitwise."""
+    from synthetic import fields
+    mesh = tri_mesh(13, 11, jitter=0.2, seed=3, neumann_sides=(1,)) if cond == "v" else quad_mesh(9, 8, jitter=0.15,
+                                                                                                  seed=2)
+    k = 2
+    ctx = hho_mod.Context(mesh, k, cond, stream=torch.cuda.Stream())
+    ctx.assemble(*hho_mod.data_arrays(ctx, fields.TrigStokes2D()))
+    ctx.pmg_setup(list(range(k, -1, -1)), prec="fp32")
+    n = ctx.ndof(0)
+    x0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    i0 = ctx.solve(x0, rtol=1e-10)
+    ctx.set_option("solve_graph_single", 1)
+    x1 = torch.empty(n, dtype=torch.float64, device="cuda")
+    i1 = ctx.solve(x1, rtol=1e-10)
+    x2 = torch.empty_like(x1)
+    x2.copy_(x1)
+    ctx.solve(x1, rtol=1e-10)
+    assert i1["rel_residual"] <= 1e-10 and i0["rel_residual"] <= 1e-10
+    assert abs(i1["iterations"] - i0["iterations"]) <= 2, (i0, i1)
+    assert (torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0)).item() < 1e-8
+    assert torch.equal(x1, x2)
+    ctx.close()
