@@ -4,7 +4,8 @@
   orthonormal bases the restriction keeps, per face and per velocity component,
   the first dim P^{k_{l+1}}_{d-1} coefficients, and per element the first
   n_P(k_{l+1}) pressure coefficients (n_P = 1 for v&p-cond); prolongation is
-  its transpose (zero padding).
+  its transpose (zero padding).  For HHO-hp (Scheme 2) the face pressure is one
+  more face component truncated the same way, and there are no element rows.
 * Coarse operators (Sec. 4.2): S^{l+1} = I^{l+1}_l S^l I^l_{l+1}, formed here
   as a sparse triple product with the selection matrix.
 * V-cycle (Sec. 3.3, Algorithm MG_V): pre-smooth, restrict the defect, solve
@@ -36,6 +37,20 @@ import scipy.sparse.linalg as spla
 from .basis import dim_P
 
 
+def n_comp(d, cond):
+    """Components of a face block: d velocity components, plus the face
+    pressure for HHO-hp (Scheme 2)."""
+    return d + 1 if cond == "hp" else d
+
+
+def n_pres(d, k_l, cond):
+    """Kept pressure coefficients per element: the mean for v&p-cond, all of
+    P^k_l for v-cond, none for HHO-hp (its element pressure is eliminated)."""
+    if cond == "hp":
+        return 0
+    return 1 if cond == "vp" else dim_P(d, k_l)
+
+
 class Level:
     """One level of the hierarchy: matrix, block layout and smoother data."""
 
@@ -43,8 +58,8 @@ class Level:
         self.S = S.tocsr()
         self.k = k_l
         self.nF = dim_P(d - 1, k_l)
-        self.b = d * self.nF
-        self.nP = 1 if cond == "vp" else dim_P(d, k_l)
+        self.b = n_comp(d, cond) * self.nF
+        self.nP = n_pres(d, k_l, cond)
         self.nf = mesh.n_face
         self.ne = mesh.n_elem
         self.n = self.nf * self.b + self.ne * self.nP
@@ -67,7 +82,7 @@ class Level:
             sl = self.face_slice(F)
             self.Dinv.append(np.linalg.inv(S[sl, sl].toarray()))
         self.Minv = []
-        for T in range(self.ne):
+        for T in range(self.ne if self.nP > 0 else 0):
             st = self.elem_slice(T)
             M = S[st, st].toarray()
             for F in self.mesh.faces_of(T):
@@ -80,7 +95,7 @@ class Level:
         for F in range(self.nf):
             sl = self.face_slice(F)
             z[sl] = self.Dinv[F] @ r[sl]
-        for T in range(self.ne):
+        for T in range(len(self.Minv)):
             st = self.elem_slice(T)
             z[st] = self.Minv[T] @ r[st]
         return z
@@ -89,12 +104,12 @@ class Level:
 def restriction(mesh, d, k_fine, k_coarse, cond):
     """Selection matrix I^{l+1}_l (Sec. 4.2: unit-diagonal local restrictions)."""
     nFf, nFc = dim_P(d - 1, k_fine), dim_P(d - 1, k_coarse)
-    bf, bc = d * nFf, d * nFc
-    nPf = 1 if cond == "vp" else dim_P(d, k_fine)
-    nPc = 1 if cond == "vp" else dim_P(d, k_coarse)
+    nc_ = n_comp(d, cond)
+    bf, bc = nc_ * nFf, nc_ * nFc
+    nPf, nPc = n_pres(d, k_fine, cond), n_pres(d, k_coarse, cond)
     rows, cols = [], []
     for F in range(mesh.n_face):
-        for c in range(d):
+        for c in range(nc_):
             for j in range(nFc):
                 rows.append(F * bc + c * nFc + j)
                 cols.append(F * bf + c * nFf + j)
@@ -227,8 +242,12 @@ class PMG:
         self.null = None
         if not mesh.has_neumann():
             n = np.zeros(L.n)
-            for T in range(L.ne):
-                n[L.elem_slice(T).start] = np.sqrt(hho.elems[T].meas)
+            if cond == "hp":  # constant hybrid pressure: the constant mode of every face pressure
+                for F in range(L.nf):
+                    n[F * L.b + d * L.nF] = np.sqrt(hho.faces[F].meas)
+            else:
+                for T in range(L.ne):
+                    n[L.elem_slice(T).start] = np.sqrt(hho.elems[T].meas)
             self.null = n / np.linalg.norm(n)
         if coarse == "lu":
             A = L.S.toarray()
@@ -240,7 +259,7 @@ class PMG:
             A = L.S.tocsc().astype(np.float64)
             if self.null is not None:
                 alpha = float(np.mean(np.abs(A.diagonal())))
-                pin = L.elem_slice(0).start
+                pin = d * L.nF if cond == "hp" else L.elem_slice(0).start
                 A = (A + sp.csc_matrix(([alpha], ([pin], [pin])), shape=A.shape)).tocsc()
             self.splu = spla.splu(A)
         self.coarse_its = []
