@@ -53,6 +53,9 @@ SPECS = {
     "c2": dict(mesh="tri", n=128, k=3, cond="v", prec="fp32", coarse_fp32=1, sample_n=24),
     "c1": dict(mesh="quad", n=16, k=3, cond="vp", prec="fp64", coarse_fp32=0, sample_n=16),
     "learned": dict(mesh="hex", n=48, k=3, cond="vp", prec="fp32", coarse_fp32=1, sample_n=4),
+    # HHO-hp (Scheme 2) on the C2 and C3 meshes
+    "hp2": dict(mesh="tri", n=128, k=3, cond="hp", prec="fp32", coarse_fp32=1, sample_n=24),
+    "hp3": dict(mesh="hex", n=32, k=3, cond="hp", prec="fp32", coarse_fp32=1, sample_n=4),
 }
 
 
@@ -62,17 +65,20 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "sweep", "batch", "learned"],
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "sweep", "batch", "learned", "hp2", "hp3"],
                     help="c3: 32^3 jittered hexahedra, k=3, v&p (default); c2: 128x128 jittered triangles, k=3, "
                          "v-cond; c1: 16x16 quadrilaterals, k=3, v&p, FP64; sweep: the c2 mesh over k=1..5, both "
                          "condensations, FP64 and FP32 V-cycles; batch: many independent small problems; learned: "
-                         "the learned smoother against the plain one")
+                         "the learned smoother against the plain one; hp2 / hp3: HHO-hp (Scheme 2) on the c2 "
+                         "triangle mesh (k=3) and the c3 hexahedral mesh (k=3)")
     ap.add_argument("--mesh", default=None, choices=["tri", "hex", "quad"],
                     help="override the workload's mesh family (tri: n x n squares split into triangles; hex: n^3 "
                          "jittered hexahedra; quad: n x n quadrilaterals)")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--k", type=int, default=None)
-    ap.add_argument("--cond", default=None, choices=["v", "vp"])
+    ap.add_argument("--cond", default=None, choices=["v", "vp", "hp"],
+                    help="Scheme 1 with velocity-only (v) or velocity-pressure (vp) condensation, or Scheme 2 "
+                         "(HHO-hp, hybrid pressure, every element unknown condensed)")
     ap.add_argument("--prec", default=None, choices=["fp32", "fp64"], help="V-cycle precision of the headline")
     ap.add_argument("--coarse-fp32", type=int, default=None, choices=[0, 1],
                     help="FP32 coarse solve inside the FP32 V-cycle")
@@ -215,18 +221,26 @@ def one_thread():
         return contextlib.nullcontext()
 
 
+def oracle_disc(mesh, k, cond):
+    """The oracle's discretisation: Scheme 1 (v, vp) or Scheme 2 (hp)."""
+    if cond == "hp":
+        from oracle.hho_hp import HHOhp
+        return HHOhp(mesh, k)
+    from oracle.hho import HHO
+    return HHO(mesh, k, cond)
+
+
 def oracle_sample(args, steps=1):
     """The oracle as it stands on a bounded sample of the workload family: the
     hierarchy is built once (timed as setup), then `steps` FGMRES solves are
     timed.  Returns (DOF/s of the last solve, ndof, its, solve seconds, setup
     seconds)."""
-    from oracle.hho import HHO
     from oracle.pmg import PMG, fgmres
     n_s = args.sample_n
     mesh, fld, _ = workload(n_s, args.k, args.cond, args.mesh)
     with one_thread():
         t0 = time.perf_counter()
-        h = HHO(mesh, args.k, args.cond)
+        h = oracle_disc(mesh, args.k, args.cond)
         rhs = h.assemble_rhs(*h.data_values(fld))
         pmg = PMG(h, list(range(args.k, -1, -1)))
         t_setup = time.perf_counter() - t0
@@ -275,8 +289,8 @@ def level_counts(mesh, k_l, cond):
     degree k_l: the face-block operator of the condensed system (stored blocks
     of every face row and element row) and the block-Jacobi data."""
     d = mesh.dim
-    b = d * _dimP(d - 1, k_l)
-    nP = 1 if cond == "vp" else _dimP(d, k_l)
+    b = (d + 1 if cond == "hp" else d) * _dimP(d - 1, k_l)  # HHO-hp: face pressure as one more component
+    nP = 0 if cond == "hp" else 1 if cond == "vp" else _dimP(d, k_l)
     nf, ne = mesh.n_face, mesh.n_elem
     N = np.diff(mesh.elem_face_ptr)
     fe = mesh.face_elem
@@ -317,8 +331,9 @@ def oracle_check(mesh, k, cond, fld, x, b_gpu, Sx_gpu, faces, seed=0):
     systems (oracle/sampled.py) at sampled faces and their elements' kept
     pressures: the oracle's residual b - S x of the GPU solution x on those
     rows against the GPU's own residual there, relative to each row's scale
-    |b| + |S| |x| (equal up to rounding when both sides build the same
-    system), and the oracle's residual on the rows scaled
+    |b_i| + sum_T max|S_T| ||x_T||_1 (the bound that element Schur complements
+    agreeing to a relative eps put on the rows: eps times it), and the
+    oracle's residual on the rows scaled
     to the global right-hand side (||r_S|| / ||b|| * sqrt(n / |S|), an estimate
     of the global relative residual)."""
     from oracle.sampled import residual_rows, sample_interior_faces

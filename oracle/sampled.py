@@ -19,6 +19,7 @@ from __future__ import annotations
 import numpy as np
 
 from .hho import HHO
+from .hho_hp import HHOhp
 
 
 def _submesh(mesh, elems):
@@ -53,15 +54,18 @@ def _submesh(mesh, elems):
 
 def residual_rows(mesh, k, cond, field, x, sample_faces, with_scale=False):
     """(rows, r, b): global indices of the condensed rows of the sampled faces
-    and of the kept pressures of their elements, the residual b - S x and the
+    and of the kept pressures of their elements (none for HHO-hp, cond "hp"), the residual b - S x and the
     right-hand side b on those rows, from the oracle's local systems.  x is the
     condensed vector of the full mesh (faces then elements).  With with_scale,
-    also the scale |b| + |S| |x| of every row (the size of the terms whose
-    difference r is; two evaluations of r in FP64 differ by about eps times it)."""
+    also the scale |b_i| + sum over the elements T of row i of
+    max|S_T| ||x_T||_1 (x_T: the element's kept unknowns).  Row i of S x is the
+    sum of the rows of S_T x_T (end of Sec. 4.1.2), so two element Schur
+    complements that agree to eps of their largest entry give rows of S x
+    that agree to eps times this scale; it bounds |b| + |S| |x| from above."""
     sample_faces = np.unique(np.asarray(sample_faces, dtype=np.int64))
     elems = np.unique([int(t) for F in sample_faces for t in mesh.face_elem[int(F)] if t >= 0])
     sub, elems, faces = _submesh(mesh, elems)
-    h = HHO(sub, k, cond)
+    h = HHOhp(sub, k) if cond == "hp" else HHO(sub, k, cond)
     b_loc = h.assemble_rhs(*h.data_values(field))
     nF_glob = mesh.n_face
     bb, nP = h.b, h.nP
@@ -73,7 +77,10 @@ def residual_rows(mesh, k, cond, field, x, sample_faces, with_scale=False):
         xs[h.n_face_dofs + i * nP:h.n_face_dofs + (i + 1) * nP] = x[nF_glob * bb + int(t) * nP:
                                                                    nF_glob * bb + (int(t) + 1) * nP]
     r_loc = b_loc - h.S @ xs
-    sc_loc = np.abs(b_loc) + abs(h.S) @ np.abs(xs)
+    sc_loc = np.abs(b_loc)
+    for t in range(len(elems)):
+        g = h.global_kept(t)
+        sc_loc[g] += np.abs(h.S_T[t]).max() * np.abs(xs[g]).sum()
     rows, r, b, sc = [], [], [], []
     fpos = {int(F): i for i, F in enumerate(faces)}
     for F in sample_faces:

@@ -11,7 +11,9 @@ Sec. 4.1.2), so it recomputes them on the submesh around sampled faces
   small parity meshes never exercise);
 * the residual b - S x of the GPU's FGMRES solution (FP32 V-cycle, 1e-8) on
   the sampled rows, recomputed by the oracle: equal to the GPU's own residual
-  on those rows up to rounding (1e-11 of each row's |b| + |S| |x|), and,
+  on those rows to the element tolerance (1e-11 of each row's |b_i| +
+  sum_T max|S_T| ||x_T||_1: the rows are sums of element contributions whose
+  Schur complements agree to 1e-11 of their largest entry), and,
   scaled to the global right-hand side (||r_S|| / ||b|| sqrt(n / |S|)),
   within 1e-6 (the global relative residual is 1e-8; the sampled rows are a
   random subset).  The rows of one face are not compared with the right-hand
