@@ -42,7 +42,13 @@ typedef enum {
     HHO_ERR_UNSUPPORTED = 9    /* element shape, degree or dimension not built */
 } hho_status;
 
-typedef enum { HHO_VCOND = 0, HHO_VPCOND = 1 } hho_cond;
+/* HHO_VCOND, HHO_VPCOND: Scheme 1 (HHO-dp, k' = k) with velocity-only or
+ * velocity-and-pressure condensation (Sec. 4.1.2).  HHO_HPCOND: Scheme 2
+ * (HHO-hp, Sec. 2.3.2: element velocity of degree k+1, hybrid element/face
+ * pressure) with every element unknown condensed; its condensed unknowns are
+ * one block of (d+1) n_F per face (velocity components, then the face
+ * pressure) and no element rows. */
+typedef enum { HHO_VCOND = 0, HHO_VPCOND = 1, HHO_HPCOND = 2 } hho_cond;
 typedef enum { HHO_FP64 = 0, HHO_FP32 = 1 } hho_prec;
 /* Preconditioner of the smoother's GMRES, selected by hho_set_option("smoother", v) before pmg_setup. */
 typedef enum { HHO_SMOOTH_BJACOBI = 0, HHO_SMOOTH_ILU = 1 } hho_smoother;
@@ -88,10 +94,14 @@ typedef struct {
 /* Build the context: copy and check the mesh, compute on the GPU the element
  * and face geometry, hierarchical orthonormal bases (Secs. 2.1, 4.2), the
  * local operators of Scheme 1 with k' = k (Sec. 2.2, Eq. HHOdiscr:residuals,
- * Eq. def:HHOAB), the element static condensation (v-cond Eq. ST.1 or
- * v&p-cond Eq. ST.2) and the assembled level-0 condensed operator in the
- * face-block layout.  k in 0..5 (2D) or 0..3 (3D).  stream: a cudaStream_t
- * (NULL = legacy default stream).  *out receives the new context. */
+ * Eq. def:HHOAB) or of Scheme 2 (cond = HHO_HPCOND, Sec. 2.3.2), the element
+ * static condensation (v-cond Eq. ST.1, v&p-cond Eq. ST.2, or every element
+ * unknown for Scheme 2) and the assembled level-0 condensed operator in the
+ * face-block layout.  k in 0..5 (2D) or 0..3 (3D).  Scheme 2 contexts support
+ * one problem (no hho_set_batch), the block-Jacobi smoother, no learned
+ * smoother, and the dense or multifrontal coarse solve.  stream: a
+ * cudaStream_t (NULL = legacy default stream).  *out receives the new
+ * context. */
 hho_status hho_setup(const hho_mesh* mesh, int k, int cond, void* stream, hho_ctx** out);
 
 /* Number of condensed unknowns at level `level` (0 = fine) after pmg_setup, or
@@ -203,8 +213,9 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
  *                       0 (default): plain smoother.  HHO_ERR_STATE without
  *                       hho_mlp_init.
  *   "spmv_warp"         1 (default): the FP32 operator and block-Jacobi
- *                       kernels of face blocks of 18 and 30 unknowns (3D, k =
- *                       2, 3) use one warp per face; 0: one thread per face
+ *                       kernels of face blocks of 18, 24, 30 and 40 unknowns
+ *                       (3D, k = 2, 3; HHO-hp k = 2, 3) use one warp per
+ *                       face; 0: one thread per face
  *   "solve_graph"       1 (default): hho_solve_batch on a non-default stream
  *                       runs as one CUDA graph captured on first use for each
  *                       (x, rtol, maxit, restart): restart cycles in a WHILE

@@ -420,8 +420,8 @@ hho_status build_level(hho_ctx* ctx, int l, int k_l) {
     LevelMat L;
     L.k = k_l;
     L.nF = dimP(D.d - 1, k_l);
-    L.b = D.d * L.nF;
-    L.nP = (D.cond == HHO_VPCOND) ? 1 : dimP(D.d, k_l);
+    L.b = (D.cond == HHO_HPCOND ? D.d + 1 : D.d) * L.nF;  // HHO-hp: the face pressure is one more component
+    L.nP = (D.cond == HHO_HPCOND) ? 0 : (D.cond == HHO_VPCOND) ? 1 : dimP(D.d, k_l);
     L.nf = D.nf;
     L.ne = D.ne;
     L.n = L.nf * L.b + L.ne * L.nP;
@@ -459,9 +459,11 @@ hho_status build_smoother(hho_ctx* ctx, int l) {
     k_face_inverse<<<(unsigned)((L.nf + 127) / 128), 128, 0, ctx->stream>>>(L.nf, L.b, L.ff, L.dinv, scratch,
                                                                                ctx->d_flag);
     cudaError_t e1 = cudaGetLastError();
-    k_elem_pivot<<<(unsigned)((L.ne + 127) / 128), 128, 0, ctx->stream>>>(L.ne, L.nf, L.b, L.nP, L.N_max, L.pf_col,
-                                                                            L.pf_nsl, ctx->disc.fe, L.fp, L.pf, L.pp,
-                                                                            L.dinv, L.minv, scratch, ctx->d_flag);
+    if (L.nP > 0)  // element pressure pivot blocks (none under HHO-hp)
+        k_elem_pivot<<<(unsigned)((L.ne + 127) / 128), 128, 0, ctx->stream>>>(L.ne, L.nf, L.b, L.nP, L.N_max,
+                                                                                L.pf_col, L.pf_nsl, ctx->disc.fe, L.fp,
+                                                                                L.pf, L.pp, L.dinv, L.minv, scratch,
+                                                                                ctx->d_flag);
     cudaError_t e2 = cudaGetLastError();
     int flag = 0;
     cudaError_t e3 = cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);

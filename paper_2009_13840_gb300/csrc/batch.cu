@@ -607,7 +607,7 @@ static hho_status batch_graph_build(hho_ctx* ctx, BatchWork* B, double rtol, int
         k_copy<<<grid1d(n), 256, 0, main>>>(n, ctx->rhs, B->b);
         k_zero<<<grid1d(n), 256, 0, main>>>(n, x);
         ctx->launches += 2;
-        hho_status e = null_project<double>(ctx, L0.nf * L0.b, L0.nP, B->b);
+        hho_status e = null_project<double>(ctx, L0, B->b);
         if (e == HHO_OK) e = S.upd_dot(B->b, nullptr, 0, 0, 0.0, B->b, 1, 0, 0, HOOK_START, 0, true);
         k_copy<<<grid1d(n), 256, 0, main>>>(n, B->b, B->w);
         k_bg_init<<<1, BG_T, 0, main>>>(P, B->stat, B->d_bnorm, B->d_conv, B->d_convit, B->d_state, maxit, h_outer);
@@ -617,7 +617,7 @@ static hho_status batch_graph_build(hho_ctx* ctx, BatchWork* B, double rtol, int
         if (e != HHO_OK) { fail(e); cudaGraph_t t; cudaStreamEndCapture(main, &t); break; }
         // epilogue: the pressure kernels' projection and the final statistics
         if (ctx->has_null) {
-            e = null_project<double>(ctx, L0.nf * L0.b, L0.nP, x);
+            e = null_project<double>(ctx, L0, x);
             if (e == HHO_OK) e = residual(ctx, 0, x, B->b, B->w);
             if (e == HHO_OK) e = S.upd_dot(B->w, nullptr, 0, 0, 0.0, B->w, 1, 0, 0, HOOK_START, 0, true);
         }
@@ -763,7 +763,7 @@ hho_status batch_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double
     k_copy<<<grid1d(n), 256, 0, ctx->stream>>>(n, ctx->rhs, B->b);
     k_zero<<<grid1d(n), 256, 0, ctx->stream>>>(n, x);
     ctx->launches += 2;
-    HHO_TRY(null_project<double>(ctx, L0.nf * L0.b, L0.nP, B->b));
+    HHO_TRY(null_project<double>(ctx, L0, B->b));
     // ||b_p|| with the START recurrence of every problem
     HHO_TRY(S.upd_dot(B->b, nullptr, 0, 0, 0.0, B->b, 1, 0, 0, HOOK_START, 0, true));
     HHO_TRY(S.read_stat());
@@ -841,7 +841,7 @@ hho_status batch_solve(hho_ctx* ctx, double rtol, int maxit, int restart, double
         r = B->w;
     }
     if (ctx->has_null) {
-        HHO_TRY(null_project<double>(ctx, L0.nf * L0.b, L0.nP, x));
+        HHO_TRY(null_project<double>(ctx, L0, x));
         HHO_TRY(residual(ctx, 0, x, B->b, B->w));
         HHO_TRY(S.upd_dot(B->w, nullptr, 0, 0, 0.0, B->w, 1, 0, 0, HOOK_START, 0, true));
         HHO_TRY(S.read_stat());

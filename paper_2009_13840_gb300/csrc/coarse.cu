@@ -1110,7 +1110,7 @@ hho_status coarse_info(const hho_ctx* ctx, int64_t out[4]) {
     if (!C) return HHO_ERR_STATE;
     out[0] = C->kind;
     out[1] = coarse_solve_bytes(ctx, 1);
-    out[2] = C->kind == 0 ? 1 : C->kind == 1 ? 6 : mf_levels(C->mf) * 2;
+    out[2] = C->kind == 0 ? 1 : C->kind == 1 ? 6 : mf_launches(C->mf, C->Ainv32 || mf_has_f32(C->mf) ? 4 : 8);
     out[3] = C->kind == 2 ? mf_factor_doubles(C->mf) : C->nAinv;
     return HHO_OK;
 }
@@ -1141,12 +1141,12 @@ static hho_status coarse_build(hho_ctx* ctx) {
         k_dense_from_level<<<grid1d(n, 128), 128, 0, ctx->stream>>>(L.nf, L.ne, L.b, L.nP, L.ff_col, L.ff_nsl, L.fp_col,
                                                                      L.pf_col, L.pf_nsl, L.ff, L.fp, L.pf, L.pp, A, n);
         if (ctx->has_null) {
-            std::vector<double> w(L.ne), v(n, 0.0);
+            std::vector<double> v(n, 0.0);
             std::vector<int32_t> rp(n, -1);
-            HHO_CUDA(cudaMemcpy(w.data(), ctx->null_w, L.ne * sizeof(double), cudaMemcpyDeviceToHost));
-            for (int64_t T = 0; T < L.ne; ++T) {
-                v[L.nf * L.b + T * L.nP] = w[T];
-                rp[L.nf * L.b + T * L.nP] = ctx->probs.elem_prob[T];
+            const bool hp = ctx->disc.cond == HHO_HPCOND;  // HHO-hp: one problem, slots are faces
+            for (int64_t E = 0; E < (int64_t)ctx->h_null_w.size(); ++E) {
+                v[null_slot(ctx, L, E)] = ctx->h_null_w[E];
+                rp[null_slot(ctx, L, E)] = hp ? 0 : ctx->probs.elem_prob[E];
             }
             double* nv = nullptr;
             int32_t* rprob = nullptr;
@@ -1182,7 +1182,7 @@ static hho_status coarse_apply_t(hho_ctx* ctx, CoarseSolver* C, const T* Ainv, c
         HHO_TRY(mf_apply<T>(ctx, C->mf, d, c));
         if (C->project) {
             const LevelMat& L = ctx->levels.back();
-            HHO_TRY(null_project<T>(ctx, L.nf * L.b, L.nP, c));
+            HHO_TRY(null_project<T>(ctx, L, c));
         }
     } else {
         k_dd_gather<T><<<grid1d(C->nIt, 256), 256, 0, ctx->stream>>>(C->nIt, C->flat_glob, d, dI);
@@ -1206,7 +1206,7 @@ static hho_status coarse_apply_t(hho_ctx* ctx, CoarseSolver* C, const T* Ainv, c
         // remove them (the dense path's rank-one fix already gives n_p . c = n_p . d / alpha)
         if (C->project) {
             const LevelMat& L = ctx->levels.back();
-            HHO_TRY(null_project<T>(ctx, L.nf * L.b, L.nP, c));
+            HHO_TRY(null_project<T>(ctx, L, c));
         }
     }
     HHO_CUDA(cudaGetLastError());

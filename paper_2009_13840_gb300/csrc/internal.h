@@ -159,9 +159,13 @@ struct hho_ctx {
     double* null_vec0 = nullptr;         // per-problem unit constant-pressure vectors at level 0 (or null)
     bool has_null = false;               // some problem has a pressure kernel
     hho::Problems probs;                 // problem partition (one problem unless a batch is declared)
-    double* null_w = nullptr;            // per element: weight of its first pressure unknown in its
-                                         // problem's unit kernel vector (0 for problems without kernel)
-    int64_t* d_elem_off = nullptr;       // device copy of probs.elem_off
+    double* null_w = nullptr;            // per kernel slot: its weight in its problem's unit kernel vector
+                                         // (0 for problems without kernel).  Slots: every element's first
+                                         // pressure unknown (Scheme 1) or every face's constant face-pressure
+                                         // coefficient (HHO-hp)
+    std::vector<double> h_null_w;        // host copy of null_w
+    int64_t* d_null_off = nullptr;       // device copy of the slot ranges per problem (probs.elem_off, or
+                                         // probs.face_off for HHO-hp)
     hho::BatchWork* batch = nullptr;
     int tile_rows = 2048;                // rows of the condensed vector per block in the segmented kernels
     hho::Learned* learned = nullptr;     // learned smoother network (or null)
@@ -278,11 +282,15 @@ void free_workspace(hho_ctx* ctx);
 void invalidate_graphs(hho_ctx* ctx);
 hho_status residual(hho_ctx* ctx, int l, const double* x, const double* b, double* r);
 hho_status null_build(hho_ctx* ctx);
-// x -= (n_p . x) n_p on the first pressure unknowns of every problem p with a
-// pressure kernel, at a level whose face blocks have b unknowns and element
-// blocks nP (one block per problem)
+// x -= (n_p . x) n_p for every problem p with a pressure kernel, x a vector of
+// level L (one block per problem)
 template <typename T>
-hho_status null_project(hho_ctx* ctx, int64_t nf_rows, int nP, T* x);
+hho_status null_project(hho_ctx* ctx, const LevelMat& L, T* x);
+// index of kernel slot i (element or face, see hho_ctx::null_w) in a vector of level L
+inline int64_t null_slot(const hho_ctx* ctx, const LevelMat& L, int64_t i) {
+    if (ctx->disc.cond == HHO_HPCOND) return i * L.b + (int64_t)ctx->disc.d * L.nF;
+    return L.nf * L.b + i * L.nP;
+}
 // v = r / *den, z = M^{-1} v with the level-0 block-Jacobi preconditioner (FP64)
 hho_status jacobi_apply(hho_ctx* ctx, const double* r, const double* den, double* v, double* z);
 // learned.cu
@@ -324,6 +332,8 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out);
 hho_status mf_make_f32(hho_ctx* ctx, MFSolver* S);
 bool mf_has_f32(const MFSolver* S);
 int mf_levels(const MFSolver* S);
+// kernel launches of one solve with values of value_bytes (8 FP64, 4 FP32)
+int mf_launches(const MFSolver* S, int value_bytes);
 int64_t mf_factor_doubles(const MFSolver* S);
 hho_status coarse_info(const hho_ctx* ctx, int64_t out[4]);
 int64_t mf_solve_bytes(const MFSolver* S, int value_bytes);

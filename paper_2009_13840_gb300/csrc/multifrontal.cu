@@ -523,6 +523,110 @@ __global__ void __launch_bounds__(MF_T) k_mf_bwd(MFView V, const int32_t* __rest
     }
 }
 
+// Entry i of the forward right-hand side f of node v: own d entries on I plus
+// the children's updates (extend-add as a gather, child 0 then child 1).
+template <typename T>
+__device__ __forceinline__ T mf_f_entry(const MFView& V, int v, int i, int nI, const T* __restrict__ d,
+                                        const T* __restrict__ U) {
+    const int32_t* gl = V.glob + V.offP[v];
+    const int32_t* cp = V.cpos + 2 * V.offP[v];
+    const int c0 = V.child[2 * v], c1 = V.child[2 * v + 1];
+    T s = i < nI ? d[gl[i]] : T(0);
+    if (c0 >= 0 && cp[2 * i] >= 0) s += U[V.offU[c0] + cp[2 * i]];
+    if (c1 >= 0 && cp[2 * i + 1] >= 0) s += U[V.offU[c1] + cp[2 * i + 1]];
+    return s;
+}
+
+// Levels with too few (node, row block) pairs to fill the GPU (the large
+// fronts near the roots) also split the columns: CTA (node q, row block rb,
+// column chunk cc) writes the partial product of its chunk to part[(q rb_max +
+// rb) cs + cc][RB]; the finishing kernel adds the cs partials in chunk order
+// (deterministic) and applies the step's epilogue.
+template <typename T, int W>
+__global__ void __launch_bounds__(MF_T) k_mf_fwd_part(MFView V, const int32_t* __restrict__ nodes, int rb_max, int cs,
+                                                     const T* __restrict__ M1all, const T* __restrict__ d,
+                                                     const T* __restrict__ U, T* __restrict__ part) {
+    constexpr int RB = 32 * W;
+    extern __shared__ unsigned char mf_smem[];
+    T* sred = reinterpret_cast<T*>(mf_smem);
+    T* f = sred + (MF_WARPS + 1) * RB;  // the chunk's columns of f
+    const int cc = blockIdx.x % cs, rest = blockIdx.x / cs;
+    const int q = rest / rb_max, rb = rest % rb_max;
+    const int v = nodes[q];
+    const int m = V.m[v], nI = V.nI[v];
+    if (rb * RB >= m) return;
+    const int chunk = (nI + cs - 1) / cs;
+    const int j0 = min(nI, cc * chunk), j1 = min(nI, j0 + chunk);
+    for (int j = j0 + (int)threadIdx.x; j < j1; j += blockDim.x) f[j - j0] = mf_f_entry<T>(V, v, j, nI, d, U);
+    __syncthreads();
+    const int64_t ld = mf_ld(m);
+    block_colmajor_gemv<T, W>(M1all + V.offM1[v] + (int64_t)j0 * ld, ld, m, j1 - j0, f, rb, sred);
+    const T* res = sred + MF_WARPS * RB;
+    T* out = part + (int64_t)blockIdx.x * RB;
+    for (int r = threadIdx.x; r < RB; r += blockDim.x) out[r] = res[r];
+}
+
+template <typename T>
+__global__ void k_mf_fwd_fin(MFView V, const int32_t* __restrict__ nodes, int cnt, int rb_max, int RB, int cs,
+                             const T* __restrict__ part, const T* __restrict__ d, T* __restrict__ Y,
+                             T* __restrict__ U) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)cnt * rb_max * RB) return;
+    const int r = (int)(t % RB);
+    const int64_t rest = t / RB;
+    const int rb = (int)(rest % rb_max), q = (int)(rest / rb_max);
+    const int v = nodes[q];
+    const int m = V.m[v], nI = V.nI[v], i = rb * RB + r;
+    if (i >= m) return;
+    const T* p = part + ((int64_t)q * rb_max + rb) * cs * RB + r;
+    T s = T(0);
+    for (int c = 0; c < cs; ++c) s += p[(int64_t)c * RB];
+    if (i < nI) Y[V.offY[v] + i] = s;
+    else U[V.offU[v] + (i - nI)] = s + mf_f_entry<T>(V, v, i, nI, d, U);
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(MF_T) k_mf_bwd_part(MFView V, const int32_t* __restrict__ nodes, int rb_max, int cs,
+                                                     const T* __restrict__ Xall, const T* __restrict__ c,
+                                                     T* __restrict__ part) {
+    constexpr int RB = 32 * W;
+    extern __shared__ unsigned char mf_smem[];
+    T* sred = reinterpret_cast<T*>(mf_smem);
+    T* xb = sred + (MF_WARPS + 1) * RB;
+    const int cc = blockIdx.x % cs, rest = blockIdx.x / cs;
+    const int q = rest / rb_max, rb = rest % rb_max;
+    const int v = nodes[q];
+    const int m = V.m[v], nI = V.nI[v], nB = m - nI;
+    if (rb * RB >= nI) return;
+    const int chunk = (nB + cs - 1) / cs;
+    const int j0 = min(nB, cc * chunk), j1 = min(nB, j0 + chunk);
+    const int32_t* gl = V.glob + V.offP[v];
+    for (int j = j0 + (int)threadIdx.x; j < j1; j += blockDim.x) xb[j - j0] = c[gl[nI + j]];
+    __syncthreads();
+    const int64_t ld = mf_ld(nI);
+    block_colmajor_gemv<T, W>(Xall + V.offX[v] + (int64_t)j0 * ld, ld, nI, j1 - j0, xb, rb, sred);
+    const T* res = sred + MF_WARPS * RB;
+    T* out = part + (int64_t)blockIdx.x * RB;
+    for (int r = threadIdx.x; r < RB; r += blockDim.x) out[r] = res[r];
+}
+
+template <typename T>
+__global__ void k_mf_bwd_fin(MFView V, const int32_t* __restrict__ nodes, int cnt, int rb_max, int RB, int cs,
+                             const T* __restrict__ part, const T* __restrict__ Y, T* __restrict__ c) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)cnt * rb_max * RB) return;
+    const int r = (int)(t % RB);
+    const int64_t rest = t / RB;
+    const int rb = (int)(rest % rb_max), q = (int)(rest / rb_max);
+    const int v = nodes[q];
+    const int nI = V.nI[v], i = rb * RB + r;
+    if (i >= nI) return;
+    const T* p = part + ((int64_t)q * rb_max + rb) * cs * RB + r;
+    T s = T(0);
+    for (int k = 0; k < cs; ++k) s += p[(int64_t)k * RB];
+    c[V.glob[V.offP[v] + i]] = Y[V.offY[v] + i] - s;
+}
+
 __global__ void k_mf_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
@@ -552,6 +656,10 @@ struct MFSolver {
     float *M1f = nullptr, *Xf = nullptr, *Yf = nullptr, *Uf = nullptr;
     size_t smem_fwd64 = 0, smem_fwd32 = 0, smem_bwd64 = 0, smem_bwd32 = 0;
     int64_t factor_doubles = 0;  // workspace used by the factorisation (freed after it)
+    // partial products of the column-split levels (see k_mf_fwd_part), FP64 and FP32
+    int64_t npart64 = 0, npart32 = 0;
+    double* part64 = nullptr;
+    float* part32 = nullptr;
     MFView view() const {
         MFView V{};
         V.m = m;
@@ -575,11 +683,38 @@ struct MFSolver {
     }
 };
 
+// Launch shape of one solve step on a tree level of cnt nodes with `rows` rows
+// and `cols` columns per node (the largest): rb row blocks of 32 W rows per
+// node; levels with at least 2 CTAs per SM use them as they are (cs = 1,
+// wide), smaller ones split the columns into cs chunks of at least 32 columns
+// for about 4 CTAs per SM (cs > 1), or, when the columns are too few for that,
+// take one row per lane (wide = false).
+struct MFShape {
+    int rb, cs;
+    bool wide;
+};
+static MFShape mf_shape(int64_t cnt, int rows, int cols, int W) {
+    MFShape sh;
+    sh.rb = (rows + 32 * W - 1) / (32 * W);
+    sh.cs = 1;
+    sh.wide = true;
+    const int64_t nsm = sm_count();
+    if (rows == 0 || cnt * sh.rb >= 2 * nsm) return sh;
+    const int64_t want = (4 * nsm + cnt * sh.rb - 1) / (cnt * sh.rb);
+    const int64_t cap = std::max<int64_t>(1, cols / 32);
+    sh.cs = (int)std::min(want, cap);
+    if (sh.cs == 1) {
+        sh.wide = false;
+        sh.rb = (rows + 31) / 32;
+    }
+    return sh;
+}
+
 void mf_free(MFSolver* S) {
     if (!S) return;
     void* ps[] = {S->m, S->nI, S->child, S->pin, S->glob, S->cpos, S->level_nodes, S->leaf_elem_ptr, S->leaf_elem,
                   S->elem_loc, S->offW, S->offM1, S->offX, S->offP, S->offY, S->offU, S->elem_loc_off, S->alpha,
-                  S->M1, S->X, S->Y, S->U, S->M1f, S->Xf, S->Yf, S->Uf};
+                  S->M1, S->X, S->Y, S->U, S->M1f, S->Xf, S->Yf, S->Uf, S->part64, S->part32};
     for (void* p : ps) dfree(p);
     delete S;
 }
@@ -729,8 +864,10 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
             const int32_t T = perm[i];
             if (nd.child[0] < 0)
                 for (int c = 1; c < nPL; ++c) nd.I.push_back((int32_t)(pbase + (int64_t)T * nPL + c));
-            if (p_owner[T] == v) nd.I.push_back((int32_t)(pbase + (int64_t)T * nPL));
-            else if (!in_subtree(p_owner[T], v)) nd.B.push_back((int32_t)(pbase + (int64_t)T * nPL));
+            if (nPL > 0) {  // HHO-hp has no element rows
+                if (p_owner[T] == v) nd.I.push_back((int32_t)(pbase + (int64_t)T * nPL));
+                else if (!in_subtree(p_owner[T], v)) nd.B.push_back((int32_t)(pbase + (int64_t)T * nPL));
+            }
             for (int q = D.h_ef_ptr[T]; q < D.h_ef_ptr[T + 1]; ++q) {
                 const int F = D.h_ef[q];
                 if (!in_subtree(face_owner[F], v)) bfaces.push_back(F);
@@ -749,12 +886,18 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
             return HHO_ERR_MESH;
         }
     // pins: the root's kept pressure of every problem with a pressure kernel
+    // (HHO-hp: the constant face-pressure coefficient of the first face the root
+    // eliminates; the kernel vector is non-zero there)
     for (int q = 0; q < pr.P; ++q) {
         if (!ctx->has_null || !pr.has_null[q]) continue;
         HostNode& rt = nodes[roots[q]];
         int32_t g = -1;
-        for (int64_t i = rt.e0; i < rt.e1 && g < 0; ++i)
-            if (p_owner[perm[i]] == roots[q]) g = (int32_t)(pbase + (int64_t)perm[i] * nPL);
+        if (nPL == 0) {
+            if (!owned_faces[roots[q]].empty()) g = (int32_t)(owned_faces[roots[q]][0] * bL + (int64_t)d * L.nF);
+        } else {
+            for (int64_t i = rt.e0; i < rt.e1 && g < 0; ++i)
+                if (p_owner[perm[i]] == roots[q]) g = (int32_t)(pbase + (int64_t)perm[i] * nPL);
+        }
         if (g < 0) {
             ctx->err = "pmg_setup: multifrontal coarse solver: no kept pressure at a root";
             return HHO_ERR_MESH;
@@ -891,6 +1034,19 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
         S->smem_bwd64 = std::max(S->smem_bwd64, (size_t)((MF_WARPS + 1) * 64 + nBmax) * 8);
         S->smem_bwd32 = std::max(S->smem_bwd32, (size_t)((MF_WARPS + 1) * 128 + nBmax) * 4);
     }
+    // partial-product buffers of the column-split levels (one level at a time)
+    for (int h = 0; h <= hmax; ++h) {
+        const int64_t cnt = S->h_level_ptr[h + 1] - S->h_level_ptr[h];
+        for (int W : {2, 4}) {
+            const MFShape f = mf_shape(cnt, S->level_mmax[h], S->level_nImax[h], W);
+            const MFShape b = mf_shape(cnt, S->level_nImax[h], S->level_nBmax[h], W);
+            int64_t need = 0;
+            if (f.cs > 1) need = std::max<int64_t>(need, cnt * f.rb * f.cs * 32 * W);
+            if (b.cs > 1) need = std::max<int64_t>(need, cnt * b.rb * b.cs * 32 * W);
+            int64_t& slot = (W == 2) ? S->npart64 : S->npart32;
+            slot = std::max(slot, need);
+        }
+    }
     const size_t smem_cap = (size_t)smem_optin();
     if (S->smem_fwd64 > smem_cap || S->smem_bwd64 > smem_cap) {
         delete S;
@@ -916,6 +1072,7 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
     HHO_TRY(mf_upload(ctx, &S->offU, h_offU));
     HHO_TRY(mf_upload(ctx, &S->elem_loc_off, h_elem_loc_off));
     HHO_TRY(dalloc(ctx, &S->alpha, 1));
+    HHO_TRY(dalloc(ctx, &S->part64, (size_t)std::max<int64_t>(S->npart64, 1)));
     S->nM1 = tM1;
     S->nX = tX;
     S->nY = tY;
@@ -1008,6 +1165,10 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
     HHO_TRY(allow_smem(ctx, k_mf_bwd<double, 1>, S->smem_bwd64));
     HHO_TRY(allow_smem(ctx, k_mf_fwd<float, 1>, S->smem_fwd32));
     HHO_TRY(allow_smem(ctx, k_mf_bwd<float, 1>, S->smem_bwd32));
+    HHO_TRY(allow_smem(ctx, k_mf_fwd_part<double, 2>, S->smem_fwd64));
+    HHO_TRY(allow_smem(ctx, k_mf_bwd_part<double, 2>, S->smem_bwd64));
+    HHO_TRY(allow_smem(ctx, k_mf_fwd_part<float, 4>, S->smem_fwd32));
+    HHO_TRY(allow_smem(ctx, k_mf_bwd_part<float, 4>, S->smem_bwd32));
     return HHO_OK;
 }
 
@@ -1017,6 +1178,7 @@ hho_status mf_make_f32(hho_ctx* ctx, MFSolver* S) {
     HHO_TRY(dalloc(ctx, &S->Xf, (size_t)std::max<int64_t>(S->nX, 1)));
     HHO_TRY(dalloc(ctx, &S->Yf, (size_t)std::max<int64_t>(S->nY, 1)));
     HHO_TRY(dalloc(ctx, &S->Uf, (size_t)std::max<int64_t>(S->nU, 1)));
+    HHO_TRY(dalloc(ctx, &S->part32, (size_t)std::max<int64_t>(S->npart32, 1)));
     k_mf_to_f32<<<mf_grid(S->nM1), MF_T, 0, ctx->stream>>>(S->nM1, S->M1, S->M1f);
     k_mf_to_f32<<<mf_grid(S->nX), MF_T, 0, ctx->stream>>>(S->nX, S->X, S->Xf);
     HHO_CUDA(cudaGetLastError());
@@ -1026,6 +1188,17 @@ hho_status mf_make_f32(hho_ctx* ctx, MFSolver* S) {
 bool mf_has_f32(const MFSolver* S) { return S && S->M1f; }
 
 int mf_levels(const MFSolver* S) { return (int)S->level_mmax.size(); }
+
+int mf_launches(const MFSolver* S, int value_bytes) {
+    const int W = value_bytes == 4 ? 4 : 2;
+    int n = 0;
+    for (size_t h = 0; h < S->level_mmax.size(); ++h) {
+        const int64_t cnt = S->h_level_ptr[h + 1] - S->h_level_ptr[h];
+        n += mf_shape(cnt, S->level_mmax[h], S->level_nImax[h], W).cs > 1 ? 2 : 1;
+        if (S->level_nImax[h] > 0) n += mf_shape(cnt, S->level_nImax[h], S->level_nBmax[h], W).cs > 1 ? 2 : 1;
+    }
+    return n;
+}
 
 int64_t mf_factor_doubles(const MFSolver* S) { return S->factor_doubles; }
 
@@ -1041,34 +1214,55 @@ hho_status mf_apply(hho_ctx* ctx, MFSolver* S, const T* d, T* c) {
     T* U = F32 ? (T*)S->Uf : (T*)S->U;
     const MFView V = S->view();
     const int H = (int)S->level_mmax.size();
-    const int64_t fill = 2LL * sm_count();  // CTAs below which a level uses one row per lane
+    T* part = F32 ? (T*)S->part32 : (T*)S->part64;
     const size_t red1 = (size_t)(MF_WARPS + 1) * 32 * sizeof(T), redw = (size_t)(MF_WARPS + 1) * 32 * WW * sizeof(T);
+    int launches = 0;
     for (int h = 0; h < H; ++h) {
         const int l0 = S->h_level_ptr[h], cnt = S->h_level_ptr[h + 1] - l0;
         const int mm = S->level_mmax[h];
-        const int rbw = (mm + 32 * WW - 1) / (32 * WW), rb1 = (mm + 31) / 32;
-        const size_t vec = (size_t)mm * sizeof(T);
-        if ((int64_t)cnt * rbw >= fill)
-            k_mf_fwd<T, WW><<<(unsigned)((int64_t)cnt * rbw), MF_T, redw + vec, ctx->stream>>>(V, S->level_nodes + l0,
-                                                                                           rbw, M1, d, Y, U);
-        else
-            k_mf_fwd<T, 1><<<(unsigned)((int64_t)cnt * rb1), MF_T, red1 + vec, ctx->stream>>>(V, S->level_nodes + l0,
-                                                                                          rb1, M1, d, Y, U);
+        const MFShape sh = mf_shape(cnt, mm, S->level_nImax[h], WW);
+        const unsigned g = (unsigned)((int64_t)cnt * sh.rb * sh.cs);
+        if (sh.cs > 1) {
+            const size_t vec = (size_t)((S->level_nImax[h] + sh.cs - 1) / sh.cs) * sizeof(T);
+            k_mf_fwd_part<T, WW><<<g, MF_T, redw + vec, ctx->stream>>>(V, S->level_nodes + l0, sh.rb, sh.cs, M1, d, U,
+                                                                       part);
+            const int64_t nt = (int64_t)cnt * sh.rb * 32 * WW;
+            k_mf_fwd_fin<T><<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(V, S->level_nodes + l0, cnt, sh.rb,
+                                                                                    32 * WW, sh.cs, part, d, Y, U);
+            launches += 2;
+        } else {
+            const size_t vec = (size_t)mm * sizeof(T);
+            if (sh.wide)
+                k_mf_fwd<T, WW><<<g, MF_T, redw + vec, ctx->stream>>>(V, S->level_nodes + l0, sh.rb, M1, d, Y, U);
+            else
+                k_mf_fwd<T, 1><<<g, MF_T, red1 + vec, ctx->stream>>>(V, S->level_nodes + l0, sh.rb, M1, d, Y, U);
+            launches += 1;
+        }
     }
     for (int h = H - 1; h >= 0; --h) {
         const int l0 = S->h_level_ptr[h], cnt = S->h_level_ptr[h + 1] - l0;
         const int nImax = S->level_nImax[h];
         if (nImax == 0) continue;
-        const int rbw = (nImax + 32 * WW - 1) / (32 * WW), rb1 = (nImax + 31) / 32;
-        const size_t vec = (size_t)S->level_nBmax[h] * sizeof(T);
-        if ((int64_t)cnt * rbw >= fill)
-            k_mf_bwd<T, WW><<<(unsigned)((int64_t)cnt * rbw), MF_T, redw + vec, ctx->stream>>>(V, S->level_nodes + l0,
-                                                                                           rbw, X, Y, c);
-        else
-            k_mf_bwd<T, 1><<<(unsigned)((int64_t)cnt * rb1), MF_T, red1 + vec, ctx->stream>>>(V, S->level_nodes + l0,
-                                                                                          rb1, X, Y, c);
+        const MFShape sh = mf_shape(cnt, nImax, S->level_nBmax[h], WW);
+        const unsigned g = (unsigned)((int64_t)cnt * sh.rb * sh.cs);
+        if (sh.cs > 1) {
+            const size_t vec = (size_t)((S->level_nBmax[h] + sh.cs - 1) / sh.cs) * sizeof(T);
+            k_mf_bwd_part<T, WW><<<g, MF_T, redw + vec, ctx->stream>>>(V, S->level_nodes + l0, sh.rb, sh.cs, X, c,
+                                                                       part);
+            const int64_t nt = (int64_t)cnt * sh.rb * 32 * WW;
+            k_mf_bwd_fin<T><<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(V, S->level_nodes + l0, cnt, sh.rb,
+                                                                                    32 * WW, sh.cs, part, Y, c);
+            launches += 2;
+        } else {
+            const size_t vec = (size_t)S->level_nBmax[h] * sizeof(T);
+            if (sh.wide)
+                k_mf_bwd<T, WW><<<g, MF_T, redw + vec, ctx->stream>>>(V, S->level_nodes + l0, sh.rb, X, Y, c);
+            else
+                k_mf_bwd<T, 1><<<g, MF_T, red1 + vec, ctx->stream>>>(V, S->level_nodes + l0, sh.rb, X, Y, c);
+            launches += 1;
+        }
     }
-    ctx->launches += 2 * H;
+    ctx->launches += launches;
     HHO_CUDA(cudaGetLastError());
     return HHO_OK;
 }

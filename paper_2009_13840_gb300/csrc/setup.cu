@@ -174,19 +174,20 @@ __device__ int elem_start(const ElemSh& E, int d, int K, const double* x, double
 //       qa[n] = (2n+1)/(n+1), qb[n] = n/(n+1)
 //   Jacobi P^{(a,0)}, a = 2p+1      J_{n} = (ja x + jb) J_{n-1} - jc J_{n-2},
 //       (ja, jb, jc)[p][n] = (c1, c2, c3)[n, a] / c0[n, a]   (n >= 2)
+constexpr int REC_N = MAX_K2 + 2;  // degrees 0..MAX_K2+1 (HHO-hp element velocity)
 struct RecTab {
-    double qa[MAX_K2 + 1], qb[MAX_K2 + 1];
-    double ja[MAX_K2 + 1][MAX_K2 + 1], jb[MAX_K2 + 1][MAX_K2 + 1], jc[MAX_K2 + 1][MAX_K2 + 1];
+    double qa[REC_N], qb[REC_N];
+    double ja[REC_N][REC_N], jb[REC_N][REC_N], jc[REC_N][REC_N];
 };
 
 // Fill a RecTab (all threads of the CTA; ends with a barrier).
 __device__ void rec_tab_fill(RecTab& T) {
-    for (int i = threadIdx.x; i <= MAX_K2; i += blockDim.x) {
+    for (int i = threadIdx.x; i < REC_N; i += blockDim.x) {
         T.qa[i] = (2.0 * i + 1.0) / (i + 1.0);
         T.qb[i] = (double)i / (i + 1.0);
     }
-    for (int i = threadIdx.x; i < (MAX_K2 + 1) * (MAX_K2 + 1); i += blockDim.x) {
-        const int p = i / (MAX_K2 + 1), n = i % (MAX_K2 + 1), a = 2 * p + 1;
+    for (int i = threadIdx.x; i < REC_N * REC_N; i += blockDim.x) {
+        const int p = i / REC_N, n = i % REC_N, a = 2 * p + 1;
         double A = 0.0, B = 0.0, C = 0.0;
         if (n >= 2) {
             const double c0 = 2.0 * n * (n + a) * (2 * n + a - 2);
@@ -205,7 +206,7 @@ __device__ void rec_tab_fill(RecTab& T) {
 }
 
 // Values of the element starting functions of elem_start (same functions,
-// same order; no gradients) at x, K <= MAX_K2, with the recursion
+// same order; no gradients) at x, K <= MAX_K2 + 1, with the recursion
 // coefficients of T; returns the count.
 __device__ int elem_start_val(const ElemSh& E, int d, int K, const double* x, double* val, const RecTab& T) {
     if (E.simplex) {
@@ -213,7 +214,7 @@ __device__ int elem_start_val(const ElemSh& E, int d, int K, const double* x, do
         const double r = 2.0 * (E.Minv[0][0] * dx + E.Minv[0][1] * dy) - 1.0;
         const double s = 2.0 * (E.Minv[1][0] * dx + E.Minv[1][1] * dy) - 1.0;
         const double t = 0.5 * (1.0 - s), u = r + 0.5 * (1.0 + s), tt = t * t;
-        double Q[MAX_K2 + 2];
+        double Q[REC_N + 1];
         Q[0] = 1.0;
         if (K >= 1) Q[1] = u;
         for (int p = 1; p < K; ++p) Q[p + 1] = T.qa[p] * u * Q[p] - T.qb[p] * tt * Q[p - 1];
@@ -238,7 +239,7 @@ __device__ int elem_start_val(const ElemSh& E, int d, int K, const double* x, do
         }
         return (K + 1) * (K + 2) / 2;
     }
-    double P[3][MAX_K2 + 2];
+    double P[3][REC_N + 1];
     for (int i = 0; i < d; ++i) {
         const double xi = (x[i] - E.bc[i]) / E.br[i];
         P[i][0] = 1.0;
@@ -626,24 +627,38 @@ __device__ void load_element(ElemSh& E, int d, int t, const int32_t* ef_ptr, con
     __syncthreads();
 }
 
+// Local sizes of one element.  Scheme 1 (v-cond, v&p-cond): element velocity
+// in P^k (n_V = n_E), element pressure P^k, face blocks of d n_F velocity
+// coefficients.  Scheme 2 (HHO-hp, Sec. 2.3.2): element velocity in P^{k+1}
+// (n_V = n_R), element pressure P^k plus a face pressure P^k(F) per face, every
+// element unknown eliminated, kept face blocks of (d+1) n_F (velocity, then
+// the face pressure).
+// Local vector: [U_T (d n_V) | U_F (N d n_F) | P_T (n_E) | P_F (N n_F, HHO-hp)].
 struct LocalDims {
-    int d, k, nR, nE, nF, b, N, ns, nvec, nloc, nel, nk, cond;
+    int d, k, nR, nE, nF, nV, bv, b, N, ns, nvec, npr, nloc, nel, nk, cond;
 };
 
-__device__ LocalDims local_dims(int d, int k, int N, int cond) {
+__host__ __device__ inline LocalDims local_dims(int d, int k, int N, int cond) {
     LocalDims D;
     D.d = d;
     D.k = k;
     D.nR = dimP(d, k + 1);
     D.nE = dimP(d, k);
     D.nF = dimP(d - 1, k);
-    D.b = d * D.nF;
+    const bool hp = (cond == HHO_HPCOND);
+    D.nV = hp ? D.nR : D.nE;
+    D.bv = d * D.nF;
+    D.b = hp ? (d + 1) * D.nF : D.bv;
     D.N = N;
-    D.ns = D.nE + N * D.nF;
-    D.nvec = d * D.nE + N * D.b;
-    D.nloc = D.nvec + D.nE;
+    D.ns = D.nV + N * D.nF;
+    D.nvec = d * D.nV + N * D.bv;
+    D.npr = D.nE + (hp ? N * D.nF : 0);
+    D.nloc = D.nvec + D.npr;
     D.cond = cond;
-    if (cond == HHO_VCOND) {
+    if (hp) {
+        D.nel = d * D.nV + D.nE;
+        D.nk = N * D.b;
+    } else if (cond == HHO_VCOND) {
         D.nel = d * D.nE;
         D.nk = N * D.b + D.nE;
     } else {
@@ -655,27 +670,31 @@ __device__ LocalDims local_dims(int d, int k, int N, int cond) {
 
 // local index (in K) of the i-th eliminated / kept unknown
 __device__ __forceinline__ int elim_idx(const LocalDims& D, int i) {
-    int nUT = D.d * D.nE;
-    return i < nUT ? i : D.nvec + 1 + (i - nUT);
+    const int nUT = D.d * D.nV;
+    if (i < nUT) return i;
+    return D.cond == HHO_HPCOND ? D.nvec + (i - nUT) : D.nvec + 1 + (i - nUT);
 }
 __device__ __forceinline__ int keep_idx(const LocalDims& D, int i) {
-    return D.d * D.nE + i;  // faces, then pressures (all for v-cond, the mean for v&p): contiguous
+    if (D.cond != HHO_HPCOND) return D.d * D.nE + i;  // faces, then pressures (all for v-cond, the mean for v&p)
+    const int f = i / D.b, r = i % D.b;                // HHO-hp: per face its velocity, then its pressure
+    return r < D.bv ? D.d * D.nV + f * D.bv + r : D.nvec + D.nE + f * D.nF + (r - D.bv);
 }
 // vector index of scalar unknown a (0..ns) for component c
 __device__ __forceinline__ int vmap(const LocalDims& D, int c, int a) {
-    if (a < D.nE) return c * D.nE + a;
-    int f = (a - D.nE) / D.nF, j = (a - D.nE) % D.nF;
-    return D.d * D.nE + f * D.b + c * D.nF + j;
+    if (a < D.nV) return c * D.nV + a;
+    int f = (a - D.nV) / D.nF, j = (a - D.nV) % D.nF;
+    return D.d * D.nV + f * D.bv + c * D.nF + j;
 }
 
 struct ScratchLayout {
     int64_t Gt, Kt, Dt, T1, T2, T3, T4, T5, C, Kst, Rhs, P, A, B, Kl, W, R, Mr, tmp, total;
 };
 
-__host__ __device__ inline ScratchLayout scratch_layout(int d, int k, int maxN) {
-    int nR = dimP(d, k + 1), nE = dimP(d, k), nF = dimP(d - 1, k), b = d * nF;
-    int ns = nE + maxN * nF, nvec = d * nE + maxN * b, nloc = nvec + nE;
-    int nel = d * nE + nE, nk = maxN * b + nE;
+__host__ __device__ inline ScratchLayout scratch_layout(int d, int k, int maxN, int cond) {
+    const LocalDims M = local_dims(d, k, maxN, cond);
+    const int nR = M.nR, nE = M.nE, nF = M.nF, nV = M.nV;
+    const int ns = M.ns, nloc = M.nloc;
+    const int nel = d * nV + nE, nk = maxN * M.b + nE;  // bounds over the condensation variants
     ScratchLayout L;
     int64_t o = 0;
     auto take = [&](int64_t n) {
@@ -685,22 +704,22 @@ __host__ __device__ inline ScratchLayout scratch_layout(int d, int k, int maxN) 
     };
     L.Gt = take(nR * nR);
     L.Kt = take(nR * nR);
-    L.Dt = take(3 * nE * nE);
-    L.T1 = take((int64_t)maxN * nR * nE);
+    L.Dt = take(3 * nE * nV);
+    L.T1 = take((int64_t)maxN * nR * nV);
     L.T2 = take((int64_t)maxN * nR * nF);
     L.T3 = take((int64_t)maxN * nR * nF);
-    L.T4 = take((int64_t)maxN * nE * nE);
+    L.T4 = take((int64_t)maxN * nV * nV);
     L.T5 = take((int64_t)maxN * nF * nF);
     L.C = take(nR * nR);
     L.Kst = take(nR * nR);
     L.Rhs = take((int64_t)nR * ns);
     L.P = take((int64_t)nR * ns);
     L.A = take((int64_t)ns * ns);
-    L.B = take((int64_t)nE * nvec);
+    L.B = take((int64_t)M.npr * M.nvec);
     L.Kl = take((int64_t)nloc * nloc);
     L.W = take((int64_t)nel * (nel + nk + nel));
-    L.R = take((int64_t)(nF + nE) * ns);
-    L.Mr = take((int64_t)(nF + nE) * (nF + nE));
+    L.R = take((int64_t)(nF + nV) * ns);
+    L.Mr = take((int64_t)(nF + nV) * (nF + nV));
     L.tmp = take((int64_t)(nR + ns) * (nR + ns) + 4 * nR);
     L.total = o;
     return L;
@@ -726,9 +745,10 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
     __shared__ double s_fval[TQ][10];
     __shared__ double s_w[TQ];
     __shared__ int s_piv;
-    const ScratchLayout SL = scratch_layout(d, k, maxN);
+    const ScratchLayout SL = scratch_layout(d, k, maxN, cond);
     double* ws = scratch + (int64_t)blockIdx.x * SL.total;
     const int nR = dimP(d, k + 1), nE = dimP(d, k), nF = dimP(d - 1, k);
+    const int nV = (cond == HHO_HPCOND) ? nR : nE;  // element velocity coefficients
 
     for (int64_t t = blockIdx.x; t < ne; t += gridDim.x) {
         load_element(E, d, (int)t, ef_ptr, ef, fv_ptr, fv, xyz, fgeo, fbc);
@@ -739,7 +759,7 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
         double* Dt = ws + SL.Dt;
         cta_zero(Gt, nR * nR);
         cta_zero(Kt, nR * nR);
-        cta_zero(Dt, 3 * nE * nE);
+        cta_zero(Dt, 3 * nE * nV);
         // ---- element integrals in the starting basis (degree 2k+2) ----
         const int pop = 2 * k + 2;
         int nq = elem_npts(E, d, pop);
@@ -767,8 +787,8 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
                 Gt[idx] += g;
                 Kt[idx] += kk;
             }
-            for (int idx = threadIdx.x; idx < d * nE * nE; idx += blockDim.x) {
-                int c = idx / (nE * nE), r = idx % (nE * nE), i = r / nE, j = r % nE;
+            for (int idx = threadIdx.x; idx < d * nE * nV; idx += blockDim.x) {
+                int c = idx / (nE * nV), r = idx % (nE * nV), i = r / nV, j = r % nV;
                 double s = 0.0;
                 for (int q = 0; q < nt; ++q) s += s_w[q] * s_val[q][i] * s_grad[q][j * 3 + c];
                 Dt[idx] += s;
@@ -800,10 +820,10 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
         double* T3 = ws + SL.T3;
         double* T4 = ws + SL.T4;
         double* T5 = ws + SL.T5;
-        cta_zero(T1, N * nR * nE);
+        cta_zero(T1, N * nR * nV);
         cta_zero(T2, N * nR * nF);
         cta_zero(T3, N * nR * nF);
-        cta_zero(T4, N * nE * nE);
+        cta_zero(T4, N * nV * nV);
         cta_zero(T5, N * nF * nF);
         for (int f = 0; f < N; ++f) {
             const FaceGeo& g = fgeo[E.fid[f]];
@@ -824,13 +844,13 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
                     }
                 }
                 __syncthreads();
-                double* t1 = T1 + f * nR * nE;
+                double* t1 = T1 + f * nR * nV;
                 double* t2 = T2 + f * nR * nF;
                 double* t3 = T3 + f * nR * nF;
-                double* t4 = T4 + f * nE * nE;
+                double* t4 = T4 + f * nV * nV;
                 double* t5 = T5 + f * nF * nF;
-                for (int idx = threadIdx.x; idx < nR * nE; idx += blockDim.x) {
-                    int i = idx / nE, m = idx % nE;
+                for (int idx = threadIdx.x; idx < nR * nV; idx += blockDim.x) {
+                    int i = idx / nV, m = idx % nV;
                     double s = 0.0;
                     for (int q = 0; q < nt; ++q) s += s_w[q] * s_grad[q][i * 3] * s_val[q][m];
                     t1[idx] += s;
@@ -845,8 +865,8 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
                     t2[idx] += s2;
                     t3[idx] += s3;
                 }
-                for (int idx = threadIdx.x; idx < nE * nE; idx += blockDim.x) {
-                    int i = idx / nE, j = idx % nE;
+                for (int idx = threadIdx.x; idx < nV * nV; idx += blockDim.x) {
+                    int i = idx / nV, j = idx % nV;
                     double s = 0.0;
                     for (int q = 0; q < nt; ++q) s += s_w[q] * s_val[q][i] * s_val[q][j];
                     t4[idx] += s;
@@ -865,30 +885,31 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
         double* Kst = ws + SL.Kst;
         cta_mm(tmp, nR, C, nR, false, Kt, nR, false, nR, nR, nR, 1.0, 0.0);
         cta_mm(Kst, nR, tmp, nR, false, C, nR, true, nR, nR, nR, 1.0, 0.0);
-        // D_c = C_E Dt_c C_E^T (in place via tmp)
+        // D_c = C_E Dt_c C_V^T (in place via tmp; C is lower triangular, so its
+        // leading n x n block maps the first n starting functions)
         for (int c = 0; c < d; ++c) {
-            cta_mm(tmp, nE, C, nR, false, Dt + c * nE * nE, nE, false, nE, nE, nE, 1.0, 0.0);
-            cta_mm(Dt + c * nE * nE, nE, tmp, nE, false, C, nR, true, nE, nE, nE, 1.0, 0.0);
+            cta_mm(tmp, nV, C, nR, false, Dt + c * nE * nV, nV, false, nE, nV, nE, 1.0, 0.0);
+            cta_mm(Dt + c * nE * nV, nV, tmp, nV, false, C, nR, true, nE, nV, nV, 1.0, 0.0);
         }
         for (int f = 0; f < N; ++f) {
             const double* CF = fC + (int64_t)E.fid[f] * nF * nF;
-            double* t1 = T1 + f * nR * nE;
+            double* t1 = T1 + f * nR * nV;
             double* t2 = T2 + f * nR * nF;
             double* t3 = T3 + f * nR * nF;
-            double* t4 = T4 + f * nE * nE;
+            double* t4 = T4 + f * nV * nV;
             double* t5 = T5 + f * nF * nF;
-            // Dn_T = C t1 C_E^T  (nR x nE)
-            cta_mm(tmp, nE, C, nR, false, t1, nE, false, nR, nE, nR, 1.0, 0.0);
-            cta_mm(t1, nE, tmp, nE, false, C, nR, true, nR, nE, nE, 1.0, 0.0);
+            // Dn_T = C t1 C_V^T  (nR x nV)
+            cta_mm(tmp, nV, C, nR, false, t1, nV, false, nR, nV, nR, 1.0, 0.0);
+            cta_mm(t1, nV, tmp, nV, false, C, nR, true, nR, nV, nV, 1.0, 0.0);
             // Dn_F = C t2 C_F^T  (nR x nF)
             cta_mm(tmp, nF, C, nR, false, t2, nF, false, nR, nF, nR, 1.0, 0.0);
             cta_mm(t2, nF, tmp, nF, false, CF, nF, true, nR, nF, nF, 1.0, 0.0);
             // M (element-face mass) = C t3 C_F^T  (nR x nF): M[m][j] = int phi_m psi_j
             cta_mm(tmp, nF, C, nR, false, t3, nF, false, nR, nF, nR, 1.0, 0.0);
             cta_mm(t3, nF, tmp, nF, false, CF, nF, true, nR, nF, nF, 1.0, 0.0);
-            // Mtt = C_E t4 C_E^T
-            cta_mm(tmp, nE, C, nR, false, t4, nE, false, nE, nE, nE, 1.0, 0.0);
-            cta_mm(t4, nE, tmp, nE, false, C, nR, true, nE, nE, nE, 1.0, 0.0);
+            // Mtt = C_V t4 C_V^T
+            cta_mm(tmp, nV, C, nR, false, t4, nV, false, nV, nV, nV, 1.0, 0.0);
+            cta_mm(t4, nV, tmp, nV, false, C, nR, true, nV, nV, nV, 1.0, 0.0);
             // Mff = C_F t5 C_F^T
             cta_mm(tmp, nF, CF, nF, false, t5, nF, false, nF, nF, nF, 1.0, 0.0);
             cta_mm(t5, nF, tmp, nF, false, CF, nF, true, nF, nF, nF, 1.0, 0.0);
@@ -899,11 +920,11 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
         for (int idx = threadIdx.x; idx < nR * ns; idx += blockDim.x) {
             int i = idx / ns, a = idx % ns;
             double v;
-            if (a < nE) {
+            if (a < nV) {
                 v = Kst[i * nR + a];
-                for (int f = 0; f < N; ++f) v -= T1[f * nR * nE + i * nE + a];
+                for (int f = 0; f < N; ++f) v -= T1[f * nR * nV + i * nV + a];
             } else {
-                int f = (a - nE) / nF, j = (a - nE) % nF;
+                int f = (a - nV) / nF, j = (a - nV) % nF;
                 v = T2[f * nR * nF + i * nF + j];
             }
             Rhs[idx] = v;
@@ -933,18 +954,19 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
         cta_mm(A, ns, P, ns, true, tmp, ns, false, ns, ns, nR, 1.0, 0.0);
         double* R = ws + SL.R;
         double* Mr = ws + SL.Mr;
-        const int nr = nF + nE;
+        const int nr = nF + nV;
         for (int f = 0; f < N; ++f) {
             double* DnF = T2 + f * nR * nF;
             double* M = T3 + f * nR * nF;
-            double* Mtt = T4 + f * nE * nE;
+            double* Mtt = T4 + f * nV * nV;
             double* Mff = T5 + f * nF * nF;
-            // R = [E_F - M^T P ; E_T - P[:nE]]  ((nF+nE) x ns)
+            // R = [E_F - M^T P ; E_T - P[:nV]]  ((nF+nV) x ns): the face residual's
+            // element part is pi_T^{k'} (v_T - p v), the first nV coefficients
             for (int idx = threadIdx.x; idx < nr * ns; idx += blockDim.x) {
                 int i = idx / ns, a = idx % ns;
                 double v;
                 if (i < nF) {
-                    v = (a == nE + f * nF + i) ? 1.0 : 0.0;
+                    v = (a == nV + f * nF + i) ? 1.0 : 0.0;
                     for (int m = 0; m < nR; ++m) v -= M[m * nF + i] * P[m * ns + a];
                 } else {
                     int ii = i - nF;
@@ -952,7 +974,7 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
                 }
                 R[idx] = v;
             }
-            // Mr = [[Mff, -Mft], [-Mft^T, Mtt]] / h_F with Mft[j][i] = M[i][j], i < nE
+            // Mr = [[Mff, -Mft], [-Mft^T, Mtt]] / h_F with Mft[j][i] = M[i][j], i < nV
             double ih = 1.0 / E.hF[f];
             for (int idx = threadIdx.x; idx < nr * nr; idx += blockDim.x) {
                 int i = idx / nr, j = idx % nr;
@@ -960,7 +982,7 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
                 if (i < nF && j < nF) v = Mff[i * nF + j];
                 else if (i < nF) v = -M[(j - nF) * nF + i];
                 else if (j < nF) v = -M[(i - nF) * nF + j];
-                else v = Mtt[(i - nF) * nE + (j - nF)];
+                else v = Mtt[(i - nF) * nV + (j - nF)];
                 Mr[idx] = v * ih;
             }
             __syncthreads();
@@ -973,7 +995,7 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
                 for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x) {
                     int a = idx / ns, bb = idx % ns;
                     double v = 0.0;
-                    int ja = a - nE - f * nF, jb = bb - nE - f * nF;
+                    int ja = a - nV - f * nF, jb = bb - nV - f * nF;
                     bool fa = (ja >= 0 && ja < nF), fb = (jb >= 0 && jb < nF);
                     if (fa) v -= tmp[ja * ns + bb];
                     if (fb) v -= tmp[jb * ns + a];
@@ -992,17 +1014,30 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
             Kl[vmap(D, c, a) * nloc + vmap(D, c, bb)] = A[r];
         }
         __syncthreads();
-        // B rows (pressure i < nE)
-        for (int idx = threadIdx.x; idx < nE * nvec; idx += blockDim.x) {
+        // B rows: element pressure (i < nE), then the face pressures of HHO-hp
+        for (int idx = threadIdx.x; idx < D.npr * nvec; idx += blockDim.x) {
             int i = idx / nvec, col = idx % nvec;
             double v = 0.0;
-            if (col < d * nE) {
-                int c = col / nE, j = col % nE;
-                v = -Dt[c * nE * nE + i * nE + j];
-                for (int f = 0; f < N; ++f) v += E.nTF[f][c] * T4[f * nE * nE + i * nE + j];
+            if (i < nE) {
+                if (col < d * nV) {
+                    int c = col / nV, j = col % nV;
+                    v = -Dt[c * nE * nV + i * nV + j];
+                    if (cond != HHO_HPCOND)
+                        for (int f = 0; f < N; ++f) v += E.nTF[f][c] * T4[f * nV * nV + i * nV + j];
+                } else if (cond != HHO_HPCOND) {
+                    int r = col - d * nV, f = r / D.bv, cc = (r % D.bv) / nF, j = r % nF;
+                    if (E.bcf[f] != 1) v = -E.nTF[f][cc] * T3[f * nR * nF + i * nF + j];
+                }
             } else {
-                int r = col - d * nE, f = r / D.b, cc = (r % D.b) / nF, j = r % nF;
-                if (E.bcf[f] != 1) v = -E.nTF[f][cc] * T3[f * nR * nF + i * nF + j];
+                // int_F (v_T - v_F) . n q_F, v_F dropped on Dirichlet faces (Sec. 2.3.2)
+                int f = (i - nE) / nF, ii = (i - nE) % nF;
+                if (col < d * nV) {
+                    int c = col / nV, j = col % nV;
+                    v = E.nTF[f][c] * T3[f * nR * nF + j * nF + ii];
+                } else {
+                    int r = col - d * nV, g = r / D.bv, cc = (r % D.bv) / nF, j = r % nF;
+                    if (g == f && E.bcf[f] != 1) v = -E.nTF[f][cc] * T5[f * nF * nF + ii * nF + j];
+                }
             }
             Kl[(nvec + i) * nloc + col] = v;
             Kl[col * nloc + (nvec + i)] = v;
@@ -1066,10 +1101,12 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
                                              const double* __restrict__ Pm, double* __restrict__ gT,
                                              double* __restrict__ yT, double* __restrict__ scratch, int64_t scratch_per) {
     __shared__ ElemSh E;
-    __shared__ double s_acc[3 * 36 + 3 * 10 + 36];
+    __shared__ double s_acc[3 * 36 + 3 * 10 + 36 + 10];
     __shared__ RecTab tab;
     rec_tab_fill(tab);
     const int nR = dimP(d, k + 1), nE = dimP(d, k), nF = dimP(d - 1, k);
+    const int nV = (cond == HHO_HPCOND) ? nR : nE;  // element velocity coefficients
+    const int kv = (cond == HHO_HPCOND) ? k + 1 : k;
     const int pd = 2 * k + 2;
     double* ws = scratch + (int64_t)blockIdx.x * scratch_per;
     for (int64_t t = blockIdx.x; t < ne; t += gridDim.x) {
@@ -1083,41 +1120,41 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
         const double* C = eC + t * nR * nR;
         const double* P = Pm + off_P[t];
         __syncthreads();
-        // body force: int f_c phi_j, j < nE (starting basis, then transform)
+        // body force: int f_c phi_j, j < nV (starting basis, then transform)
         {
-            __shared__ double red[TPB / 32][3 * 21];
+            __shared__ double red[TPB / 32][3 * 36];
             int nq = elem_npts(E, d, pd);
             int64_t o = enode_off[t];
-            double part[3 * 21];
-            for (int i = 0; i < d * nE; ++i) part[i] = 0.0;
+            double part[3 * 36];
+            for (int i = 0; i < d * nV; ++i) part[i] = 0.0;
             for (int q = threadIdx.x; q < nq; q += blockDim.x) {
                 double x[3] = {0, 0, 0}, w, val[36];
                 elem_point(E, d, gl, pd, q, x, &w);
-                elem_start_val(E, d, k, x, val, tab);
+                elem_start_val(E, d, kv, x, val, tab);
                 for (int c = 0; c < d; ++c) {
                     double wf = w * fdat[(o + q) * d + c];
-                    for (int a = 0; a < nE; ++a) part[c * nE + a] += wf * val[a];
+                    for (int a = 0; a < nV; ++a) part[c * nV + a] += wf * val[a];
                 }
             }
             // warp sums by shuffles (every lane of the CTA is here), then the
             // TPB / 32 warp sums in warp order: no serial chain on one thread
-            for (int i = 0; i < d * nE; ++i) {
+            for (int i = 0; i < d * nV; ++i) {
                 double v = part[i];
                 for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
                 if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i] = v;
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < d * nE; i += blockDim.x) {
+            for (int i = threadIdx.x; i < d * nV; i += blockDim.x) {
                 double tot = 0.0;
                 for (int w = 0; w < TPB / 32; ++w) tot += red[w][i];
                 s_acc[i] = tot;
             }
             __syncthreads();
-            for (int idx = threadIdx.x; idx < d * nE; idx += blockDim.x) {
-                int c = idx / nE, j = idx % nE;
+            for (int idx = threadIdx.x; idx < d * nV; idx += blockDim.x) {
+                int c = idx / nV, j = idx % nV;
                 double v = 0.0;
-                for (int a = 0; a <= j; ++a) v += C[j * nR + a] * s_acc[c * nE + a];
-                rhs[c * nE + j] += v;
+                for (int a = 0; a <= j; ++a) v += C[j * nR + a] * s_acc[c * nV + a];
+                rhs[c * nV + j] += v;
             }
             __syncthreads();
         }
@@ -1131,9 +1168,10 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
             int nqf = face_npts(d, E.nvf[f], pd);
             int64_t o = fnode_off[F];
             const double* gv = (bc == 1) ? gD : gN;
-            // accumulators: for each c: sum w g_c dn phi~_m (nR), sum w g_c psi~_j (nF); sum w (g.n) phi~_i (nR)
+            // accumulators: for each c: sum w g_c dn phi~_m (nR), sum w g_c psi~_j (nF); sum w (g.n) phi~_i (nR);
+            // sum w (g.n) psi~_j (nF)
             if (threadIdx.x == 0) {
-                for (int i = 0; i < 3 * 36 + 3 * 10 + 36; ++i) s_acc[i] = 0.0;
+                for (int i = 0; i < 3 * 36 + 3 * 10 + 36 + 10; ++i) s_acc[i] = 0.0;
                 for (int q = 0; q < nqf; ++q) {
                     double x[3] = {0, 0, 0}, w, val[36], grad[36 * 3], fval[10];
                     face_point(d, E.V[f], E.nvf[f], E.xF[f], gl, pd, q, x, &w);
@@ -1147,8 +1185,10 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
                         for (int c = 0; c < d; ++c) s_acc[c * 36 + m] += w * gv[(o + q) * d + c] * dn;
                         s_acc[3 * 36 + 3 * 10 + m] += w * gn * val[m];
                     }
-                    for (int j = 0; j < nF; ++j)
+                    for (int j = 0; j < nF; ++j) {
                         for (int c = 0; c < d; ++c) s_acc[3 * 36 + c * 10 + j] += w * gv[(o + q) * d + c] * fval[j];
+                        s_acc[3 * 36 + 3 * 10 + 36 + j] += w * gn * fval[j];
+                    }
                 }
             }
             __syncthreads();
@@ -1162,7 +1202,7 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
                         for (int a = 0; a <= j; ++a) v += CF[j * nF + a] * s_acc[3 * 36 + c * 10 + a];
                         gpsi[j] = v;
                     }
-                    int base = D.d * nE + f * D.b + c * nF;
+                    int base = D.d * nV + f * D.bv + c * nF;
                     if (bc == 1) {
                         // tdn_m = int g_c dn phi_m (orthonormal)
                         double tdn[36];
@@ -1181,11 +1221,17 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
                         for (int j = 0; j < nF; ++j) rhs[base + j] += gpsi[j];
                     }
                 }
-                if (bc == 1) {
+                if (bc == 1 && cond != HHO_HPCOND) {  // - int g_D . n q_T  (Eq. HHOdiscrCNT)
                     for (int i = 0; i < nE; ++i) {
                         double v = 0.0;
                         for (int a = 0; a <= i; ++a) v += C[i * nR + a] * s_acc[3 * 36 + 3 * 10 + a];
                         rhs[D.nvec + i] += v;
+                    }
+                } else if (bc == 1) {  // HHO-hp: - int g_D . n q_F on the Dirichlet face
+                    for (int j = 0; j < nF; ++j) {
+                        double v = 0.0;
+                        for (int a = 0; a <= j; ++a) v += CF[j * nF + a] * s_acc[3 * 36 + 3 * 10 + 36 + a];
+                        rhs[D.nvec + nE + f * nF + j] += v;
                     }
                 }
             }
@@ -1276,7 +1322,7 @@ __global__ void k_recover(int d, int k, int cond, int64_t ne, int64_t nf, int b,
         int f0 = ef_ptr[t], N = ef_ptr[t + 1] - f0;
         LocalDims D = local_dims(d, k, N, cond);
         double* o = out + off_loc[t];
-        // kept unknowns
+        // kept unknowns (face blocks, then the element's kept pressures; HHO-hp keeps face blocks only)
         for (int j = threadIdx.x; j < D.nk; j += blockDim.x) {
             double v;
             if (j < N * b) v = x[(int64_t)ef[f0 + j / b] * b + j % b];
@@ -1307,6 +1353,7 @@ __global__ void k_errors(int d, int k, int cond, int64_t ne, const double* __res
     __shared__ double s_coef[3][36];
     __shared__ double red[6][TPB];
     const int nR = dimP(d, k + 1), nE = dimP(d, k);
+    const int nV = (cond == HHO_HPCOND) ? nR : nE;  // element velocity coefficients
     const int pd = 2 * k + 2;
     for (int64_t t = blockIdx.x; t < ne; t += gridDim.x) {
         load_element(E, d, (int)t, ef_ptr, ef, fv_ptr, fv, xyz, fgeo, fbc);
@@ -1328,9 +1375,9 @@ __global__ void k_errors(int d, int k, int cond, int64_t ne, const double* __res
             int c = idx / nR, a = idx % nR;
             double s = 0.0, su = 0.0;
             for (int m = a; m < nR; ++m) s += s_coef[c][m] * C[m * nR + a];
-            for (int m = a; m < nE; ++m) su += U[c * nE + m] * C[m * nR + a];
+            for (int m = a; m < nV; ++m) su += U[c * nV + m] * C[m * nR + a];
             s_st[c][a] = s;
-            s_ut[c][a] = (a < nE) ? su : 0.0;
+            s_ut[c][a] = (a < nV) ? su : 0.0;
         }
         for (int a = threadIdx.x; a < nR; a += blockDim.x) {
             double s = 0.0;
@@ -1442,8 +1489,8 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
     D.nR = dimP(d, k + 1);
     D.nE = dimP(d, k);
     D.nF = dimP(d - 1, k);
-    D.b = d * D.nF;
-    D.nP = (cond == HHO_VPCOND) ? 1 : D.nE;
+    D.b = local_dims(d, k, 0, cond).b;
+    D.nP = (cond == HHO_HPCOND) ? 0 : (cond == HHO_VPCOND) ? 1 : D.nE;
     // host topology (int32)
     D.h_ef_ptr.resize(D.ne + 1);
     D.h_ef.resize(m->elem_face_ptr[D.ne]);
@@ -1473,10 +1520,8 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
     std::vector<int64_t> oS(D.ne), oX(D.ne), oK(D.ne), oP(D.ne), oL(D.ne), oG(D.ne), oY(D.ne);
     int64_t tS = 0, tX = 0, tK = 0, tP = 0, tL = 0, tG = 0, tY = 0;
     for (int64_t t = 0; t < D.ne; ++t) {
-        int N = D.h_ef_ptr[t + 1] - D.h_ef_ptr[t];
-        int ns = D.nE + N * D.nF, nvec = d * D.nE + N * D.b, nloc = nvec + D.nE;
-        int nel = (cond == HHO_VCOND) ? d * D.nE : d * D.nE + D.nE - 1;
-        int nk = (cond == HHO_VCOND) ? N * D.b + D.nE : N * D.b + 1;
+        const LocalDims L = local_dims(d, k, D.h_ef_ptr[t + 1] - D.h_ef_ptr[t], cond);
+        const int ns = L.ns, nloc = L.nloc, nel = L.nel, nk = L.nk;
         oS[t] = tS;
         tS += (int64_t)nk * nk;
         oX[t] = tX;
@@ -1574,7 +1619,7 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
                                                                       D.fC);
     HHO_CUDA(cudaGetLastError());
     int grid = element_grid(D.ne);
-    ScratchLayout SL = scratch_layout(d, k, D.maxN);
+    ScratchLayout SL = scratch_layout(d, k, D.maxN, cond);
     double* scratch = nullptr;
     HHO_TRY(dalloc(ctx, &scratch, (size_t)grid * SL.total));
     HHO_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
@@ -1599,11 +1644,7 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
 hho_status build_rhs(hho_ctx* ctx, const double* f, const double* gD, const double* gN) {
     Disc& D = ctx->disc;
     int grid = element_grid(D.ne);
-    int64_t per = 0;
-    {
-        int nloc = D.d * D.nE + D.maxN * D.b + D.nE;
-        per = (nloc + 3) & ~3;
-    }
+    const int64_t per = (local_dims(D.d, D.k, D.maxN, D.cond).nloc + 3) & ~3;
     double* scratch = nullptr;
     HHO_TRY(dalloc(ctx, &scratch, (size_t)grid * per));
     k_rhs<<<grid, TPB, 0, ctx->stream>>>(D.d, D.k, D.cond, D.ne, D.xyz, D.ef_ptr, D.ef, D.fv_ptr, D.fv, D.fbc, D.fgeo,
@@ -1624,8 +1665,7 @@ hho_status build_rhs(hho_ctx* ctx, const double* f, const double* gD, const doub
 hho_status build_rhs_scratch(hho_ctx* ctx, const double* f, const double* gD, const double* gN, double* scratch,
                              int64_t capacity) {
     Disc& D = ctx->disc;
-    const int nloc = D.d * D.nE + D.maxN * D.b + D.nE;
-    const int64_t per = (nloc + 3) & ~3;
+    const int64_t per = (local_dims(D.d, D.k, D.maxN, D.cond).nloc + 3) & ~3;
     const int64_t fit = capacity / per;
     if (fit < 1) {
         ctx->err = "hho_assemble_noalloc: one element's local system needs more working memory than the fixed array holds";

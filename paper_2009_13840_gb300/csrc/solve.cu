@@ -686,13 +686,15 @@ __global__ void __launch_bounds__(RT, 4) k_spmv_v(LV<float> L, Items it, const f
                 block_mv<RF, B>(L.ff + ((int64_t)s * B * nf + F) * B + r0, nf * B, xv, acc);
                 G = Gn;
             }
+            if constexpr (NP > 0) {  // HHO-hp levels have no element rows (NP = 0)
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const int T = L.fp_col[p * nf + F];
-                if (T < 0) continue;
-                float xp[NP];
-                load_run_plain<NP>(x + nf * B + (int64_t)T * NP, xp);
-                block_mv<RF, NP>(L.fp + ((int64_t)p * NP * nf + F) * B + r0, nf * B, xp, acc);
+                for (int p = 0; p < 2; ++p) {
+                    const int T = L.fp_col[p * nf + F];
+                    if (T < 0) continue;
+                    float xp[NP];
+                    load_run_plain<NP>(x + nf * B + (int64_t)T * NP, xp);
+                    block_mv<RF, NP>(L.fp + ((int64_t)p * NP * nf + F) * B + r0, nf * B, xp, acc);
+                }
             }
 #pragma unroll
             for (int i = 0; i < RF; ++i) {
@@ -710,7 +712,7 @@ __global__ void __launch_bounds__(RT, 4) k_spmv_v(LV<float> L, Items it, const f
                     accumulate_dots(dacc, V, ld, o, nv, self, v);
                 }
             }
-        } else {
+        } else if constexpr (NP > 0) {
             const int64_t E = (w - nfi) * 32 + lane;  // one thread per element block (egroups = 1)
             if (E >= ne) continue;
             float acc[NP];
@@ -757,17 +759,42 @@ __global__ void __launch_bounds__(RT, 4) k_spmv_v(LV<float> L, Items it, const f
 // rr * VW ..); each lane accumulates its rows over the columns c = g (mod GC)
 // and the GC partial sums of a row are added across the lane groups in group
 // order (deterministic).
-constexpr int wv_vw(int B) { return (B % 2 == 0 && B / 2 <= 16) ? 2 : 1; }
+// The 3D HHO-hp blocks (24 and 40 unknowns, multiples of 4) take 16-byte loads
+// of 4 rows: RL = 6 or 10 lanes per column, 5 or 3 columns per load.
+constexpr int wv_vw(int B) { return (B >= 24 && B % 4 == 0) ? 4 : (B % 2 == 0 && B / 2 <= 16) ? 2 : 1; }
 constexpr int wv_rl(int B) { return B / wv_vw(B); }
 constexpr int wv_gc(int B) { return 32 / wv_rl(B); }
 constexpr int wv_nk(int B) { return (B + wv_gc(B) - 1) / wv_gc(B); }
+constexpr int wv_xr(int B) { return (B + 31) / 32; }  // registers per lane holding a column block of x
 static_assert(wv_rl(30) == 15 && wv_gc(30) == 2 && wv_rl(18) == 9 && wv_gc(18) == 3 && wv_rl(9) == 9 &&
-                  wv_gc(9) == 3 && wv_nk(30) * wv_gc(30) == 30 && wv_nk(18) * wv_gc(18) == 18,
+                  wv_gc(9) == 3 && wv_nk(30) * wv_gc(30) == 30 && wv_nk(18) * wv_gc(18) == 18 &&
+                  wv_rl(40) == 10 && wv_gc(40) == 3 && wv_nk(40) == 14 && wv_rl(24) == 6 && wv_gc(24) == 5 &&
+                  wv_xr(40) == 2 && wv_xr(30) == 1,
               "warp lane layout");
+
+// entry c (0 <= c < 32 XR, lane-dependent) of a column block held as XR
+// registers per lane (register i of lane l holds entry 32 i + l); every lane
+// takes part in every shuffle
+template <int XR>
+__device__ __forceinline__ float wv_bcast(const float (&xr)[XR], int c) {
+    float v = __shfl_sync(0xffffffffu, xr[0], c & 31);
+#pragma unroll
+    for (int i = 1; i < XR; ++i) {
+        const float t = __shfl_sync(0xffffffffu, xr[i], c & 31);
+        if ((c >> 5) == i) v = t;
+    }
+    return v;
+}
 
 template <int VW>
 __device__ __forceinline__ void load_vw(const float* __restrict__ p, float (&v)[VW]) {
-    if constexpr (VW == 2) {
+    if constexpr (VW == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    } else if constexpr (VW == 2) {
         const float2 t = __ldg(reinterpret_cast<const float2*>(p));
         v[0] = t.x;
         v[1] = t.y;
@@ -802,7 +829,7 @@ __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t
                                              double* __restrict__ partial, unsigned* __restrict__ counter,
                                              double* __restrict__ out, int hook, double* sc, GS gsl, int j,
                                              Restr rs) {
-    constexpr int VW = wv_vw(B), RL = wv_rl(B), GC = wv_gc(B), NK = wv_nk(B);
+    constexpr int VW = wv_vw(B), RL = wv_rl(B), GC = wv_gc(B), NK = wv_nk(B), XR = wv_xr(B);
     constexpr int SU = (NK * VW <= 12) ? 2 : 1;  // slots in flight per warp
     const int lane = threadIdx.x & 31;
     const int g = lane / RL, rr = lane - g * RL;
@@ -823,14 +850,15 @@ __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t
             // SU slots per iteration: their column-index -> x chains and their
             // value loads are all issued before the first multiply
             for (int s0 = 0; s0 < ns; s0 += SU) {
-                float xl[SU];
+                float xl[SU][XR];
                 float av[SU][NK][VW];
 #pragma unroll
                 for (int u = 0; u < SU; ++u) {
                     const int s = s0 + u;
                     const bool has = s < ns;
                     const int64_t G = has ? L.ff_col[(int64_t)s * nf + F] : 0;
-                    xl[u] = (has && lane < B) ? x[G * B + lane] : 0.f;
+#pragma unroll
+                    for (int i = 0; i < XR; ++i) xl[u][i] = (has && 32 * i + lane < B) ? x[G * B + 32 * i + lane] : 0.f;
                     const float* a = L.ff + ((int64_t)s * B * nf + F) * B + rr * VW;
 #pragma unroll
                     for (int k = 0; k < NK; ++k) {
@@ -845,28 +873,30 @@ __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t
                 for (int u = 0; u < SU; ++u)
 #pragma unroll
                     for (int k = 0; k < NK; ++k) {
-                        const float xc = __shfl_sync(0xffffffffu, xl[u], (k * GC + g) & 31);
+                        const float xc = wv_bcast<XR>(xl[u], k * GC + g);
 #pragma unroll
                         for (int q = 0; q < VW; ++q) acc[q] += av[u][k][q] * xc;
                     }
             }
+            if constexpr (NP > 0) {  // HHO-hp levels have no element rows (NP = 0)
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const int T = L.fp_col[p * nf + F];
-                if (T < 0) continue;
-                const float* xp = x + nf * B + (int64_t)T * NP;
-                const float* a = L.fp + ((int64_t)p * NP * nf + F) * B + rr * VW;
-                for (int c = g; c < NP; c += GC) {
-                    if (!lane_ok) break;
-                    float av[VW];
-                    load_vw<VW>(a + (int64_t)c * nf * B, av);
-                    const float xc = xp[c];
+                for (int p = 0; p < 2; ++p) {
+                    const int T = L.fp_col[p * nf + F];
+                    if (T < 0) continue;
+                    const float* xp = x + nf * B + (int64_t)T * NP;
+                    const float* a = L.fp + ((int64_t)p * NP * nf + F) * B + rr * VW;
+                    for (int c = g; c < NP; c += GC) {
+                        if (!lane_ok) break;
+                        float av[VW];
+                        load_vw<VW>(a + (int64_t)c * nf * B, av);
+                        const float xc = xp[c];
 #pragma unroll
-                    for (int q = 0; q < VW; ++q) acc[q] += av[q] * xc;
+                        for (int q = 0; q < VW; ++q) acc[q] += av[q] * xc;
+                    }
                 }
             }
             wv_group_sum<B, VW>(acc, rr);
-            if (g == 0) {
+            if (lane_ok && g == 0) {
 #pragma unroll
                 for (int q = 0; q < VW; ++q) {
                     const int r = rr * VW + q;
@@ -884,7 +914,7 @@ __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t
                     }
                 }
             }
-        } else {
+        } else if constexpr (NP > 0) {
             const int64_t E = (w - nfw) * 32 + lane;
             if (E >= ne) continue;
             float acc[NP];
@@ -936,7 +966,7 @@ __global__ void __launch_bounds__(RT) k_jacobi_w(LV<float> L, int64_t etiles, co
                                                const double* __restrict__ den, float* __restrict__ v,
                                                float* __restrict__ z, const float* __restrict__ Vp, int64_t ld,
                                                int npend, const double* __restrict__ pc) {
-    constexpr int VW = wv_vw(B), RL = wv_rl(B), GC = wv_gc(B), NK = wv_nk(B);
+    constexpr int VW = wv_vw(B), RL = wv_rl(B), GC = wv_gc(B), NK = wv_nk(B), XR = wv_xr(B);
     const float inv = block_inverse<float>(den);
     const float* s_pc = stage_pending<float>(pc, npend);
     const int lane = threadIdx.x & 31;
@@ -948,7 +978,10 @@ __global__ void __launch_bounds__(RT) k_jacobi_w(LV<float> L, int64_t etiles, co
     for (int64_t wi = warp; wi < nf + etiles; wi += nwarps) {
         if (wi < nf) {
             const int64_t F = wi;
-            const float ul = lane < B ? pending(w, Vp, ld, npend, s_pc, F * B + lane) : 0.f;
+            float ul[XR];
+#pragma unroll
+            for (int i = 0; i < XR; ++i)
+                ul[i] = 32 * i + lane < B ? pending(w, Vp, ld, npend, s_pc, F * B + 32 * i + lane) : 0.f;
             const float* a = L.dinv + F * B + rr * VW;
             float av[NK][VW];
 #pragma unroll
@@ -964,16 +997,18 @@ __global__ void __launch_bounds__(RT) k_jacobi_w(LV<float> L, int64_t etiles, co
             for (int q = 0; q < VW; ++q) acc[q] = 0.f;
 #pragma unroll
             for (int k = 0; k < NK; ++k) {
-                const float uc = __shfl_sync(0xffffffffu, ul, (k * GC + g) & 31);
+                const float uc = wv_bcast<XR>(ul, k * GC + g);
 #pragma unroll
                 for (int q = 0; q < VW; ++q) acc[q] += av[k][q] * uc;
             }
             wv_group_sum<B, VW>(acc, rr);
-            if (g == 0)
+            if (lane_ok && g == 0)
 #pragma unroll
                 for (int q = 0; q < VW; ++q) z[F * B + rr * VW + q] = acc[q] * inv;
-            if (lane < B) v[F * B + lane] = ul * inv;
-        } else {
+#pragma unroll
+            for (int i = 0; i < XR; ++i)
+                if (32 * i + lane < B) v[F * B + 32 * i + lane] = ul[i] * inv;
+        } else if constexpr (NP > 0) {
             const int64_t E = (wi - nf) * 32 + lane;
             if (E >= ne) continue;
             const int64_t ob = nf * B + E * NP;
@@ -1022,7 +1057,7 @@ __global__ void __launch_bounds__(RT) k_jacobi_v(LV<float> L, Items it, const fl
                 z[F * B + r] = acc[r] * inv;
                 v[F * B + r] = u[r] * inv;
             }
-        } else {
+        } else if constexpr (NP > 0) {
             const int64_t E = (wi - it.ftiles) * 32 + lane;
             if (E >= ne) continue;
             const int64_t ob = nf * B + E * NP;
@@ -1178,14 +1213,16 @@ __global__ void k_zero(int64_t n, T* __restrict__ dst) {
 }
 
 // x -= (n_p . x) n_p for every problem p (one block each): n_p is non-zero
-// only on the first pressure unknown of p's elements, with weight w[T]
-// (0 throughout for a problem without pressure kernel).  xp points at the
-// element part of the vector (element blocks of nP).  Fixed-order tree.
+// only on one unknown per kernel slot E (the first pressure unknown of an
+// element, or the constant face-pressure coefficient of a face for HHO-hp),
+// xp[E * stride], with weight w[E] (0 throughout for a problem without
+// pressure kernel).  Fixed-order tree.
 template <typename T>
-__global__ void __launch_bounds__(512) k_null_proj(const int64_t* __restrict__ elem_off,
-                                                   const double* __restrict__ w, T* __restrict__ xp, int nP) {
+__global__ void __launch_bounds__(512) k_null_proj(const int64_t* __restrict__ slot_off,
+                                                   const double* __restrict__ w, T* __restrict__ xp, int stride) {
     __shared__ double sm[512];
-    const int64_t e0 = elem_off[blockIdx.x], e1 = elem_off[blockIdx.x + 1];
+    const int64_t e0 = slot_off[blockIdx.x], e1 = slot_off[blockIdx.x + 1];
+    const int nP = stride;
     double s = 0.0;
     for (int64_t E = e0 + threadIdx.x; E < e1; E += blockDim.x) s += w[E] * (double)xp[E * nP];
     sm[threadIdx.x] = s;
@@ -1293,8 +1330,11 @@ static int op_grid(const hho_ctx* ctx, const Items& it) {
 // rows of a face held by one thread in k_spmv_b: small blocks whole, larger
 // ones split in two or three row groups so that enough warps are in flight
 constexpr int face_rows_for(int B) {
-    return B <= 4 ? B : (B % 2 == 0 && B <= 12 ? B / 2 : (B % 3 == 0 ? (B / 3 <= 10 ? B / 3 : B / 6) : B));
+    return B <= 4 ? B
+                  : (B % 2 == 0 && B <= 12 ? B / 2
+                                           : (B % 3 == 0 ? (B / 3 <= 10 ? B / 3 : B / 6) : (B % 4 == 0 ? B / 4 : B)));
 }
+static_assert(face_rows_for(40) == 10 && face_rows_for(24) == 8 && face_rows_for(30) == 10, "face row groups");
 
 // rows of an element held by one thread: a divisor of the pressure block size
 // that the degree behind B gives under velocity-only condensation
@@ -1369,7 +1409,9 @@ static void launch_jacobi(hho_ctx* ctx, const LevelMat& L, const T* w, const dou
         case 10: launch_jacobi_b_B<10, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
         case 12: launch_jacobi_b_B<12, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
         case 18: launch_jacobi_b_B<18, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 24: launch_jacobi_b_B<24, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
         case 30: launch_jacobi_b_B<30, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
+        case 40: launch_jacobi_b_B<40, T>(ctx, L, w, den, v, z, Vp, ld, npend, pc); break;
         default:
             k_apply_jacobi<T><<<grid1d(L.n, 256), 256, 0, ctx->stream>>>(view<T>(L), w, den, v, z, Vp, ld, npend,
                                                                          pc);
@@ -1378,7 +1420,12 @@ static void launch_jacobi(hho_ctx* ctx, const LevelMat& L, const T* w, const dou
 }
 
 // ---- interleaved FP32 kernels (LevelMat::ilv) ----
-static bool ilv_supported(int b, int nP) { return np_full(b) > 0 && (nP == 1 || nP == np_full(b)); }
+// Scheme 1 levels with the block sizes of np_full, and the HHO-hp levels above
+// the coarse one (no element rows; 2D b = 3 (k+1), 3D b = 12, 24, 40)
+static bool ilv_supported(int b, int nP) {
+    if (nP == 0) return b == 3 || b == 6 || b == 9 || b == 12 || b == 24 || b == 40;
+    return np_full(b) > 0 && (nP == 1 || nP == np_full(b));
+}
 
 static Items items_v(const LevelMat& L) {
     Items it;
@@ -1403,11 +1450,11 @@ template <int B, int NP>
 static void launch_spmv_v_BN(hho_ctx* ctx, const LevelMat& L, const float* x, const float* bv, float* y, int mode,
                              const float* V, int64_t ld, int nv, int self, double* partial, unsigned* counter,
                              double* out, int hook, double* sc, GS gsl, int j, Restr rs) {
-    if constexpr (B == 18 || B == 30) {  // large 3D face blocks: warp per face
+    if constexpr (B == 18 || B == 30 || B == 24 || B == 40) {  // large 3D face blocks: warp per face
         if (ctx->spmv_warp) {
             Items it;
             it.ftiles = L.nf;
-            it.etiles = (L.ne + 31) / 32;
+            it.etiles = NP > 0 ? (L.ne + 31) / 32 : 0;
             it.fgroups = it.egroups = 1;
             const int g = op_grid(ctx, it);
             k_spmv_w<B, NP><<<g, RT, 0, ctx->stream>>>(view<float>(L), it.ftiles, it.etiles, x, bv, y, mode, V, ld,
@@ -1418,6 +1465,7 @@ static void launch_spmv_v_BN(hho_ctx* ctx, const LevelMat& L, const float* x, co
     constexpr int RF = rf_v(B);
     Items it = items_v(L);
     it.fgroups = B / RF;
+    if constexpr (NP == 0) it.etiles = 0;
     const int g = op_grid(ctx, it);
     k_spmv_v<B, NP, RF><<<g, RT, 0, ctx->stream>>>(view<float>(L), it, x, bv, y, mode, V, ld, nv, self, partial,
                                                    counter, out, hook, sc, gsl, j, rs);
@@ -1426,16 +1474,17 @@ static void launch_spmv_v_BN(hho_ctx* ctx, const LevelMat& L, const float* x, co
 template <int B, int NP>
 static void launch_jacobi_v_BN(hho_ctx* ctx, const LevelMat& L, const float* w, const double* den, float* v,
                                float* z, const float* Vp, int64_t ld, int npend, const double* pc) {
-    if constexpr (B == 18 || B == 30) {
+    if constexpr (B == 18 || B == 30 || B == 24 || B == 40) {
         if (ctx->spmv_warp) {
-            const int64_t etiles = (L.ne + 31) / 32;
+            const int64_t etiles = NP > 0 ? (L.ne + 31) / 32 : 0;
             const int64_t g = std::max<int64_t>(1, std::min<int64_t>((L.nf + etiles + RT / 32 - 1) / (RT / 32), GMAX));
             k_jacobi_w<B, NP><<<(int)g, RT, 0, ctx->stream>>>(view<float>(L), etiles, w, den, v, z, Vp, ld, npend,
                                                               pc);
             return;
         }
     }
-    const Items it = items_v(L);
+    Items it = items_v(L);
+    if constexpr (NP == 0) it.etiles = 0;
     const int64_t g = std::max<int64_t>(1, std::min<int64_t>((it.total() + RT / 32 - 1) / (RT / 32), GMAX));
     k_jacobi_v<B, NP><<<(int)g, RT, 0, ctx->stream>>>(view<float>(L), it, w, den, v, z, Vp, ld, npend, pc);
 }
@@ -1460,6 +1509,12 @@ static void launch_jacobi_v_BN(hho_ctx* ctx, const LevelMat& L, const float* w, 
         case 18 * 64 + 1: CALL(18, 1); break;                                                                      \
         case 30 * 64 + 20: CALL(30, 20); break;                                                                    \
         case 30 * 64 + 1: CALL(30, 1); break;                                                                      \
+        case 3 * 64 + 0: CALL(3, 0); break;                                                                        \
+        case 6 * 64 + 0: CALL(6, 0); break;                                                                        \
+        case 9 * 64 + 0: CALL(9, 0); break;                                                                        \
+        case 12 * 64 + 0: CALL(12, 0); break;                                                                      \
+        case 24 * 64 + 0: CALL(24, 0); break;                                                                      \
+        case 40 * 64 + 0: CALL(40, 0); break;                                                                      \
         default: return false;                                                                                     \
     }
 
@@ -1504,7 +1559,9 @@ static bool launch_spmv_b(hho_ctx* ctx, const LevelMat& L, const T* x, const T* 
         HHO_B_CASE(10)
         HHO_B_CASE(12)
         HHO_B_CASE(18)
+        HHO_B_CASE(24)
         HHO_B_CASE(30)
+        HHO_B_CASE(40)
         default:
             return false;
     }
@@ -1806,20 +1863,25 @@ hho_status vcycle(hho_ctx* ctx, const double* r, double* z) {
 }
 
 template <typename T>
-hho_status null_project(hho_ctx* ctx, int64_t nf_rows, int nP, T* x) {
+hho_status null_project(hho_ctx* ctx, const LevelMat& L, T* x) {
     if (!ctx->has_null) return HHO_OK;
-    k_null_proj<T><<<ctx->probs.P, 512, 0, ctx->stream>>>(ctx->d_elem_off, ctx->null_w, x + nf_rows, nP);
+    const bool hp = ctx->disc.cond == HHO_HPCOND;
+    T* xp = hp ? x + null_slot(ctx, L, 0) : x + L.nf * L.b;
+    k_null_proj<T><<<ctx->probs.P, 512, 0, ctx->stream>>>(ctx->d_null_off, ctx->null_w, xp, hp ? L.b : L.nP);
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());
     return HHO_OK;
 }
-template hho_status null_project<double>(hho_ctx*, int64_t, int, double*);
-template hho_status null_project<float>(hho_ctx*, int64_t, int, float*);
+template hho_status null_project<double>(hho_ctx*, const LevelMat&, double*);
+template hho_status null_project<float>(hho_ctx*, const LevelMat&, float*);
 
 // Per-problem pressure kernels: a problem without Neumann face has the
-// constant pressure in the kernel of its operator; its unit kernel vector
-// has sqrt(|T|) / sqrt(|Omega_p|) on the first (constant) pressure unknown of
-// each element T (orthonormal bases: the constant 1 has coefficient sqrt|T|).
+// constant pressure in the kernel of its operator.  Scheme 1: its unit kernel
+// vector has sqrt(|T|) / sqrt(|Omega_p|) on the first (constant) pressure
+// unknown of each element T (orthonormal bases: the constant 1 has
+// coefficient sqrt|T|).  HHO-hp: the constant hybrid pressure (p_T = p_F = 1)
+// condensed to the skeleton is sqrt(|F|) on the constant face-pressure
+// coefficient of every face F, normalised by sqrt(sum_F |F|).
 hho_status null_build(hho_ctx* ctx) {
     Problems& pr = ctx->probs;
     const Disc& D = ctx->disc;
@@ -1834,23 +1896,33 @@ hho_status null_build(hho_ctx* ctx) {
     for (char h : pr.has_null) ctx->has_null |= (h != 0);
     dfree(ctx->null_w);
     ctx->null_w = nullptr;
-    dfree(ctx->d_elem_off);
-    ctx->d_elem_off = nullptr;
+    dfree(ctx->d_null_off);
+    ctx->d_null_off = nullptr;
+    ctx->h_null_w.clear();
     if (!ctx->has_null) return HHO_OK;
-    std::vector<double> meas(D.ne), w(D.ne, 0.0);
-    HHO_CUDA(cudaMemcpy(meas.data(), D.emeas, D.ne * sizeof(double), cudaMemcpyDeviceToHost));
+    const bool hp = D.cond == HHO_HPCOND;
+    const std::vector<int64_t>& off = hp ? pr.face_off : pr.elem_off;
+    const int64_t ns = hp ? D.nf : D.ne;
+    std::vector<double> meas(ns), w(ns, 0.0);
+    if (hp) {
+        std::vector<FaceGeo> g(D.nf);
+        HHO_CUDA(cudaMemcpy(g.data(), D.fgeo, D.nf * sizeof(FaceGeo), cudaMemcpyDeviceToHost));
+        for (int64_t F = 0; F < D.nf; ++F) meas[F] = g[F].meas;
+    } else {
+        HHO_CUDA(cudaMemcpy(meas.data(), D.emeas, D.ne * sizeof(double), cudaMemcpyDeviceToHost));
+    }
     for (int p = 0; p < pr.P; ++p) {
         if (!pr.has_null[p]) continue;
         double tot = 0.0;
-        for (int64_t T = pr.elem_off[p]; T < pr.elem_off[p + 1]; ++T) tot += meas[T];
+        for (int64_t E = off[p]; E < off[p + 1]; ++E) tot += meas[E];
         const double inv = 1.0 / std::sqrt(tot);
-        for (int64_t T = pr.elem_off[p]; T < pr.elem_off[p + 1]; ++T) w[T] = std::sqrt(meas[T]) * inv;
+        for (int64_t E = off[p]; E < off[p + 1]; ++E) w[E] = std::sqrt(meas[E]) * inv;
     }
+    ctx->h_null_w = w;
     HHO_TRY(dalloc(ctx, &ctx->null_w, w.size()));
     HHO_CUDA(cudaMemcpy(ctx->null_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
-    HHO_TRY(dalloc(ctx, &ctx->d_elem_off, pr.elem_off.size()));
-    HHO_CUDA(cudaMemcpy(ctx->d_elem_off, pr.elem_off.data(), pr.elem_off.size() * sizeof(int64_t),
-                        cudaMemcpyHostToDevice));
+    HHO_TRY(dalloc(ctx, &ctx->d_null_off, off.size()));
+    HHO_CUDA(cudaMemcpy(ctx->d_null_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     return HHO_OK;
 }
 
@@ -1963,7 +2035,7 @@ hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, 
     ctx->coarse_its_total = 0;
     k_convert<double, double><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, ctx->rhs, bvec);
     ++ctx->launches;
-    HHO_TRY(null_project<double>(ctx, L0.nf * L0.b, L0.nP, bvec));
+    HHO_TRY(null_project<double>(ctx, L0, bvec));
     k_zero<double><<<grid1d(n, 256), 256, 0, ctx->stream>>>(n, x);
     ++ctx->launches;
     // ||b||, which is also beta of the first restart cycle (r = b)
@@ -2021,7 +2093,7 @@ hho_status fgmres(hho_ctx* ctx, double rtol, int maxit, int restart, double* x, 
             }
         }
         if (ctx->has_null) {
-            HHO_TRY(null_project<double>(ctx, L0.nf * L0.b, L0.nP, x));
+            HHO_TRY(null_project<double>(ctx, L0, x));
             launch_spmv_dot<double>(ctx, 0, x, bvec, W->fw, 1, nullptr, n, 0, 1, sc + 0, HOOK_START, sc, G, 0);
             HHO_TRY(host_read(ctx, sc + 1, hs, 1));
             beta = hs[0];

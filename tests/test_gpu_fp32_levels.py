@@ -6,9 +6,10 @@ blocks: one warp per face).  Every level above the coarse one is checked
 against the FP64 operator (itself pinned to the oracle at 1e-13) for the block
 sizes of 2D triangles (k = 1..5: face blocks of 4..12 unknowns, pressure
 blocks of 3..21) and 3D hexahedra (k = 1..3: face blocks of 9, 18 and 30),
-under both condensations; for the large 3D blocks the warp-per-face kernel is
-also compared with the one-thread-per-face one.  One FP32 V-cycle is compared
-with the oracle's FP64 V-cycle: FP32 rounding amplified by the coarse
+under both condensations and for HHO-hp (face blocks of 3 (k+1) in 2D, 12, 24
+and 40 in 3D, no element rows); for the large 3D blocks the warp-per-face
+kernel is also compared with the one-thread-per-face one.  One FP32 V-cycle is
+compared with the oracle's FP64 V-cycle: FP32 rounding amplified by the coarse
 conditioning, 1e-3 relative.
 """
 import numpy as np
@@ -18,6 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle.hho import HHO  # noqa: E402
+from oracle.hho_hp import HHOhp  # noqa: E402
 from oracle.pmg import PMG  # noqa: E402
 from synthetic import tri_mesh, hex_mesh, fields  # noqa: E402
 from parity_util import report  # noqa: E402
@@ -35,7 +37,7 @@ def hho_mod():
 CASES = [("tri", k) for k in (1, 2, 3, 4, 5)] + [("hex", 1), ("hex", 2), ("hex", 3)]
 
 
-@pytest.mark.parametrize("cond", ["v", "vp"])
+@pytest.mark.parametrize("cond", ["v", "vp", "hp"])
 @pytest.mark.parametrize("shape,k", CASES, ids=[f"{s}-k{k}" for s, k in CASES])
 def test_fp32_levels_match_fp64(hho_mod, shape, k, cond):
     if shape == "tri":
@@ -68,7 +70,7 @@ def test_fp32_levels_match_fp64(hho_mod, shape, k, cond):
     b = rng.standard_normal(ctx.ndof(0))
     z32 = torch.empty(ctx.ndof(0), dtype=torch.float64, device="cuda")
     ctx.vcycle(torch.from_numpy(b).cuda(), z32)
-    h = HHO(mesh, k, cond)
+    h = HHOhp(mesh, k) if cond == "hp" else HHO(mesh, k, cond)
     ref = PMG(h, degrees).apply(b)
     e_v = float(np.linalg.norm(z32.cpu().numpy() - ref) / np.linalg.norm(ref))
     report(f"fp32levels {shape} k={k} {cond}", operator=worst, vcycle_vs_oracle=e_v)
