@@ -13,6 +13,8 @@ coefficients whose first is the mean mode (the constant basis function).
 
 Global condensed ordering: one block of b = d*n_F per face (component-major),
 then one block of n_P per element (n_P = 1 for v&p-cond, n_E for v-cond).
+Uncondensed ("unc", Sec. 5.4's reference formulation): the same face blocks,
+then one block of n_P = (d+1) n_E per element, [U_T (d components) | P_T].
 
 Readings of the paper (each listed in the design notes):
 * Penalty (Eq. HHOdiscrMNT, "eta large enough"): eta_F = 4 (k+1)(k+d)/d |F| h_F / |T|.
@@ -40,6 +42,7 @@ from .geometry import mesh_geometry
 
 VCOND = "v"
 VPCOND = "vp"
+UNCOND = "unc"  # uncondensed (the reference point of Sec. 5.4): nothing eliminated
 
 
 def penalty(k, d, meas_F, h_F, meas_T):
@@ -176,6 +179,8 @@ class LocalSystem:
         UT = list(range(nUT))
         UdT = list(range(nUT, self.nvec))
         Pidx = [self.nvec + i for i in range(nE)]
+        if cond == UNCOND:
+            return [], UdT + UT + Pidx
         if cond == VCOND:
             return UT, UdT + Pidx
         return UT + Pidx[1:], UdT + Pidx[:1]
@@ -183,6 +188,9 @@ class LocalSystem:
 
 def schur(K, rhs, elim, keep):
     """Schur complement of the eliminated block: S = K_kk - K_ke K_ee^{-1} K_ek."""
+    if not elim:  # nothing eliminated (uncondensed)
+        S = K[np.ix_(keep, keep)]
+        return S, (None if rhs is None else rhs[keep]), np.zeros((0, len(keep))), (None if rhs is None else np.zeros(0))
     Kee = K[np.ix_(elim, elim)]
     Kek = K[np.ix_(elim, keep)]
     Kke = K[np.ix_(keep, elim)]
@@ -209,7 +217,7 @@ class HHO:
         self.nE = dim_P(self.d, k)
         self.nF = dim_P(self.d - 1, k)
         self.b = self.d * self.nF
-        self.nP = 1 if cond == VPCOND else self.nE
+        self.nP = 1 if cond == VPCOND else (self.d + 1) * self.nE if cond == UNCOND else self.nE
         self.local = [LocalSystem(self, t) for t in range(mesh.n_elem)]
         self.n_face_dofs = mesh.n_face * self.b
         self.ndof = self.n_face_dofs + mesh.n_elem * self.nP
@@ -271,7 +279,7 @@ class HHO:
             r = L.rhs(self, f_vals, gD, gN)
             self.local_rhs.append(r)
             elim, keep, X = self.elim_ops[t]
-            y = np.linalg.solve(L.K[np.ix_(elim, elim)], r[elim])
+            y = np.linalg.solve(L.K[np.ix_(elim, elim)], r[elim]) if elim else np.zeros(0)
             g = r[keep] - L.K[np.ix_(keep, elim)] @ y
             rhs[self.global_kept(t)] += g
         return rhs
@@ -282,8 +290,9 @@ class HHO:
         if self.mesh.has_neumann():
             return None
         n = np.zeros(self.ndof)
+        off = self.d * self.nE if self.cond == UNCOND else 0  # the mean pressure in the element block
         for t in range(self.mesh.n_elem):
-            n[self.n_face_dofs + t * self.nP] = np.sqrt(self.elems[t].meas)
+            n[self.n_face_dofs + t * self.nP + off] = np.sqrt(self.elems[t].meas)
         return n / np.linalg.norm(n)
 
     def direct_solve(self, rhs):
@@ -336,7 +345,7 @@ class HHO:
             elim, keep, X = self.elim_ops[t]
             xk = x[self.global_kept(t)]
             r = self.local_rhs[t]
-            y = np.linalg.solve(L.K[np.ix_(elim, elim)], r[elim])
+            y = np.linalg.solve(L.K[np.ix_(elim, elim)], r[elim]) if elim else np.zeros(0)
             full = np.zeros(L.K.shape[0])
             full[keep] = xk
             full[elim] = y - X @ xk

@@ -4,7 +4,8 @@
   orthonormal bases the restriction keeps, per face and per velocity component,
   the first dim P^{k_{l+1}}_{d-1} coefficients, and per element the first
   n_P(k_{l+1}) pressure coefficients (n_P = 1 for v&p-cond); prolongation is
-  its transpose (zero padding).  For HHO-hp (Scheme 2) the face pressure is one
+  its transpose (zero padding).  Uncondensed, every element block is d+1
+  components (velocity, pressure) truncated the same way.  For HHO-hp (Scheme 2) the face pressure is one
   more face component truncated the same way, and there are no element rows.
 * Coarse operators (Sec. 4.2): S^{l+1} = I^{l+1}_l S^l I^l_{l+1}, formed here
   as a sparse triple product with the selection matrix.
@@ -44,11 +45,27 @@ def n_comp(d, cond):
 
 
 def n_pres(d, k_l, cond):
-    """Kept pressure coefficients per element: the mean for v&p-cond, all of
-    P^k_l for v-cond, none for HHO-hp (its element pressure is eliminated)."""
+    """Kept unknowns per element: the mean pressure for v&p-cond, all of
+    P^k_l for v-cond, none for HHO-hp (its element pressure is eliminated),
+    the d velocity components and the pressure (d+1 blocks of P^k_l) when
+    nothing is condensed."""
     if cond == "hp":
         return 0
+    if cond == "unc":
+        return (d + 1) * dim_P(d, k_l)
     return 1 if cond == "vp" else dim_P(d, k_l)
+
+
+def e_comp(d, cond):
+    """Components of an element block, each truncated on its own: d + 1
+    (velocity and pressure) when nothing is condensed, else 1 (the kept
+    pressure coefficients form one prefix)."""
+    return d + 1 if cond == "unc" else 1
+
+
+def mean_offset(d, k_l, cond):
+    """Position of the constant pressure mode in an element block."""
+    return d * dim_P(d, k_l) if cond == "unc" else 0
 
 
 class Level:
@@ -113,10 +130,13 @@ def restriction(mesh, d, k_fine, k_coarse, cond):
             for j in range(nFc):
                 rows.append(F * bc + c * nFc + j)
                 cols.append(F * bf + c * nFf + j)
+    ec = e_comp(d, cond)
+    nEc, nEf = nPc // ec if ec else 0, nPf // ec if ec else 0
     for T in range(mesh.n_elem):
-        for i in range(nPc):
-            rows.append(mesh.n_face * bc + T * nPc + i)
-            cols.append(mesh.n_face * bf + T * nPf + i)
+        for c in range(ec):
+            for i in range(nEc):
+                rows.append(mesh.n_face * bc + T * nPc + c * nEc + i)
+                cols.append(mesh.n_face * bf + T * nPf + c * nEf + i)
     nc = mesh.n_face * bc + mesh.n_elem * nPc
     nf_ = mesh.n_face * bf + mesh.n_elem * nPf
     return sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(nc, nf_))
@@ -246,8 +266,9 @@ class PMG:
                 for F in range(L.nf):
                     n[F * L.b + d * L.nF] = np.sqrt(hho.faces[F].meas)
             else:
+                off = mean_offset(d, L.k, cond)
                 for T in range(L.ne):
-                    n[L.elem_slice(T).start] = np.sqrt(hho.elems[T].meas)
+                    n[L.elem_slice(T).start + off] = np.sqrt(hho.elems[T].meas)
             self.null = n / np.linalg.norm(n)
         if coarse == "lu":
             A = L.S.toarray()
@@ -259,7 +280,7 @@ class PMG:
             A = L.S.tocsc().astype(np.float64)
             if self.null is not None:
                 alpha = float(np.mean(np.abs(A.diagonal())))
-                pin = d * L.nF if cond == "hp" else L.elem_slice(0).start
+                pin = d * L.nF if cond == "hp" else L.elem_slice(0).start + mean_offset(d, L.k, cond)
                 A = (A + sp.csc_matrix(([alpha], ([pin], [pin])), shape=A.shape)).tocsc()
             self.splu = spla.splu(A)
         self.coarse_its = []
