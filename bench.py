@@ -42,10 +42,12 @@ METRIC = "FGMRES+p-MG time & DOFs/s to 1e-8 rel. residual; V-cycle GB/s vs HBM p
 UNIT = "DOF/s"
 # DRAM bytes (read + write) of one FP32 level-0 operator launch, from the ncu
 # captures summarised under profiles/ (kernels unchanged since); keyed by
-# (mesh, n, k, condensation).  The 32^3 entry is the 16^3 capture (516.5 MB per
-# launch, 1.035x its algorithmic bytes) scaled by the ratio of the algorithmic
-# bytes (7.976): the full-size workload is too large for a multi-pass capture.
-SPMV_F32_TRAFFIC = {("tri", 128, 3, "v"): 144286208 + 3245056, ("hex", 32, 3, "vp"): 4119717980}
+# (mesh, n, k, condensation).  The 32^3 entries are the 16^3 captures (v&p:
+# 516.5 MB per launch, 1.035x its algorithmic bytes; HHO-hp: 894.1 MB, 1.022x)
+# scaled by the ratio of the algorithmic bytes (7.976): the full-size workload is
+# too large for a multi-pass capture.
+SPMV_F32_TRAFFIC = {("tri", 128, 3, "v"): 144286208 + 3245056, ("hex", 32, 3, "vp"): 4119717980,
+                    ("hex", 32, 3, "hp"): round((892412928 + 1694208) * 6979174400 / 874983424)}
 
 # the named workloads (BASELINE configurations); command-line values override
 SPECS = {
@@ -56,6 +58,8 @@ SPECS = {
     # HHO-hp (Scheme 2) on the C2 and C3 meshes
     "hp2": dict(mesh="tri", n=128, k=3, cond="hp", prec="fp32", coarse_fp32=1, sample_n=24),
     "hp3": dict(mesh="hex", n=32, k=3, cond="hp", prec="fp32", coarse_fp32=1, sample_n=4),
+    # uncondensed HHO-dp on the C2 mesh (the reference point of the condensation gains), block ILU(0) smoother
+    "unc2": dict(mesh="tri", n=128, k=3, cond="unc", prec="fp32", coarse_fp32=1, sample_n=16, smoother="ilu"),
 }
 
 
@@ -65,24 +69,26 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "sweep", "batch", "learned", "hp2", "hp3"],
+    ap.add_argument("--workload", default="c3",
+                    choices=["c3", "c2", "c1", "sweep", "batch", "learned", "hp2", "hp3", "unc2"],
                     help="c3: 32^3 jittered hexahedra, k=3, v&p (default); c2: 128x128 jittered triangles, k=3, "
                          "v-cond; c1: 16x16 quadrilaterals, k=3, v&p, FP64; sweep: the c2 mesh over k=1..5, both "
                          "condensations, FP64 and FP32 V-cycles; batch: many independent small problems; learned: "
                          "the learned smoother against the plain one; hp2 / hp3: HHO-hp (Scheme 2) on the c2 "
-                         "triangle mesh (k=3) and the c3 hexahedral mesh (k=3)")
+                         "triangle mesh (k=3) and the c3 hexahedral mesh (k=3); unc2: uncondensed HHO-dp on the c2 "
+                         "mesh (k=3, block ILU(0) smoother)")
     ap.add_argument("--mesh", default=None, choices=["tri", "hex", "quad"],
                     help="override the workload's mesh family (tri: n x n squares split into triangles; hex: n^3 "
                          "jittered hexahedra; quad: n x n quadrilaterals)")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--k", type=int, default=None)
-    ap.add_argument("--cond", default=None, choices=["v", "vp", "hp"],
-                    help="Scheme 1 with velocity-only (v) or velocity-pressure (vp) condensation, or Scheme 2 "
-                         "(HHO-hp, hybrid pressure, every element unknown condensed)")
+    ap.add_argument("--cond", default=None, choices=["v", "vp", "hp", "unc"],
+                    help="Scheme 1 with velocity-only (v) or velocity-pressure (vp) condensation, Scheme 2 "
+                         "(HHO-hp, hybrid pressure, every element unknown condensed), or Scheme 1 uncondensed (unc)")
     ap.add_argument("--prec", default=None, choices=["fp32", "fp64"], help="V-cycle precision of the headline")
     ap.add_argument("--coarse-fp32", type=int, default=None, choices=[0, 1],
                     help="FP32 coarse solve inside the FP32 V-cycle")
-    ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "ilu"],
+    ap.add_argument("--smoother", default=None, choices=["jacobi", "ilu"],
                     help="preconditioner of the smoother's GMRES: block Jacobi or block ILU(0)")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--sample-n", type=int, default=None, help="mesh size of the CPU-oracle sample")
@@ -115,6 +121,8 @@ def parse():
             setattr(args, key, spec[key])
     if args.coarse_fp32 is None:
         args.coarse_fp32 = spec["coarse_fp32"]
+    if args.smoother is None:
+        args.smoother = spec.get("smoother", "jacobi")
     return args
 
 
@@ -242,7 +250,7 @@ def oracle_sample(args, steps=1):
         t0 = time.perf_counter()
         h = oracle_disc(mesh, args.k, args.cond)
         rhs = h.assemble_rhs(*h.data_values(fld))
-        pmg = PMG(h, list(range(args.k, -1, -1)))
+        pmg = PMG(h, list(range(args.k, -1, -1)), smoother=args.smoother)
         t_setup = time.perf_counter() - t0
         rates = []
         for _ in range(max(1, steps)):
@@ -290,7 +298,7 @@ def level_counts(mesh, k_l, cond):
     of every face row and element row) and the block-Jacobi data."""
     d = mesh.dim
     b = (d + 1 if cond == "hp" else d) * _dimP(d - 1, k_l)  # HHO-hp: face pressure as one more component
-    nP = 0 if cond == "hp" else 1 if cond == "vp" else _dimP(d, k_l)
+    nP = 0 if cond == "hp" else 1 if cond == "vp" else (d + 1) * _dimP(d, k_l) if cond == "unc" else _dimP(d, k_l)
     nf, ne = mesh.n_face, mesh.n_elem
     N = np.diff(mesh.elem_face_ptr)
     fe = mesh.face_elem
@@ -308,18 +316,22 @@ def spmv_bytes(mesh, k_l, cond, value_bytes):
     return z * value_bytes + idx + 2 * n * value_bytes
 
 
-def vcycle_bytes(mesh, degrees, cond, s, coarse_values, coarse_s, m=2):
+def vcycle_bytes(mesh, degrees, cond, s, coarse_values, coarse_s, m=2, smoother="jacobi"):
     """Algorithmic bytes of one V-cycle (Algorithm MG_V with m GMRES smoothing
     steps): per level above the coarse one (2m+3) operator products (pre/post
     Arnoldi steps, the post-smoother's initial residual, the fused defect),
-    2m block-Jacobi applies, 6m n_l vector passes of orthogonalisation and
+    2m block-Jacobi applies (block ILU(0): 2m sweeps over factors the size of
+    the level operator), 6m n_l vector passes of orthogonalisation and
     updates, 3 n_l of transfers; the coarse solve reads its stored operators
     once and two vectors."""
     tot = 0
     for kl in degrees[:-1]:
         n, z, idx, J, b, nP = level_counts(mesh, kl, cond)
         tot += (2 * m + 3) * (z * s + idx + 2 * n * s)
-        tot += 2 * m * (J * s + 2 * n * s)
+        if smoother == "ilu":  # block ILU(0) factors on the operator's block pattern, one sweep each way
+            tot += 2 * m * (z * s + idx + 2 * n * s)
+        else:
+            tot += 2 * m * (J * s + 2 * n * s)
         tot += 6 * m * n * s + 3 * n * s
     nL = level_counts(mesh, degrees[-1], cond)[0]
     tot += coarse_values * coarse_s + 2 * nL * coarse_s
@@ -472,7 +484,7 @@ def run_ours(args):
         # V-cycle: algorithmic bytes over its time (graph replay, inputs larger than L2 or L2 flushed)
         s_val = 4 if args.prec == "fp32" else 8
         cs = 4 if (args.prec == "fp32" and args.coarse_fp32) else 8
-        vbytes = vcycle_bytes(mesh, degrees, args.cond, s_val, coarse["values_per_solve"], cs)
+        vbytes = vcycle_bytes(mesh, degrees, args.cond, s_val, coarse["values_per_solve"], cs, smoother=args.smoother)
         rv = torch.randn(ndof, dtype=torch.float64, device="cuda")
         zv = torch.empty_like(rv)
         ms_v = time_on_stream(lambda: ctx.vcycle(rv, zv), 10)
