@@ -47,8 +47,12 @@ typedef enum {
  * (HHO-hp, Sec. 2.3.2: element velocity of degree k+1, hybrid element/face
  * pressure) with every element unknown condensed; its condensed unknowns are
  * one block of (d+1) n_F per face (velocity components, then the face
- * pressure) and no element rows. */
-typedef enum { HHO_VCOND = 0, HHO_VPCOND = 1, HHO_HPCOND = 2 } hho_cond;
+ * pressure) and no element rows.  HHO_UNCOND: Scheme 1 uncondensed (the
+ * reference formulation of Sec. 5.4): face blocks of d n_F, then one block of
+ * (d+1) n_E per element ([U_T (d components) | P_T]); its p-multilevel
+ * hierarchy truncates every element component like a face component, and its
+ * V-cycle needs the block ILU(0) smoother (hho_set_option "smoother" = 1). */
+typedef enum { HHO_VCOND = 0, HHO_VPCOND = 1, HHO_HPCOND = 2, HHO_UNCOND = 3 } hho_cond;
 typedef enum { HHO_FP64 = 0, HHO_FP32 = 1 } hho_prec;
 /* Preconditioner of the smoother's GMRES, selected by hho_set_option("smoother", v) before pmg_setup. */
 typedef enum { HHO_SMOOTH_BJACOBI = 0, HHO_SMOOTH_ILU = 1 } hho_smoother;
@@ -96,10 +100,13 @@ typedef struct {
  * local operators of Scheme 1 with k' = k (Sec. 2.2, Eq. HHOdiscr:residuals,
  * Eq. def:HHOAB) or of Scheme 2 (cond = HHO_HPCOND, Sec. 2.3.2), the element
  * static condensation (v-cond Eq. ST.1, v&p-cond Eq. ST.2, or every element
- * unknown for Scheme 2) and the assembled level-0 condensed operator in the
- * face-block layout.  k in 0..5 (2D) or 0..3 (3D).  Scheme 2 contexts support
- * one problem (no hho_set_batch), the block-Jacobi smoother, no learned
- * smoother, and the dense or multifrontal coarse solve.  stream: a
+ * unknown for Scheme 2, none for HHO_UNCOND) and the assembled level-0
+ * operator in the face-block layout.  k in 0..5 (2D) or 0..3 (3D).  Scheme 2
+ * contexts support one problem (no hho_set_batch), the block-Jacobi smoother,
+ * no learned smoother, and the dense or multifrontal coarse solve;
+ * uncondensed contexts likewise one problem, no learned smoother and the dense
+ * or multifrontal coarse solve, with element blocks of at most 32 unknowns
+ * (2D k <= 3, 3D k <= 1).  stream: a
  * cudaStream_t (NULL = legacy default stream).  *out receives the new
  * context. */
 hho_status hho_setup(const hho_mesh* mesh, int k, int cond, void* stream, hho_ctx** out);

@@ -107,13 +107,17 @@ __global__ void k_assemble_p(int64_t nf, int64_t ne, int b, int nP, int N_max, c
 // coarse index within a face block -> fine index (component-major prefix)
 __device__ __forceinline__ int face_map(int i, int nFc, int nFf) { return (i / nFc) * nFf + (i % nFc); }
 
+// Element blocks hold ec components (1: a prefix of pressure coefficients;
+// d + 1 when nothing is condensed: velocity components and pressure), each
+// truncated like a face component.
 __global__ void k_extract(int64_t nf, int64_t ne, int S_max, int N_max, int bf, int nFf, int nPf, int bc, int nFc,
-                          int nPc, const double* __restrict__ ff0, const double* __restrict__ fp0,
+                          int nPc, int ec, const double* __restrict__ ff0, const double* __restrict__ fp0,
                           const double* __restrict__ pf0, const double* __restrict__ pp0, double* __restrict__ ff,
                           double* __restrict__ fp, double* __restrict__ pf, double* __restrict__ pp) {
     int64_t n_ff = (int64_t)S_max * bc * bc * nf, n_fp = 2LL * nPc * bc * nf, n_pf = (int64_t)N_max * bc * nPc * ne,
             n_pp = (int64_t)nPc * nPc * ne;
     int64_t tot = n_ff + n_fp + n_pf + n_pp;
+    const int nEc = nPc / ec, nEf = nPf / ec;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         if (i < n_ff) {
             int64_t F = i % nf, rest = i / nf;
@@ -130,7 +134,7 @@ __global__ void k_extract(int64_t nf, int64_t ne, int S_max, int N_max, int bf, 
             rest /= bc;
             int c = rest % nPc;
             int p = (int)(rest / nPc);
-            fp[j] = fp0[(((int64_t)p * nPf + c) * bf + face_map(r, nFc, nFf)) * nf + F];
+            fp[j] = fp0[(((int64_t)p * nPf + face_map(c, nEc, nEf)) * bf + face_map(r, nFc, nFf)) * nf + F];
         } else if (i < n_ff + n_fp + n_pf) {
             int64_t j = i - n_ff - n_fp;
             int64_t T = j % ne, rest = j / ne;
@@ -138,13 +142,13 @@ __global__ void k_extract(int64_t nf, int64_t ne, int S_max, int N_max, int bf, 
             rest /= nPc;
             int c = rest % bc;
             int f = (int)(rest / bc);
-            pf[j] = pf0[(((int64_t)f * bf + face_map(c, nFc, nFf)) * nPf + r) * ne + T];
+            pf[j] = pf0[(((int64_t)f * bf + face_map(c, nFc, nFf)) * nPf + face_map(r, nEc, nEf)) * ne + T];
         } else {
             int64_t j = i - n_ff - n_fp - n_pf;
             int64_t T = j % ne, rest = j / ne;
             int r = rest % nPc;
             int c = (int)(rest / nPc);
-            pp[j] = pp0[((int64_t)c * nPf + r) * ne + T];
+            pp[j] = pp0[((int64_t)face_map(c, nEc, nEf) * nPf + face_map(r, nEc, nEf)) * ne + T];
         }
     }
 }
@@ -421,7 +425,10 @@ hho_status build_level(hho_ctx* ctx, int l, int k_l) {
     L.k = k_l;
     L.nF = dimP(D.d - 1, k_l);
     L.b = (D.cond == HHO_HPCOND ? D.d + 1 : D.d) * L.nF;  // HHO-hp: the face pressure is one more component
-    L.nP = (D.cond == HHO_HPCOND) ? 0 : (D.cond == HHO_VPCOND) ? 1 : dimP(D.d, k_l);
+    L.nP = (D.cond == HHO_HPCOND)   ? 0
+           : (D.cond == HHO_VPCOND) ? 1
+           : (D.cond == HHO_UNCOND) ? (D.d + 1) * dimP(D.d, k_l)  // velocity components and pressure
+                                    : dimP(D.d, k_l);
     L.nf = D.nf;
     L.ne = D.ne;
     L.n = L.nf * L.b + L.ne * L.nP;
@@ -430,7 +437,8 @@ hho_status build_level(hho_ctx* ctx, int l, int k_l) {
     int64_t tot = (int64_t)L.S_max * L.b * L.b * L.nf + 2LL * L.nP * L.b * L.nf + (int64_t)L.N_max * L.b * L.nP * L.ne +
                   (int64_t)L.nP * L.nP * L.ne;
     k_extract<<<grid_for(tot, 256), 256, 0, ctx->stream>>>(L.nf, L.ne, L.S_max, L.N_max, Fm.b, Fm.nF, Fm.nP, L.b, L.nF,
-                                                           L.nP, Fm.ff, Fm.fp, Fm.pf, Fm.pp, L.ff, L.fp, L.pf, L.pp);
+                                                           L.nP, elem_comp(D.cond, D.d), Fm.ff, Fm.fp, Fm.pf, Fm.pp,
+                                                           L.ff, L.fp, L.pf, L.pp);
     HHO_CUDA(cudaGetLastError());
     if ((int)ctx->levels.size() > l) {
         free_level(ctx->levels[l]);

@@ -286,10 +286,16 @@ hho_status null_build(hho_ctx* ctx);
 // level L (one block per problem)
 template <typename T>
 hho_status null_project(hho_ctx* ctx, const LevelMat& L, T* x);
+// components of an element block, each truncated on its own by the
+// restriction: d + 1 (velocity, pressure) uncondensed, else 1 (a prefix of
+// kept pressure coefficients)
+inline int elem_comp(int cond, int d) { return cond == HHO_UNCOND ? d + 1 : 1; }
+// position of the constant pressure mode in an element block of nP unknowns
+inline int mean_slot(int cond, int d, int nP) { return cond == HHO_UNCOND ? d * (nP / (d + 1)) : 0; }
 // index of kernel slot i (element or face, see hho_ctx::null_w) in a vector of level L
 inline int64_t null_slot(const hho_ctx* ctx, const LevelMat& L, int64_t i) {
     if (ctx->disc.cond == HHO_HPCOND) return i * L.b + (int64_t)ctx->disc.d * L.nF;
-    return L.nf * L.b + i * L.nP;
+    return L.nf * L.b + i * L.nP + mean_slot(ctx->disc.cond, ctx->disc.d, L.nP);
 }
 // v = r / *den, z = M^{-1} v with the level-0 block-Jacobi preconditioner (FP64)
 hho_status jacobi_apply(hho_ctx* ctx, const double* r, const double* den, double* v, double* z);

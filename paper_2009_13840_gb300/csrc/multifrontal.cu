@@ -79,6 +79,7 @@ struct MFView {
     const int64_t* off_S;
     const double* S;               // fine element Schur complements
     int b0, nF0, nP0, bL, nFL, nPL;
+    int ec;  // components of an element block (1, or d + 1 uncondensed), each truncated on its own
     const double* alpha;
 };
 
@@ -141,10 +142,12 @@ __device__ void assemble_leaf(const MFView& V, double* __restrict__ Wall, int v)
         const int32_t* loc = V.elem_loc + V.elem_loc_off[T];
         for (int idx = threadIdx.x; idx < nkL * nkL; idx += blockDim.x) {
             const int a = idx / nkL, bb = idx % nkL;
+            const int nEL = V.nPL / V.ec, nE0 = V.nP0 / V.ec;
+            const int ea = a - N * V.bL, eb = bb - N * V.bL;
             const int fa = a < N * V.bL ? (a / V.bL) * V.b0 + ((a % V.bL) / V.nFL) * V.nF0 + (a % V.bL) % V.nFL
-                                        : N * V.b0 + (a - N * V.bL);
+                                        : N * V.b0 + (ea / nEL) * nE0 + ea % nEL;
             const int fb = bb < N * V.bL ? (bb / V.bL) * V.b0 + ((bb % V.bL) / V.nFL) * V.nF0 + (bb % V.bL) % V.nFL
-                                         : N * V.b0 + (bb - N * V.bL);
+                                         : N * V.b0 + (eb / nEL) * nE0 + eb % nEL;
             W[(int64_t)loc[a] * w + loc[bb]] += ST[(int64_t)fa * nk0 + fb];
         }
         __syncthreads();
@@ -679,6 +682,7 @@ struct MFSolver {
         V.elem_loc_off = elem_loc_off;
         V.elem_loc = elem_loc;
         V.alpha = alpha;
+        V.ec = 1;
         return V;
     }
 };
@@ -777,6 +781,7 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
     const int d = D.d;
     const int64_t ne = D.ne, nf = D.nf;
     const int bL = L.b, nPL = L.nP;
+    const int pm = mean_slot(D.cond, d, nPL);  // the constant pressure mode in an element block
     const Problems& pr = ctx->probs;
     // element centroids (vertex averages)
     std::vector<double> cen((size_t)ne * d, 0.0);
@@ -863,10 +868,11 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
         for (int64_t i = nd.e0; i < nd.e1; ++i) {
             const int32_t T = perm[i];
             if (nd.child[0] < 0)
-                for (int c = 1; c < nPL; ++c) nd.I.push_back((int32_t)(pbase + (int64_t)T * nPL + c));
+                for (int c = 0; c < nPL; ++c)
+                    if (c != pm) nd.I.push_back((int32_t)(pbase + (int64_t)T * nPL + c));
             if (nPL > 0) {  // HHO-hp has no element rows
-                if (p_owner[T] == v) nd.I.push_back((int32_t)(pbase + (int64_t)T * nPL));
-                else if (!in_subtree(p_owner[T], v)) nd.B.push_back((int32_t)(pbase + (int64_t)T * nPL));
+                if (p_owner[T] == v) nd.I.push_back((int32_t)(pbase + (int64_t)T * nPL + pm));
+                else if (!in_subtree(p_owner[T], v)) nd.B.push_back((int32_t)(pbase + (int64_t)T * nPL + pm));
             }
             for (int q = D.h_ef_ptr[T]; q < D.h_ef_ptr[T + 1]; ++q) {
                 const int F = D.h_ef[q];
@@ -896,7 +902,7 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
             if (!owned_faces[roots[q]].empty()) g = (int32_t)(owned_faces[roots[q]][0] * bL + (int64_t)d * L.nF);
         } else {
             for (int64_t i = rt.e0; i < rt.e1 && g < 0; ++i)
-                if (p_owner[perm[i]] == roots[q]) g = (int32_t)(pbase + (int64_t)perm[i] * nPL);
+                if (p_owner[perm[i]] == roots[q]) g = (int32_t)(pbase + (int64_t)perm[i] * nPL + pm);
         }
         if (g < 0) {
             ctx->err = "pmg_setup: multifrontal coarse solver: no kept pressure at a root";
@@ -1096,6 +1102,7 @@ hho_status mf_build(hho_ctx* ctx, int64_t leaf, MFSolver** out) {
     V.bL = bL;
     V.nFL = L.nF;
     V.nPL = nPL;
+    V.ec = elem_comp(D.cond, d);
     if (ctx->has_null) k_mf_mean_abs_diag<<<1, MF_T, 0, ctx->stream>>>(L.nf, L.ne, L.b, L.nP, L.ff, L.pp, S->alpha);
     else HHO_CUDA(cudaMemsetAsync(S->alpha, 0, sizeof(double), ctx->stream));
     HHO_CUDA(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));

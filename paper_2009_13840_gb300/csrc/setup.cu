@@ -633,6 +633,8 @@ __device__ void load_element(ElemSh& E, int d, int t, const int32_t* ef_ptr, con
 // (n_V = n_R), element pressure P^k plus a face pressure P^k(F) per face, every
 // element unknown eliminated, kept face blocks of (d+1) n_F (velocity, then
 // the face pressure).
+// Uncondensed Scheme 1 eliminates nothing and keeps the faces, then the
+// element block [U_T | P_T].
 // Local vector: [U_T (d n_V) | U_F (N d n_F) | P_T (n_E) | P_F (N n_F, HHO-hp)].
 struct LocalDims {
     int d, k, nR, nE, nF, nV, bv, b, N, ns, nvec, npr, nloc, nel, nk, cond;
@@ -658,6 +660,9 @@ __host__ __device__ inline LocalDims local_dims(int d, int k, int N, int cond) {
     if (hp) {
         D.nel = d * D.nV + D.nE;
         D.nk = N * D.b;
+    } else if (cond == HHO_UNCOND) {
+        D.nel = 0;
+        D.nk = N * D.b + (d + 1) * D.nE;
     } else if (cond == HHO_VCOND) {
         D.nel = d * D.nE;
         D.nk = N * D.b + D.nE;
@@ -675,6 +680,11 @@ __device__ __forceinline__ int elim_idx(const LocalDims& D, int i) {
     return D.cond == HHO_HPCOND ? D.nvec + (i - nUT) : D.nvec + 1 + (i - nUT);
 }
 __device__ __forceinline__ int keep_idx(const LocalDims& D, int i) {
+    if (D.cond == HHO_UNCOND) {  // faces, then the element block [U_T | P_T]
+        if (i < D.N * D.b) return D.d * D.nE + i;
+        const int e = i - D.N * D.b;
+        return e < D.d * D.nE ? e : D.nvec + (e - D.d * D.nE);
+    }
     if (D.cond != HHO_HPCOND) return D.d * D.nE + i;  // faces, then pressures (all for v-cond, the mean for v&p)
     const int f = i / D.b, r = i % D.b;                // HHO-hp: per face its velocity, then its pressure
     return r < D.bv ? D.d * D.nV + f * D.bv + r : D.nvec + D.nE + f * D.nF + (r - D.bv);
@@ -694,7 +704,7 @@ __host__ __device__ inline ScratchLayout scratch_layout(int d, int k, int maxN, 
     const LocalDims M = local_dims(d, k, maxN, cond);
     const int nR = M.nR, nE = M.nE, nF = M.nF, nV = M.nV;
     const int ns = M.ns, nloc = M.nloc;
-    const int nel = d * nV + nE, nk = maxN * M.b + nE;  // bounds over the condensation variants
+    const int nel = d * nV + nE, nk = maxN * M.b + (d + 1) * nE;  // bounds over the condensation variants
     ScratchLayout L;
     int64_t o = 0;
     auto take = [&](int64_t n) {
@@ -1490,7 +1500,7 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
     D.nE = dimP(d, k);
     D.nF = dimP(d - 1, k);
     D.b = local_dims(d, k, 0, cond).b;
-    D.nP = (cond == HHO_HPCOND) ? 0 : (cond == HHO_VPCOND) ? 1 : D.nE;
+    D.nP = (cond == HHO_HPCOND) ? 0 : (cond == HHO_VPCOND) ? 1 : (cond == HHO_UNCOND) ? (d + 1) * D.nE : D.nE;
     // host topology (int32)
     D.h_ef_ptr.resize(D.ne + 1);
     D.h_ef.resize(m->elem_face_ptr[D.ne]);

@@ -324,11 +324,17 @@ __global__ void __launch_bounds__(RT) k_spmv_dot(LV<T> L, Items it, const T* __r
 
 // Row selection of the restriction d = I(bv - S x) (mode 2 of k_spmv_b): of a
 // fine face block (components of nFf unknowns each) the first nFc of every
-// component are kept, of a fine element pressure block the first nPc; d is
-// written in the coarse layout (face blocks of bc, then element blocks of nPc).
+// component are kept, of a fine element block (components of nEf unknowns:
+// one pressure prefix, or velocity and pressure when nothing is condensed) the
+// first nEc of every component; d is written in the coarse layout (face blocks
+// of bc, then element blocks of nPc).
 struct Restr {
-    int nFf, nFc, bc, nPc;
+    int nFf, nFc, bc, nPc, nEf, nEc;
 };
+__device__ __forceinline__ int restr_elem_row(const Restr& rs, int r) {  // coarse position of fine element row r, or -1
+    const int comp = r / rs.nEf, rr = r - comp * rs.nEf;
+    return rr < rs.nEc ? comp * rs.nEc + rr : -1;
+}
 
 // Same operator with the face block size B known at compile time: a thread
 // holds RF consecutive rows of one face (RF = B up to B = 12), the column loops
@@ -430,8 +436,9 @@ __global__ void __launch_bounds__(RT) k_spmv_b(LV<T> L, Items it, const T* __res
                 const int64_t o = nf * B + E * nP + r0 + i;
                 const T v = mode ? T(bv[o] - acc[i]) : acc[i];
                 if (mode == 2) {
-                    if (r0 + i < rs.nPc) {
-                        y[nf * rs.bc + E * rs.nPc + r0 + i] = v;
+                    const int rc = restr_elem_row(rs, r0 + i);
+                    if (rc >= 0) {
+                        y[nf * rs.bc + E * rs.nPc + rc] = v;
                         if (self) dacc[NVMAX] += (A)v * (A)v;
                     }
                 } else {
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(RT) k_spmv_b(LV<T> L, Items it, const T* __res
 // formed; optionally ||d||^2 with the START hook of the coarse smoother.
 template <int R, typename T>
 __global__ void __launch_bounds__(RT) k_residual_restrict(LV<T> L, Items it, int nFf, int bc, int nFc, int nPc,
-                                                           const T* __restrict__ x, const T* __restrict__ bv,
+                                                           int nEf, int nEc, const T* __restrict__ x, const T* __restrict__ bv,
                                                            T* __restrict__ d, int do_norm, double* __restrict__ partial,
                                                            unsigned* __restrict__ counter, double* __restrict__ out,
                                                            double* sc, GS gsl) {
@@ -472,7 +479,7 @@ __global__ void __launch_bounds__(RT) k_residual_restrict(LV<T> L, Items it, int
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int rc = g * R + i;
-            rows[i] = face ? (rc / nFc) * nFf + rc % nFc : rc;
+            rows[i] = face ? (rc / nFc) * nFf + rc % nFc : (rc / nEc) * nEf + rc % nEc;
             if (rc < nrow) nr = i + 1;
         }
         T acc[R];
@@ -737,8 +744,9 @@ __global__ void __launch_bounds__(RT, 4) k_spmv_v(LV<float> L, Items it, const f
                 const int64_t o = nf * B + E * NP + r;
                 const float v = mode ? bv[o] - acc[r] : acc[r];
                 if (mode == 2) {
-                    if (r < rs.nPc) {
-                        y[nf * rs.bc + E * rs.nPc + r] = v;
+                    const int rc = restr_elem_row(rs, r);
+                    if (rc >= 0) {
+                        y[nf * rs.bc + E * rs.nPc + rc] = v;
                         if (self) dacc[NVMAX] += v * v;
                     }
                 } else {
@@ -944,8 +952,9 @@ __global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t
                 const int64_t o = nf * B + E * NP + q;
                 const float v = mode ? bv[o] - acc[q] : acc[q];
                 if (mode == 2) {
-                    if (q < rs.nPc) {
-                        y[nf * rs.bc + E * rs.nPc + q] = v;
+                    const int rc = restr_elem_row(rs, q);
+                    if (rc >= 0) {
+                        y[nf * rs.bc + E * rs.nPc + rc] = v;
                         if (self) dacc[NVMAX] += v * v;
                     }
                 } else {
@@ -1185,8 +1194,8 @@ size_t xupd_smem(int m) { return (size_t)((m + 1) * m + m) * sizeof(double); }
 
 // x += zero-padded xc (prolongation)
 template <typename T>
-__global__ void k_prolong_add(int64_t nf, int64_t ne, int bf, int nFf, int nPf, int bc, int nFc, int nPc,
-                              const T* __restrict__ xc, T* __restrict__ x) {
+__global__ void k_prolong_add(int64_t nf, int64_t ne, int bf, int nFf, int nPf, int bc, int nFc, int nPc, int nEf,
+                              int nEc, const T* __restrict__ xc, T* __restrict__ x) {
     const int64_t nfr = nf * bc, ner = ne * nPc;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfr + ner; i += (int64_t)gridDim.x * blockDim.x) {
         if (i < nfr) {
@@ -1195,7 +1204,8 @@ __global__ void k_prolong_add(int64_t nf, int64_t ne, int bf, int nFf, int nPf, 
             x[F * bf + (rc / nFc) * nFf + rc % nFc] += xc[i];
         } else {
             const int64_t jj = i - nfr, E = jj / nPc;
-            x[nf * bf + E * nPf + (int)(jj % nPc)] += xc[i];
+            const int rc = (int)(jj % nPc);
+            x[nf * bf + E * nPf + (rc / nEc) * nEf + rc % nEc] += xc[i];
         }
     }
 }
@@ -1539,7 +1549,7 @@ static bool launch_jacobi_v(hho_ctx* ctx, const LevelMat& L, const float* w, con
 template <typename T>
 static bool launch_spmv_b(hho_ctx* ctx, const LevelMat& L, const T* x, const T* bv, T* y, int mode, const T* V,
                           int64_t ld, int nv, int self, double* partial, unsigned* counter, double* out, int hook,
-                          double* sc, GS gsl, int j, Restr rs = Restr{0, 0, 0, 0}) {
+                          double* sc, GS gsl, int j, Restr rs = Restr{0, 0, 0, 0, 1, 0}) {
     if constexpr (std::is_same<T, float>::value) {
         if (L.ilv) return launch_spmv_v(ctx, L, x, bv, y, mode, V, ld, nv, self, partial, counter, out, hook, sc, gsl,
                                         j, rs);
@@ -1744,8 +1754,10 @@ template <int R, typename T>
 static void restrict_R(hho_ctx* ctx, const LevelMat& F, const LevelMat& C, Items it, const T* x, const T* bv, T* d,
                        int do_norm, double* sc, GS G) {
     Workspace* W = ctx->ws;
-    k_residual_restrict<R, T><<<op_grid(ctx, it), RT, 0, ctx->stream>>>(view<T>(F), it, F.nF, C.b, C.nF, C.nP, x, bv,
-                                                                        d, do_norm, W->partial, W->counter, sc, sc, G);
+    const int ec = elem_comp(ctx->disc.cond, ctx->disc.d);
+    k_residual_restrict<R, T><<<op_grid(ctx, it), RT, 0, ctx->stream>>>(view<T>(F), it, F.nF, C.b, C.nF, C.nP,
+                                                                        F.nP / ec, C.nP / ec, x, bv, d, do_norm,
+                                                                        W->partial, W->counter, sc, sc, G);
 }
 
 template <typename T>
@@ -1784,7 +1796,8 @@ static hho_status vcycle_level(hho_ctx* ctx, int l, const T* bv, T* x, bool x_ze
     Items it = items_for(F, Rc, C.b, C.nP);
     GS Gc = gs_layout(std::max(ctx->smooth_its, 1));
     const int do_norm = (!coarse_next && ctx->smooth_its > 0) ? 1 : 0;
-    const Restr rs{F.nF, C.nF, C.b, C.nP};
+    const int ec = elem_comp(ctx->disc.cond, ctx->disc.d);
+    const Restr rs{F.nF, C.nF, C.b, C.nP, F.nP / ec, C.nP / ec};
     if (launch_spmv_b<T>(ctx, F, x, bv, cbv, 2, nullptr, 0, 0, do_norm, ctx->ws->partial, ctx->ws->counter, cw.sc,
                          do_norm ? HOOK_START : HOOK_NONE, cw.sc, Gc, 0, rs)) {
         // fused into the operator kernel specialised on the fine block size
@@ -1798,7 +1811,8 @@ static hho_status vcycle_level(hho_ctx* ctx, int l, const T* bv, T* x, bool x_ze
     HHO_CUDA(cudaGetLastError());
     if (coarse_next) HHO_TRY(coarse_level<T>(ctx, l + 1, cbv, cx));
     else HHO_TRY(vcycle_level<T>(ctx, l + 1, cbv, cx, true, do_norm != 0));
-    k_prolong_add<T><<<grid1d(C.n, 256), 256, 0, ctx->stream>>>(F.nf, F.ne, F.b, F.nF, F.nP, C.b, C.nF, C.nP, cx, x);
+    k_prolong_add<T><<<grid1d(C.n, 256), 256, 0, ctx->stream>>>(F.nf, F.ne, F.b, F.nF, F.nP, C.b, C.nF, C.nP,
+                                                                F.nP / ec, C.nP / ec, cx, x);
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());
     // the iterate after the coarse correction, for the learned smoother's training pairs
@@ -1866,7 +1880,7 @@ template <typename T>
 hho_status null_project(hho_ctx* ctx, const LevelMat& L, T* x) {
     if (!ctx->has_null) return HHO_OK;
     const bool hp = ctx->disc.cond == HHO_HPCOND;
-    T* xp = hp ? x + null_slot(ctx, L, 0) : x + L.nf * L.b;
+    T* xp = x + null_slot(ctx, L, 0);
     k_null_proj<T><<<ctx->probs.P, 512, 0, ctx->stream>>>(ctx->d_null_off, ctx->null_w, xp, hp ? L.b : L.nP);
     ++ctx->launches;
     HHO_CUDA(cudaGetLastError());

@@ -20,7 +20,7 @@ HHO_OK = 0
 STATUS = {0: "HHO_OK", 1: "HHO_ERR_ARG", 2: "HHO_ERR_MESH", 3: "HHO_ERR_CUDA", 4: "HHO_ERR_NOMEM",
           5: "HHO_ERR_SINGULAR", 6: "HHO_ERR_NOT_CONVERGED", 7: "HHO_ERR_TIMEOUT", 8: "HHO_ERR_STATE",
           9: "HHO_ERR_UNSUPPORTED"}
-COND = {"v": 0, "vp": 1, "hp": 2}
+COND = {"v": 0, "vp": 1, "hp": 2, "unc": 3}
 NODES = {"elem": 0, "face": 1}
 
 # every entry point declared in include/hho.h
