@@ -512,6 +512,7 @@ hho_status hho_destroy(hho_ctx* ctx) {
     dfree(ctx->null_vec0);
     dfree(ctx->null_w);
     dfree(ctx->d_null_off);
+    dfree(ctx->null_part);
     dfree(ctx->d_flag);
     delete ctx;
     return HHO_OK;

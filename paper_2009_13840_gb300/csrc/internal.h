@@ -166,6 +166,8 @@ struct hho_ctx {
     std::vector<double> h_null_w;        // host copy of null_w
     int64_t* d_null_off = nullptr;       // device copy of the slot ranges per problem (probs.elem_off, or
                                          // probs.face_off for HHO-hp)
+    int null_nch = 1;                    // chunks per problem of the projection kernels
+    double* null_part = nullptr;         // their partial products (problems x chunks)
     hho::BatchWork* batch = nullptr;
     int tile_rows = 2048;                // rows of the condensed vector per block in the segmented kernels
     hho::Learned* learned = nullptr;     // learned smoother network (or null)

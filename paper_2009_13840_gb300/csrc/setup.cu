@@ -42,6 +42,8 @@ namespace {
 constexpr int TPB = 128;     // threads per element CTA
 static_assert(TPB % 32 == 0, "element CTAs are whole warps (warp-shuffle reductions)");
 constexpr int TQ = 32;       // quadrature points per tile
+constexpr int RQ_E = 64;     // element points per tile of the right-hand-side kernel
+constexpr int RQ_F = 32;     // face points per tile of the right-hand-side kernel
 
 __device__ __forceinline__ double glx(const double* gl, int n, int i) { return gl[n * MAX_GL + i]; }
 __device__ __forceinline__ double glw(const double* gl, int n, int i) {
@@ -1112,6 +1114,7 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
                                              double* __restrict__ yT, double* __restrict__ scratch, int64_t scratch_per) {
     __shared__ ElemSh E;
     __shared__ double s_acc[3 * 36 + 3 * 10 + 36 + 10];
+    __shared__ double s_tile[RQ_F * 86 > RQ_E * 39 ? RQ_F * 86 : RQ_E * 39];
     __shared__ RecTab tab;
     rec_tab_fill(tab);
     const int nR = dimP(d, k + 1), nE = dimP(d, k), nF = dimP(d - 1, k);
@@ -1130,35 +1133,32 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
         const double* C = eC + t * nR * nR;
         const double* P = Pm + off_P[t];
         __syncthreads();
-        // body force: int f_c phi_j, j < nV (starting basis, then transform)
+        // body force: int f_c phi_j, j < nV (starting basis, then transform).
+        // Tiles of RQ_E points: one thread per point evaluates the starting
+        // functions into shared memory, then thread idx < d nV adds its
+        // product over the tile's points in order (one register accumulator
+        // per thread; every sum has a fixed order).
         {
-            __shared__ double red[TPB / 32][3 * 36];
             int nq = elem_npts(E, d, pd);
             int64_t o = enode_off[t];
-            double part[3 * 36];
-            for (int i = 0; i < d * nV; ++i) part[i] = 0.0;
-            for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-                double x[3] = {0, 0, 0}, w, val[36];
-                elem_point(E, d, gl, pd, q, x, &w);
-                elem_start_val(E, d, kv, x, val, tab);
-                for (int c = 0; c < d; ++c) {
-                    double wf = w * fdat[(o + q) * d + c];
-                    for (int a = 0; a < nV; ++a) part[c * nV + a] += wf * val[a];
+            double* s_v = s_tile;                  // [RQ_E][36]
+            double* s_wf = s_tile + RQ_E * 36;     // [RQ_E][3] weight times f_c
+            double acc = 0.0;
+            const int cI = threadIdx.x / (nV > 0 ? nV : 1), aI = threadIdx.x - cI * nV;
+            for (int q0 = 0; q0 < nq; q0 += RQ_E) {
+                const int nt = min(RQ_E, nq - q0);
+                if (threadIdx.x < nt) {
+                    double x[3] = {0, 0, 0}, w;
+                    elem_point(E, d, gl, pd, q0 + threadIdx.x, x, &w);
+                    elem_start_val(E, d, kv, x, s_v + threadIdx.x * 36, tab);
+                    for (int c = 0; c < d; ++c) s_wf[threadIdx.x * 3 + c] = w * fdat[(o + q0 + threadIdx.x) * d + c];
                 }
+                __syncthreads();
+                if (threadIdx.x < d * nV)
+                    for (int q = 0; q < nt; ++q) acc += s_wf[q * 3 + cI] * s_v[q * 36 + aI];
+                __syncthreads();
             }
-            // warp sums by shuffles (every lane of the CTA is here), then the
-            // TPB / 32 warp sums in warp order: no serial chain on one thread
-            for (int i = 0; i < d * nV; ++i) {
-                double v = part[i];
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i] = v;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < d * nV; i += blockDim.x) {
-                double tot = 0.0;
-                for (int w = 0; w < TPB / 32; ++w) tot += red[w][i];
-                s_acc[i] = tot;
-            }
+            if (threadIdx.x < d * nV) s_acc[threadIdx.x] = acc;
             __syncthreads();
             for (int idx = threadIdx.x; idx < d * nV; idx += blockDim.x) {
                 int c = idx / nV, j = idx % nV;
@@ -1179,26 +1179,66 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
             int64_t o = fnode_off[F];
             const double* gv = (bc == 1) ? gD : gN;
             // accumulators: for each c: sum w g_c dn phi~_m (nR), sum w g_c psi~_j (nF); sum w (g.n) phi~_i (nR);
-            // sum w (g.n) psi~_j (nF)
-            if (threadIdx.x == 0) {
-                for (int i = 0; i < 3 * 36 + 3 * 10 + 36 + 10; ++i) s_acc[i] = 0.0;
-                for (int q = 0; q < nqf; ++q) {
-                    double x[3] = {0, 0, 0}, w, val[36], grad[36 * 3], fval[10];
-                    face_point(d, E.V[f], E.nvf[f], E.xF[f], gl, pd, q, x, &w);
-                    elem_start(E, d, k + 1, x, val, grad);
-                    face_start(g, d, k, x, fval);
-                    double gn = 0.0;
-                    for (int c = 0; c < d; ++c) gn += gv[(o + q) * d + c] * E.nTF[f][c];
-                    for (int m = 0; m < nR; ++m) {
-                        double dn = 0.0;
-                        for (int c = 0; c < d; ++c) dn += grad[m * 3 + c] * E.nTF[f][c];
-                        for (int c = 0; c < d; ++c) s_acc[c * 36 + m] += w * gv[(o + q) * d + c] * dn;
-                        s_acc[3 * 36 + 3 * 10 + m] += w * gn * val[m];
+            // sum w (g.n) psi~_j (nF).  Tiles of RQ_F points as for the body force; accumulator slot sl of
+            // thread t is acc index t + sl TPB.
+            {
+                double* s_fv = s_tile;                 // [RQ_F][36] values
+                double* s_dn = s_tile + RQ_F * 36;     // [RQ_F][36] normal derivatives
+                double* s_ff = s_tile + RQ_F * 72;     // [RQ_F][10] face functions
+                double* s_gw = s_tile + RQ_F * 82;     // [RQ_F][4] w g_c, w (g . n)
+                const int n1 = d * nR, n2 = n1 + d * nF, n3 = n2 + nR, nacc = n3 + nF;
+                double accf[2] = {0.0, 0.0};
+                for (int q0 = 0; q0 < nqf; q0 += RQ_F) {
+                    const int nt = min(RQ_F, nqf - q0);
+                    if (threadIdx.x < nt) {
+                        const int q = q0 + threadIdx.x;
+                        double x[3] = {0, 0, 0}, w, grad[36 * 3];
+                        face_point(d, E.V[f], E.nvf[f], E.xF[f], gl, pd, q, x, &w);
+                        elem_start(E, d, k + 1, x, s_fv + threadIdx.x * 36, grad);
+                        face_start(g, d, k, x, s_ff + threadIdx.x * 10);
+                        for (int m = 0; m < nR; ++m) {
+                            double dn = 0.0;
+                            for (int c = 0; c < d; ++c) dn += grad[m * 3 + c] * E.nTF[f][c];
+                            s_dn[threadIdx.x * 36 + m] = dn;
+                        }
+                        double gn = 0.0;
+                        for (int c = 0; c < d; ++c) {
+                            gn += gv[(o + q) * d + c] * E.nTF[f][c];
+                            s_gw[threadIdx.x * 4 + c] = w * gv[(o + q) * d + c];
+                        }
+                        s_gw[threadIdx.x * 4 + 3] = w * gn;
                     }
-                    for (int j = 0; j < nF; ++j) {
-                        for (int c = 0; c < d; ++c) s_acc[3 * 36 + c * 10 + j] += w * gv[(o + q) * d + c] * fval[j];
-                        s_acc[3 * 36 + 3 * 10 + 36 + j] += w * gn * fval[j];
+                    __syncthreads();
+                    for (int sl = 0; sl < 2; ++sl) {
+                        const int i = threadIdx.x + sl * TPB;
+                        if (i >= nacc) continue;
+                        double sum = 0.0;
+                        if (i < n1) {
+                            const int c = i / nR, m = i % nR;
+                            for (int qq = 0; qq < nt; ++qq) sum += s_gw[qq * 4 + c] * s_dn[qq * 36 + m];
+                        } else if (i < n2) {
+                            const int c = (i - n1) / nF, j = (i - n1) % nF;
+                            for (int qq = 0; qq < nt; ++qq) sum += s_gw[qq * 4 + c] * s_ff[qq * 10 + j];
+                        } else if (i < n3) {
+                            const int m = i - n2;
+                            for (int qq = 0; qq < nt; ++qq) sum += s_gw[qq * 4 + 3] * s_fv[qq * 36 + m];
+                        } else {
+                            const int j = i - n3;
+                            for (int qq = 0; qq < nt; ++qq) sum += s_gw[qq * 4 + 3] * s_ff[qq * 10 + j];
+                        }
+                        accf[sl] += sum;
                     }
+                    __syncthreads();
+                }
+                for (int sl = 0; sl < 2; ++sl) {
+                    const int i = threadIdx.x + sl * TPB;
+                    if (i >= nacc) continue;
+                    int slot;
+                    if (i < n1) slot = (i / nR) * 36 + i % nR;
+                    else if (i < n2) slot = 3 * 36 + ((i - n1) / nF) * 10 + (i - n1) % nF;
+                    else if (i < n3) slot = 3 * 36 + 3 * 10 + (i - n2);
+                    else slot = 3 * 36 + 3 * 10 + 36 + (i - n3);
+                    s_acc[slot] = accf[sl];
                 }
             }
             __syncthreads();

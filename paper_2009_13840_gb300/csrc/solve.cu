@@ -774,6 +774,11 @@ constexpr int wv_rl(int B) { return B / wv_vw(B); }
 constexpr int wv_gc(int B) { return 32 / wv_rl(B); }
 constexpr int wv_nk(int B) { return (B + wv_gc(B) - 1) / wv_gc(B); }
 constexpr int wv_xr(int B) { return (B + 31) / 32; }  // registers per lane holding a column block of x
+// resident blocks of 256 threads per SM the operator kernel is compiled for
+// (the largest count without register spills): 4 (64 registers a thread) for
+// the blocks of 18 and 24 unknowns, 3 for 30 with one pressure per element, 2
+// for 30 with element pressure blocks and for 40
+constexpr int wv_minb(int B, int NP) { return (B == 18 || B == 24) ? 4 : (B == 30 && NP <= 1) ? 3 : 2; }
 static_assert(wv_rl(30) == 15 && wv_gc(30) == 2 && wv_rl(18) == 9 && wv_gc(18) == 3 && wv_rl(9) == 9 &&
                   wv_gc(9) == 3 && wv_nk(30) * wv_gc(30) == 30 && wv_nk(18) * wv_gc(18) == 18 &&
                   wv_rl(40) == 10 && wv_gc(40) == 3 && wv_nk(40) == 14 && wv_rl(24) == 6 && wv_gc(24) == 5 &&
@@ -831,7 +836,8 @@ __device__ __forceinline__ void wv_group_sum(float (&acc)[VW], int rr) {
 // block is read as NK wide coalesced loads per slot.  Element rows stay one
 // thread per element (their values are contiguous across elements).
 template <int B, int NP>
-__global__ void __launch_bounds__(RT) k_spmv_w(LV<float> L, int64_t nfw, int64_t etiles, const float* __restrict__ x,
+__global__ void __launch_bounds__(RT, wv_minb(B, NP)) k_spmv_w(LV<float> L, int64_t nfw, int64_t etiles,
+                                                          const float* __restrict__ x,
                                              const float* __restrict__ bv, float* __restrict__ y, int mode,
                                              const float* __restrict__ V, int64_t ld, int nv, int self,
                                              double* __restrict__ partial, unsigned* __restrict__ counter,
@@ -1222,28 +1228,50 @@ __global__ void k_zero(int64_t n, T* __restrict__ dst) {
         dst[i] = T(0);
 }
 
-// x -= (n_p . x) n_p for every problem p (one block each): n_p is non-zero
-// only on one unknown per kernel slot E (the first pressure unknown of an
-// element, or the constant face-pressure coefficient of a face for HHO-hp),
-// xp[E * stride], with weight w[E] (0 throughout for a problem without
-// pressure kernel).  Fixed-order tree.
+// x -= (n_p . x) n_p for every problem p: n_p is non-zero only on one unknown
+// per kernel slot E (the first pressure unknown of an element, or the
+// constant face-pressure coefficient of a face for HHO-hp), xp[E * stride],
+// with weight w[E] (0 throughout for a problem without pressure kernel).
+// Problem p's slots are split into nch chunks of NP_CHUNK; block (p, c) of
+// k_null_dot writes the chunk's partial product, block (p, c) of k_null_sub
+// adds the nch partials of p in chunk order (fixed-order trees: deterministic)
+// and updates its chunk.
+constexpr int NP_CHUNK = 2048;
+
 template <typename T>
-__global__ void __launch_bounds__(512) k_null_proj(const int64_t* __restrict__ slot_off,
-                                                   const double* __restrict__ w, T* __restrict__ xp, int stride) {
+__global__ void __launch_bounds__(512) k_null_dot(const int64_t* __restrict__ slot_off, int nch,
+                                                  const double* __restrict__ w, const T* __restrict__ xp, int stride,
+                                                  double* __restrict__ part) {
     __shared__ double sm[512];
-    const int64_t e0 = slot_off[blockIdx.x], e1 = slot_off[blockIdx.x + 1];
-    const int nP = stride;
+    const int p = blockIdx.x / nch, c = blockIdx.x % nch;
+    const int64_t e0 = slot_off[p] + (int64_t)c * NP_CHUNK, e1 = min(slot_off[p + 1], e0 + NP_CHUNK);
     double s = 0.0;
-    for (int64_t E = e0 + threadIdx.x; E < e1; E += blockDim.x) s += w[E] * (double)xp[E * nP];
+    for (int64_t E = e0 + threadIdx.x; E < e1; E += blockDim.x) s += w[E] * (double)xp[E * stride];
     sm[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
         __syncthreads();
     }
-    const double a = sm[0];
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_null_sub(const int64_t* __restrict__ slot_off, int nch,
+                                                  const double* __restrict__ w, T* __restrict__ xp, int stride,
+                                                  const double* __restrict__ part) {
+    __shared__ double s_a;
+    const int p = blockIdx.x / nch, c = blockIdx.x % nch;
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int q = 0; q < nch; ++q) a += part[p * nch + q];
+        s_a = a;
+    }
+    __syncthreads();
+    const double a = s_a;
     if (a == 0.0) return;
-    for (int64_t E = e0 + threadIdx.x; E < e1; E += blockDim.x) xp[E * nP] = T((double)xp[E * nP] - a * w[E]);
+    const int64_t e0 = slot_off[p] + (int64_t)c * NP_CHUNK, e1 = min(slot_off[p + 1], e0 + NP_CHUNK);
+    for (int64_t E = e0 + threadIdx.x; E < e1; E += blockDim.x) xp[E * stride] = T((double)xp[E * stride] - a * w[E]);
 }
 
 int rows_per_thread(int nrow) {
@@ -1881,8 +1909,11 @@ hho_status null_project(hho_ctx* ctx, const LevelMat& L, T* x) {
     if (!ctx->has_null) return HHO_OK;
     const bool hp = ctx->disc.cond == HHO_HPCOND;
     T* xp = x + null_slot(ctx, L, 0);
-    k_null_proj<T><<<ctx->probs.P, 512, 0, ctx->stream>>>(ctx->d_null_off, ctx->null_w, xp, hp ? L.b : L.nP);
-    ++ctx->launches;
+    const int stride = hp ? L.b : L.nP, nch = ctx->null_nch;
+    const unsigned g = (unsigned)(ctx->probs.P * nch);
+    k_null_dot<T><<<g, 512, 0, ctx->stream>>>(ctx->d_null_off, nch, ctx->null_w, xp, stride, ctx->null_part);
+    k_null_sub<T><<<g, 512, 0, ctx->stream>>>(ctx->d_null_off, nch, ctx->null_w, xp, stride, ctx->null_part);
+    ctx->launches += 2;
     HHO_CUDA(cudaGetLastError());
     return HHO_OK;
 }
@@ -1912,6 +1943,8 @@ hho_status null_build(hho_ctx* ctx) {
     ctx->null_w = nullptr;
     dfree(ctx->d_null_off);
     ctx->d_null_off = nullptr;
+    dfree(ctx->null_part);
+    ctx->null_part = nullptr;
     ctx->h_null_w.clear();
     if (!ctx->has_null) return HHO_OK;
     const bool hp = D.cond == HHO_HPCOND;
@@ -1937,6 +1970,10 @@ hho_status null_build(hho_ctx* ctx) {
     HHO_CUDA(cudaMemcpy(ctx->null_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
     HHO_TRY(dalloc(ctx, &ctx->d_null_off, off.size()));
     HHO_CUDA(cudaMemcpy(ctx->d_null_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    int64_t most = 1;
+    for (int p = 0; p < pr.P; ++p) most = std::max<int64_t>(most, off[p + 1] - off[p]);
+    ctx->null_nch = (int)((most + NP_CHUNK - 1) / NP_CHUNK);
+    HHO_TRY(dalloc(ctx, &ctx->null_part, (size_t)pr.P * ctx->null_nch));
     return HHO_OK;
 }
 

@@ -19,6 +19,8 @@ Sec. 4.1.2), so it recomputes them on the submesh around sampled faces
   random subset).  The rows of one face are not compared with the right-hand
   side on the same rows alone: boundary rows carry the Nitsche terms and
   dominate ||b||, so interior rows have a much smaller right-hand side.
+The cases cover Scheme 1 (v-cond, v&p-cond), Scheme 2 (HHO-hp) and the
+uncondensed formulation.
 """
 import numpy as np
 import pytest
@@ -27,6 +29,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle.hho import HHO  # noqa: E402
+from oracle.hho_hp import HHOhp  # noqa: E402
 from oracle.sampled import _submesh, residual_rows, sample_interior_faces  # noqa: E402
 from synthetic import tri_mesh, hex_mesh, fields  # noqa: E402
 from parity_util import report  # noqa: E402
@@ -48,6 +51,12 @@ CASES = [
      "vp", True),
     ("hex16-dir-k3-vp", lambda: hex_mesh(16, jitter=0.15, seed=0), fields.CurlStokes3D(), 3, "vp", True),
     ("hex32-dir-k3-vp", lambda: hex_mesh(32, jitter=0.15, seed=0), fields.CurlStokes3D(), 3, "vp", False),
+    # HHO-hp (Scheme 2) and the uncondensed formulation (block ILU(0) smoother) at the sizes of their workloads
+    ("hex16-dir-k3-hp", lambda: hex_mesh(16, jitter=0.15, seed=0), fields.CurlStokes3D(), 3, "hp", True),
+    ("tri128-mixed-k3-hp", lambda: tri_mesh(128, jitter=0.2, seed=0, neumann_sides=(1,)), fields.TrigStokes2D(), 3,
+     "hp", False),
+    ("tri128-mixed-k3-unc", lambda: tri_mesh(128, jitter=0.2, seed=0, neumann_sides=(1,)), fields.TrigStokes2D(), 3,
+     "unc", True),
 ]
 
 
@@ -66,7 +75,7 @@ def test_sampled_elements_rhs_and_residual(hho_mod, name, mk, fld, k, cond, schu
         S = ctx.element_schur()
         elems = np.unique([int(t) for F in faces for t in mesh.face_elem[F] if t >= 0])
         sub, el, _ = _submesh(mesh, elems)
-        h = HHO(sub, k, cond)
+        h = HHOhp(sub, k) if cond == "hp" else HHO(sub, k, cond)
         nk = np.array([len(mesh.faces_of(int(t))) * h.b + h.nP for t in range(mesh.n_elem)])
         off = np.concatenate([[0], np.cumsum(nk * nk)])
         worst, where = 0.0, None
@@ -77,6 +86,8 @@ def test_sampled_elements_rhs_and_residual(hho_mod, name, mk, fld, k, cond, schu
                 worst, where = e, int(t)
         report(f"fullsize-schur {name}", max_rel=worst, worst_elem=where, elems=len(el))
         assert worst < 1e-11, (worst, where)
+    if cond == "unc":
+        ctx.set_option("smoother", 1)  # block Jacobi does not smooth the uncondensed system
     ctx.pmg_setup(list(range(k, -1, -1)), prec="fp32")
     x = torch.empty(ctx.ndof(0), dtype=torch.float64, device="cuda")
     info = ctx.solve(x, rtol=1e-8, maxit=2000)
