@@ -41,6 +41,8 @@ from .basis import dim_P
 def n_comp(d, cond):
     """Components of a face block: d velocity components, plus the face
     pressure for HHO-hp (Scheme 2)."""
+    if cond == "dg":  # the DG scheme has element unknowns only
+        return 0
     return d + 1 if cond == "hp" else d
 
 
@@ -51,7 +53,7 @@ def n_pres(d, k_l, cond):
     nothing is condensed."""
     if cond == "hp":
         return 0
-    if cond == "unc":
+    if cond in ("unc", "dg"):
         return (d + 1) * dim_P(d, k_l)
     return 1 if cond == "vp" else dim_P(d, k_l)
 
@@ -60,12 +62,12 @@ def e_comp(d, cond):
     """Components of an element block, each truncated on its own: d + 1
     (velocity and pressure) when nothing is condensed, else 1 (the kept
     pressure coefficients form one prefix)."""
-    return d + 1 if cond == "unc" else 1
+    return d + 1 if cond in ("unc", "dg") else 1
 
 
 def mean_offset(d, k_l, cond):
     """Position of the constant pressure mode in an element block."""
-    return d * dim_P(d, k_l) if cond == "unc" else 0
+    return d * dim_P(d, k_l) if cond in ("unc", "dg") else 0
 
 
 class Level:
