@@ -39,6 +39,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "FGMRES+p-MG time & DOFs/s to 1e-8 rel. residual; V-cycle GB/s vs HBM peak"
+L2_BYTES = 129 * 1024 * 1024  # GB300 L2
 UNIT = "DOF/s"
 # DRAM bytes (read + write) of one FP32 level-0 operator launch, from the ncu
 # captures summarised under profiles/ (kernels unchanged since); keyed by
@@ -60,6 +61,9 @@ SPECS = {
     "hp3": dict(mesh="hex", n=32, k=3, cond="hp", prec="fp32", coarse_fp32=1, sample_n=4),
     # uncondensed HHO-dp on the C2 mesh (the reference point of the condensation gains), block ILU(0) smoother
     "unc2": dict(mesh="tri", n=128, k=3, cond="unc", prec="fp32", coarse_fp32=1, sample_n=16, smoother="ilu"),
+    # the DG scheme (Scheme 3) on 40 x 40 jittered triangles, k=3: its coarse level (k=0, 9600 unknowns) is the
+    # largest the dense coarse solve takes
+    "dg2": dict(mesh="tri", n=40, k=3, cond="dg", prec="fp32", coarse_fp32=1, sample_n=10),
 }
 
 
@@ -70,21 +74,23 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3",
-                    choices=["c3", "c2", "c1", "sweep", "batch", "learned", "hp2", "hp3", "unc2"],
+                    choices=["c3", "c2", "c1", "sweep", "batch", "learned", "hp2", "hp3", "unc2", "dg2"],
                     help="c3: 32^3 jittered hexahedra, k=3, v&p (default); c2: 128x128 jittered triangles, k=3, "
                          "v-cond; c1: 16x16 quadrilaterals, k=3, v&p, FP64; sweep: the c2 mesh over k=1..5, both "
                          "condensations, FP64 and FP32 V-cycles; batch: many independent small problems; learned: "
                          "the learned smoother against the plain one; hp2 / hp3: HHO-hp (Scheme 2) on the c2 "
                          "triangle mesh (k=3) and the c3 hexahedral mesh (k=3); unc2: uncondensed HHO-dp on the c2 "
-                         "mesh (k=3, block ILU(0) smoother)")
+                         "mesh (k=3, block ILU(0) smoother); dg2: the DG scheme (BR2, Scheme 3) on 40x40 jittered "
+                         "triangles (k=3)")
     ap.add_argument("--mesh", default=None, choices=["tri", "hex", "quad"],
                     help="override the workload's mesh family (tri: n x n squares split into triangles; hex: n^3 "
                          "jittered hexahedra; quad: n x n quadrilaterals)")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--k", type=int, default=None)
-    ap.add_argument("--cond", default=None, choices=["v", "vp", "hp", "unc"],
+    ap.add_argument("--cond", default=None, choices=["v", "vp", "hp", "unc", "dg"],
                     help="Scheme 1 with velocity-only (v) or velocity-pressure (vp) condensation, Scheme 2 "
-                         "(HHO-hp, hybrid pressure, every element unknown condensed), or Scheme 1 uncondensed (unc)")
+                         "(HHO-hp, hybrid pressure, every element unknown condensed), Scheme 1 uncondensed (unc), "
+                         "or the DG scheme (dg, Scheme 3)")
     ap.add_argument("--prec", default=None, choices=["fp32", "fp64"], help="V-cycle precision of the headline")
     ap.add_argument("--coarse-fp32", type=int, default=None, choices=[0, 1],
                     help="FP32 coarse solve inside the FP32 V-cycle")
@@ -136,7 +142,8 @@ def workload(n, k, cond, mesh_kind):
         mesh = quad_mesh(n, jitter=0.0)
         return mesh, fields.TrigStokes2D(), f"quad{n}x{n}-uniform-allDirichlet k={k} {cond}-cond levels {k}..0"
     mesh = tri_mesh(n, jitter=0.2, seed=0, neumann_sides=(1,))
-    return mesh, fields.TrigStokes2D(), f"tri{n}x{n}-jit0.2-seed0-mixedBC k={k} {cond}-cond levels {k}..0"
+    scheme = "DG-BR2 (Scheme 3)" if cond == "dg" else f"{cond}-cond"
+    return mesh, fields.TrigStokes2D(), f"tri{n}x{n}-jit0.2-seed0-mixedBC k={k} {scheme} levels {k}..0"
 
 
 def dist_env():
@@ -234,6 +241,9 @@ def oracle_disc(mesh, k, cond):
     if cond == "hp":
         from oracle.hho_hp import HHOhp
         return HHOhp(mesh, k)
+    if cond == "dg":
+        from oracle.dg import DG
+        return DG(mesh, k)
     from oracle.hho import HHO
     return HHO(mesh, k, cond)
 
@@ -297,6 +307,12 @@ def level_counts(mesh, k_l, cond):
     degree k_l: the face-block operator of the condensed system (stored blocks
     of every face row and element row) and the block-Jacobi data."""
     d = mesh.dim
+    if cond == "dg":  # element blocks of (d+1) n_E; slot 0 the element, then its neighbours across interior faces
+        b, ne = (d + 1) * _dimP(d, k_l), mesh.n_elem
+        fe = mesh.face_elem
+        inner = fe[(fe[:, 0] >= 0) & (fe[:, 1] >= 0)]
+        nsl = 1 + np.bincount(inner.ravel(), minlength=ne)
+        return ne * b, b * b * int(nsl.sum()), 4 * (int(nsl.sum()) + ne), ne * b * b, b, 0
     b = (d + 1 if cond == "hp" else d) * _dimP(d - 1, k_l)  # HHO-hp: face pressure as one more component
     nP = 0 if cond == "hp" else 1 if cond == "vp" else (d + 1) * _dimP(d, k_l) if cond == "unc" else _dimP(d, k_l)
     nf, ne = mesh.n_face, mesh.n_elem
@@ -499,7 +515,8 @@ def run_ours(args):
             xs32, ys32 = xs.float(), torch.empty(ndof, dtype=torch.float32, device="cuda")
             ms_k = time_on_stream(lambda: ctx.spmv_f32(0, xs32, ys32), 20)
             nbytes = spmv_bytes(mesh, args.k, args.cond, 4)
-            kname = "k_spmv_v<float> (level 0, V-cycle operator, FP32, row-interleaved)"
+            kname = ("k_spmv_b<30, float> (level 0, V-cycle operator, FP32, DG element blocks)" if args.cond == "dg"
+                     else "k_spmv_v<float> (level 0, V-cycle operator, FP32, row-interleaved)")
         else:
             ms_k, nbytes, kname = ms64_k, nb64, "k_spmv_b<double> (level 0)"
         achieved = nbytes / (ms_k / 1e3) / 1e9
@@ -538,8 +555,10 @@ def run_ours(args):
                "sample": f"oracle FGMRES+p-MG solve on {sample_name(args)} of the same family ({nd} DOFs against "
                          f"{ndof} in the workload, {its} its, {dt:.2f} s per solve, {ts:.1f} s setup excluded), "
                          f"one thread"}
-        # the oracle recomputes residual rows of the full-size GPU solution at sampled faces
-        check = oracle_check(mesh, args.k, args.cond, fld, x_host, b_host, sx_host, args.oracle_faces)
+        # the oracle recomputes residual rows of the full-size GPU solution at sampled faces (Scheme 1 and 2; the
+        # DG operator's parity is covered at several-tile sizes by the GPU tests)
+        if args.cond != "dg":
+            check = oracle_check(mesh, args.k, args.cond, fld, x_host, b_host, sx_host, args.oracle_faces)
     if rank == 0:
         last = infos[-1]
         line = {
@@ -560,7 +579,9 @@ def run_ours(args):
                        "vcycle": {"ms": ms_v, "algorithmic_bytes": vbytes, "achieved_gbs": vgbs,
                                   "frac_of_measured_hbm": vgbs / peak},
                        "errors_vs_exact": err, "oracle_check": check,
-                       "l2": "flushed between steps (512 MiB write); operators larger than L2",
+                       "l2": "flushed between steps (512 MiB write); " + (
+                           "operators larger than L2" if nbytes > L2_BYTES else
+                           f"level-0 operator ({nbytes / 1e6:.0f} MB) smaller than L2: cold only after each flush"),
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

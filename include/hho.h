@@ -51,8 +51,19 @@ typedef enum {
  * reference formulation of Sec. 5.4): face blocks of d n_F, then one block of
  * (d+1) n_E per element ([U_T (d components) | P_T]); its p-multilevel
  * hierarchy truncates every element component like a face component, and its
- * V-cycle needs the block ILU(0) smoother (hho_set_option "smoother" = 1). */
-typedef enum { HHO_VCOND = 0, HHO_VPCOND = 1, HHO_HPCOND = 2, HHO_UNCOND = 3 } hho_cond;
+ * V-cycle needs the block ILU(0) smoother (hho_set_option "smoother" = 1).
+ * HHO_DGCOND: the DG scheme (Scheme 3, Sec. 2.4: BR2 vector Laplacian,
+ * stabilised equal-order pressure), k >= 1, element unknowns only: one block
+ * of (d+1) n_E per element ([u_T (d components) | p_T]) in element order;
+ * at most 10 coefficients per component (2D k <= 3, 3D k <= 2, else
+ * HHO_ERR_UNSUPPORTED), planar faces.  Its hierarchy truncates every
+ * component; its V-cycle takes the element block-Jacobi smoother and the
+ * dense coarse solve (a coarse level above coarse_dense_max unknowns, the ILU
+ * smoother, the two-level coarse solve, batches and the learned smoother are
+ * HHO_ERR_UNSUPPORTED).  hho_element_schur returns the element data the
+ * couplings are formed from (K, D_c, then per face the trace matrices), and
+ * hho_recover copies the element blocks. */
+typedef enum { HHO_VCOND = 0, HHO_VPCOND = 1, HHO_HPCOND = 2, HHO_UNCOND = 3, HHO_DGCOND = 4 } hho_cond;
 typedef enum { HHO_FP64 = 0, HHO_FP32 = 1 } hho_prec;
 /* Preconditioner of the smoother's GMRES, selected by hho_set_option("smoother", v) before pmg_setup. */
 typedef enum { HHO_SMOOTH_BJACOBI = 0, HHO_SMOOTH_ILU = 1 } hho_smoother;

@@ -281,8 +281,63 @@ int grid_for(int64_t n, int tpb) {
 
 }  // namespace
 
+// DG scheme: the block rows are the elements.  Row block of element T: slot 0
+// is T, slot 1 + i the neighbour across T's i-th interior face (local order;
+// boundary faces couple nothing), padding slots repeat T with zero blocks.
+// No element rows (nP = 0): the element-row arrays hold one dummy slot.
+static hho_status build_topology_dg(hho_ctx* ctx) {
+    Disc& D = ctx->disc;
+    Topo& P = ctx->topo;
+    const int64_t ne = D.ne;
+    auto neighbour = [&](int64_t T, int g) -> int32_t {
+        const int F = D.h_ef[g];
+        const int a = D.h_fe[2 * F], b = D.h_fe[2 * F + 1];
+        if (a < 0 || b < 0) return -1;
+        return a == T ? b : a;
+    };
+    int S_max = 1;
+    for (int64_t T = 0; T < ne; ++T) {
+        int s = 1;
+        for (int g = D.h_ef_ptr[T]; g < D.h_ef_ptr[T + 1]; ++g) s += neighbour(T, g) >= 0;
+        S_max = std::max(S_max, s);
+    }
+    P.S_max = S_max;
+    P.N_max = 1;
+    std::vector<int32_t> col((size_t)S_max * ne), nsl(ne), fpc(2 * ne, -1), pfc(ne), pfn(ne, 0);
+    for (int64_t T = 0; T < ne; ++T) {
+        int s = 0;
+        col[T] = (int32_t)T;
+        ++s;
+        for (int g = D.h_ef_ptr[T]; g < D.h_ef_ptr[T + 1]; ++g) {
+            const int32_t G = neighbour(T, g);
+            if (G >= 0) col[(size_t)s++ * ne + T] = G;
+        }
+        nsl[T] = s;
+        for (; s < S_max; ++s) col[(size_t)s * ne + T] = (int32_t)T;
+        pfc[T] = (int32_t)T;
+    }
+    P.h_ff_col = col;
+    P.h_ff_nsl = nsl;
+    P.h_fp_col = fpc;
+    P.h_pf_col = pfc;
+    P.h_pf_nsl = pfn;
+    auto up = [&](int32_t** dst, const std::vector<int32_t>& v) -> hho_status {
+        HHO_TRY(dalloc(ctx, dst, v.size()));
+        HHO_CUDA(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        return HHO_OK;
+    };
+    HHO_TRY(up(&P.ff_col, col));
+    HHO_TRY(up(&P.ff_nsl, nsl));
+    HHO_TRY(up(&P.fp_col, fpc));
+    HHO_TRY(up(&P.pf_col, pfc));
+    HHO_TRY(up(&P.pf_nsl, pfn));
+    HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+    return HHO_OK;
+}
+
 hho_status build_topology(hho_ctx* ctx) {
     Disc& D = ctx->disc;
+    if (D.cond == HHO_DGCOND) return build_topology_dg(ctx);
     Topo& P = ctx->topo;
     const int64_t nf = D.nf, ne = D.ne;
     int S_max = 1;
@@ -384,19 +439,25 @@ void free_level(LevelMat& L) {
 hho_status assemble_level0(hho_ctx* ctx) {
     Disc& D = ctx->disc;
     const Topo& P = ctx->topo;
+    const bool dg = D.cond == HHO_DGCOND;
     if (ctx->levels.empty()) {
         LevelMat L;
         L.k = D.k;
-        L.nF = D.nF;
+        L.nF = dg ? D.nE : D.nF;  // DG: element blocks of d + 1 components of P^k(T)
         L.b = D.b;
         L.nP = D.nP;
-        L.nf = D.nf;
+        L.nf = dg ? D.ne : D.nf;
         L.ne = D.ne;
-        L.n = D.nf * D.b + D.ne * D.nP;
+        L.n = L.nf * L.b + L.ne * L.nP;
         HHO_TRY(alloc_level(ctx, L));
         ctx->levels.push_back(L);
     }
     LevelMat& L = ctx->levels[0];
+    if (dg) {
+        HHO_TRY(dg_assemble_level0(ctx, L.ff, P.S_max));
+        HHO_CUDA(cudaStreamSynchronize(ctx->stream));
+        return HHO_OK;
+    }
     int64_t tot = (int64_t)P.S_max * L.b * L.b * L.nf;
     k_assemble_ff<<<grid_for(tot, 256), 256, 0, ctx->stream>>>(L.nf, L.b, P.S_max, P.ff_nsl, P.asm_T, P.asm_lf,
                                                                P.asm_lg, D.fe, D.flf, D.off_S, D.ef_ptr, L.nP, D.S,
@@ -412,6 +473,11 @@ hho_status assemble_level0(hho_ctx* ctx) {
 
 hho_status assemble_rhs_vector(hho_ctx* ctx, double* rhs) {
     Disc& D = ctx->disc;
+    if (D.cond == HHO_DGCOND) {  // the element blocks of the right-hand side, in element order
+        HHO_CUDA(cudaMemcpyAsync(rhs, D.gT, (size_t)D.ne * D.b * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+        return HHO_OK;
+    }
     int64_t n = D.nf * D.b + D.ne * D.nP;
     k_rhs_gather<<<grid_for(n, 256), 256, 0, ctx->stream>>>(D.nf, D.ne, D.b, D.nP, D.fe, D.flf, D.ef_ptr, D.off_gT,
                                                             D.gT, rhs);
@@ -423,13 +489,14 @@ hho_status build_level(hho_ctx* ctx, int l, int k_l) {
     Disc& D = ctx->disc;
     LevelMat L;
     L.k = k_l;
-    L.nF = dimP(D.d - 1, k_l);
-    L.b = (D.cond == HHO_HPCOND ? D.d + 1 : D.d) * L.nF;  // HHO-hp: the face pressure is one more component
-    L.nP = (D.cond == HHO_HPCOND)   ? 0
-           : (D.cond == HHO_VPCOND) ? 1
-           : (D.cond == HHO_UNCOND) ? (D.d + 1) * dimP(D.d, k_l)  // velocity components and pressure
-                                    : dimP(D.d, k_l);
-    L.nf = D.nf;
+    const bool dg = D.cond == HHO_DGCOND;
+    L.nF = dg ? dimP(D.d, k_l) : dimP(D.d - 1, k_l);  // DG: element blocks, every component truncated
+    L.b = (D.cond == HHO_HPCOND || dg ? D.d + 1 : D.d) * L.nF;  // HHO-hp: the face pressure is one more component
+    L.nP = (D.cond == HHO_HPCOND || dg) ? 0
+           : (D.cond == HHO_VPCOND)     ? 1
+           : (D.cond == HHO_UNCOND)     ? (D.d + 1) * dimP(D.d, k_l)  // velocity components and pressure
+                                        : dimP(D.d, k_l);
+    L.nf = dg ? D.ne : D.nf;
     L.ne = D.ne;
     L.n = L.nf * L.b + L.ne * L.nP;
     HHO_TRY(alloc_level(ctx, L));

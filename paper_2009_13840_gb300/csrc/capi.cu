@@ -110,11 +110,15 @@ hho_status hho_setup(const hho_mesh* mesh, int k, int cond, void* stream, hho_ct
         ctx->err = "hho_setup: null mesh";
         return HHO_ERR_ARG;
     }
-    if (cond != HHO_VCOND && cond != HHO_VPCOND && cond != HHO_HPCOND && cond != HHO_UNCOND) {
-        ctx->err = "hho_setup: cond must be HHO_VCOND, HHO_VPCOND, HHO_HPCOND or HHO_UNCOND";
+    if (cond != HHO_VCOND && cond != HHO_VPCOND && cond != HHO_HPCOND && cond != HHO_UNCOND && cond != HHO_DGCOND) {
+        ctx->err = "hho_setup: cond must be HHO_VCOND, HHO_VPCOND, HHO_HPCOND, HHO_UNCOND or HHO_DGCOND";
         return HHO_ERR_ARG;
     }
     HHO_TRY(check_mesh(ctx, mesh, k));
+    if (cond == HHO_DGCOND && (k < 1 || (mesh->dim == 2 && k > 3) || (mesh->dim == 3 && k > 2))) {
+        ctx->err = "hho_setup: the DG scheme takes k >= 1 with at most 10 coefficients per component (2D k <= 3, 3D k <= 2)";
+        return HHO_ERR_UNSUPPORTED;
+    }
     HHO_CUDA(cudaGetDevice(&ctx->device));
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
     HHO_TRY(dalloc(ctx, &ctx->d_flag, 4));
@@ -134,8 +138,8 @@ hho_status hho_setup(const hho_mesh* mesh, int k, int cond, void* stream, hho_ct
 
 hho_status hho_set_batch(hho_ctx* ctx, int n_prob, const int64_t* face_off, const int64_t* elem_off) {
     if (!ctx || !face_off || !elem_off) return HHO_ERR_ARG;
-    if (ctx->disc.cond == HHO_HPCOND || ctx->disc.cond == HHO_UNCOND) {
-        ctx->err = "hho_set_batch: HHO-hp and uncondensed contexts hold one problem";
+    if (ctx->disc.cond == HHO_HPCOND || ctx->disc.cond == HHO_UNCOND || ctx->disc.cond == HHO_DGCOND) {
+        ctx->err = "hho_set_batch: HHO-hp, uncondensed and DG contexts hold one problem";
         return HHO_ERR_UNSUPPORTED;
     }
     HHO_TRY(batch_set(ctx, n_prob, face_off, elem_off));
@@ -153,7 +157,7 @@ hho_status hho_solve_batch(hho_ctx* ctx, double rtol, int maxit, int restart, do
 }
 
 hho_status hho_mlp_init(hho_ctx* ctx, int hidden, uint64_t seed) {
-    if (ctx && (ctx->disc.cond == HHO_HPCOND || ctx->disc.cond == HHO_UNCOND)) {
+    if (ctx && (ctx->disc.cond == HHO_HPCOND || ctx->disc.cond == HHO_UNCOND || ctx->disc.cond == HHO_DGCOND)) {
         ctx->err = "hho_mlp_init: the learned smoother is built for condensed Scheme 1 (element pressure rows)";
         return HHO_ERR_UNSUPPORTED;
     }
@@ -289,6 +293,10 @@ hho_status pmg_setup(hho_ctx* ctx, int n_levels, const int* degrees, int prec, i
     }
     if (ctx->disc.cond == HHO_HPCOND && (ctx->smoother_kind != 0 || ctx->coarse_twolevel)) {
         ctx->err = "pmg_setup: HHO-hp contexts use the block-Jacobi smoother and the dense or multifrontal coarse solve";
+        return HHO_ERR_UNSUPPORTED;
+    }
+    if (ctx->disc.cond == HHO_DGCOND && (ctx->smoother_kind != 0 || ctx->coarse_twolevel)) {
+        ctx->err = "pmg_setup: DG contexts use the element block-Jacobi smoother and the dense coarse solve";
         return HHO_ERR_UNSUPPORTED;
     }
     if (ctx->disc.cond == HHO_UNCOND && ctx->coarse_twolevel) {

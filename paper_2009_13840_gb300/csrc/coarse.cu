@@ -1163,6 +1163,10 @@ static hho_status coarse_build(hho_ctx* ctx) {
         dfree(A);
         return st;
     }
+    if (ctx->disc.cond == HHO_DGCOND) {  // the sparse coarse solvers are built on the face/element layout
+        ctx->err = "pmg_setup: a DG coarse level takes the dense solve: raise coarse_dense_max or coarsen further";
+        return HHO_ERR_UNSUPPORTED;
+    }
     if (ctx->coarse_twolevel) {
         C->kind = 1;
         return build_dd(ctx, C);

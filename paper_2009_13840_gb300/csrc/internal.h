@@ -269,6 +269,8 @@ hho_status compute_errors(hho_ctx* ctx, const double* local, const double* u, co
 // assemble.cu
 hho_status build_topology(hho_ctx* ctx);
 hho_status assemble_level0(hho_ctx* ctx);
+// DG scheme: element-block level-0 operator (setup.cu)
+hho_status dg_assemble_level0(hho_ctx* ctx, double* ff, int S_max);
 hho_status assemble_rhs_vector(hho_ctx* ctx, double* rhs);
 hho_status build_level(hho_ctx* ctx, int l, int k_l);
 hho_status build_smoother(hho_ctx* ctx, int l);
@@ -295,8 +297,11 @@ inline int elem_comp(int cond, int d) { return cond == HHO_UNCOND ? d + 1 : 1; }
 // position of the constant pressure mode in an element block of nP unknowns
 inline int mean_slot(int cond, int d, int nP) { return cond == HHO_UNCOND ? d * (nP / (d + 1)) : 0; }
 // index of kernel slot i (element or face, see hho_ctx::null_w) in a vector of level L
+// HHO-hp (face pressure) and DG (element pressure in the block rows): the
+// constant pressure sits in component d of the block rows
+inline bool null_in_blocks(int cond) { return cond == HHO_HPCOND || cond == HHO_DGCOND; }
 inline int64_t null_slot(const hho_ctx* ctx, const LevelMat& L, int64_t i) {
-    if (ctx->disc.cond == HHO_HPCOND) return i * L.b + (int64_t)ctx->disc.d * L.nF;
+    if (null_in_blocks(ctx->disc.cond)) return i * L.b + (int64_t)ctx->disc.d * L.nF;
     return L.nf * L.b + i * L.nP + mean_slot(ctx->disc.cond, ctx->disc.d, L.nP);
 }
 // v = r / *den, z = M^{-1} v with the level-0 block-Jacobi preconditioner (FP64)

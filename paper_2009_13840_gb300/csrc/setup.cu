@@ -42,7 +42,7 @@ namespace {
 constexpr int TPB = 128;     // threads per element CTA
 static_assert(TPB % 32 == 0, "element CTAs are whole warps (warp-shuffle reductions)");
 constexpr int TQ = 32;       // quadrature points per tile
-constexpr int RQ_E = 64;     // element points per tile of the right-hand-side kernel
+constexpr int RQ_E = TPB;    // element points per tile of the right-hand-side kernel (one per thread)
 constexpr int RQ_F = 32;     // face points per tile of the right-hand-side kernel
 
 __device__ __forceinline__ double glx(const double* gl, int n, int i) { return gl[n * MAX_GL + i]; }
@@ -665,6 +665,9 @@ __host__ __device__ inline LocalDims local_dims(int d, int k, int N, int cond) {
     } else if (cond == HHO_UNCOND) {
         D.nel = 0;
         D.nk = N * D.b + (d + 1) * D.nE;
+    } else if (cond == HHO_DGCOND) {  // no local system: the element data of the DG couplings instead
+        D.nel = 0;
+        D.nk = 0;
     } else if (cond == HHO_VCOND) {
         D.nel = d * D.nE;
         D.nk = N * D.b + D.nE;
@@ -926,6 +929,28 @@ __global__ void __launch_bounds__(TPB) k_elements(int d, int k, int cond, int64_
             cta_mm(tmp, nF, CF, nF, false, t5, nF, false, nF, nF, nF, 1.0, 0.0);
             cta_mm(t5, nF, tmp, nF, false, CF, nF, true, nF, nF, nF, 1.0, 0.0);
         }
+        if (cond == HHO_DGCOND) {
+            // DG scheme: the element's stiffness K, Dv[c][e][a] = int phi_e d_c phi_a, and per face the trace
+            // matrices M[a][j] = int_F phi_a psi_j and DN[a][j] = int_F (grad phi_a . n_TF) psi_j (a < nE):
+            // traces of P^k(T) on a planar face lie in P^k(F), so every face coupling is a product of these
+            double* o = outS + off_S[t];
+            for (int idx = threadIdx.x; idx < nE * nE; idx += blockDim.x)
+                o[idx] = Kst[(idx / nE) * nR + idx % nE];
+            o += nE * nE;
+            for (int idx = threadIdx.x; idx < d * nE * nE; idx += blockDim.x) o[idx] = Dt[idx];
+            o += d * nE * nE;
+            for (int f = 0; f < N; ++f) {
+                const double* t2 = T2 + f * nR * nF;
+                const double* t3 = T3 + f * nR * nF;
+                for (int idx = threadIdx.x; idx < nE * nF; idx += blockDim.x) {
+                    o[idx] = t3[idx];
+                    o[nE * nF + idx] = t2[idx];
+                }
+                o += 2 * nE * nF;
+            }
+            __syncthreads();
+            continue;
+        }
         // ---- reconstruction: Kst[1:,1:] P[1:,:] = Rhs[1:,:], P[0,:] = e_0 ----
         double* Rhs = ws + SL.Rhs;
         double* P = ws + SL.P;
@@ -1141,7 +1166,7 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
         {
             int nq = elem_npts(E, d, pd);
             int64_t o = enode_off[t];
-            double* s_v = s_tile;                  // [RQ_E][36]
+            double* s_v = s_tile;                  // [RQ_E][nV]
             double* s_wf = s_tile + RQ_E * 36;     // [RQ_E][3] weight times f_c
             double acc = 0.0;
             const int cI = threadIdx.x / (nV > 0 ? nV : 1), aI = threadIdx.x - cI * nV;
@@ -1150,12 +1175,12 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
                 if (threadIdx.x < nt) {
                     double x[3] = {0, 0, 0}, w;
                     elem_point(E, d, gl, pd, q0 + threadIdx.x, x, &w);
-                    elem_start_val(E, d, kv, x, s_v + threadIdx.x * 36, tab);
+                    elem_start_val(E, d, kv, x, s_v + threadIdx.x * nV, tab);
                     for (int c = 0; c < d; ++c) s_wf[threadIdx.x * 3 + c] = w * fdat[(o + q0 + threadIdx.x) * d + c];
                 }
                 __syncthreads();
                 if (threadIdx.x < d * nV)
-                    for (int q = 0; q < nt; ++q) acc += s_wf[q * 3 + cI] * s_v[q * 36 + aI];
+                    for (int q = 0; q < nt; ++q) acc += s_wf[q * 3 + cI] * s_v[q * nV + aI];
                 __syncthreads();
             }
             if (threadIdx.x < d * nV) s_acc[threadIdx.x] = acc;
@@ -1242,7 +1267,59 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
                 }
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
+            if (cond == HHO_DGCOND && threadIdx.x == 0) {
+                // DG (Scheme 3): data through the face basis (traces of P^k(T) lie in P^k(F)):
+                // Neumann: + int g_N . v_T; Dirichlet: the g_D part of the jump 2 (u_T - g_D) in the BR2 terms,
+                // - (-int L_FT(-2 g_D) . grad v_T + eta int n . L_FT(-2 g_D) v_T), and + int (g_D . n) q_T
+                const double* Dv = P + nE * nE;
+                const double* Mf = P + (d + 1) * nE * nE + (int64_t)f * 2 * nE * nF;
+                double G[3][10], Gn[10];
+                for (int j = 0; j < nF; ++j) {
+                    for (int c = 0; c < d; ++c) {
+                        double v = 0.0;
+                        for (int a = 0; a <= j; ++a) v += CF[j * nF + a] * s_acc[3 * 36 + c * 10 + a];
+                        G[c][j] = v;
+                    }
+                    double v = 0.0;
+                    for (int a = 0; a <= j; ++a) v += CF[j * nF + a] * s_acc[3 * 36 + 3 * 10 + 36 + a];
+                    Gn[j] = v;
+                }
+                if (bc == 2) {
+                    for (int c = 0; c < d; ++c)
+                        for (int a = 0; a < nE; ++a) {
+                            double v = 0.0;
+                            for (int j = 0; j < nF; ++j) v += Mf[a * nF + j] * G[c][j];
+                            rhs[c * nE + a] += v;
+                        }
+                } else {
+                    const double eta = E.N + 1.0;
+                    for (int c = 0; c < d; ++c) {
+                        double MG[36], Wj[10];
+                        for (int e = 0; e < nE; ++e) {
+                            double v = 0.0;
+                            for (int j = 0; j < nF; ++j) v += Mf[e * nF + j] * G[c][j];
+                            MG[e] = v;
+                        }
+                        for (int j = 0; j < nF; ++j) {
+                            double v = 0.0;
+                            for (int e = 0; e < nE; ++e) v += Mf[e * nF + j] * MG[e];
+                            Wj[j] = v;
+                        }
+                        for (int a = 0; a < nE; ++a) {
+                            double a1 = 0.0, a3 = 0.0;
+                            for (int cc = 0; cc < d; ++cc)
+                                for (int e = 0; e < nE; ++e) a1 += E.nTF[f][cc] * Dv[(cc * nE + e) * nE + a] * MG[e];
+                            for (int j = 0; j < nF; ++j) a3 -= eta * Mf[a * nF + j] * Wj[j];
+                            rhs[c * nE + a] -= a1 + a3;
+                        }
+                    }
+                    for (int a = 0; a < nE; ++a) {
+                        double v = 0.0;
+                        for (int j = 0; j < nF; ++j) v += Mf[a * nF + j] * Gn[j];
+                        rhs[d * nE + a] += v;
+                    }
+                }
+            } else if (threadIdx.x == 0) {
                 double eta = 4.0 * (k + 1) * (k + d) / (double)d * E.mF[f] * E.hF[f] / E.meas;
                 for (int c = 0; c < d; ++c) {
                     // face coefficients: int g_c psi_j
@@ -1286,6 +1363,11 @@ __global__ void __launch_bounds__(TPB) k_rhs(int d, int k, int cond, int64_t ne,
                 }
             }
             __syncthreads();
+        }
+        if (cond == HHO_DGCOND) {  // DG: the element's block of the global right-hand side
+            for (int i = threadIdx.x; i < (d + 1) * nE; i += blockDim.x) gT[off_gT[t] + i] = rhs[i];
+            __syncthreads();
+            continue;
         }
         // condensation of the RHS: g = rhs_k - X^T rhs_e, y = Kee^{-1} rhs_e
         const double* Xt = X + off_X[t];
@@ -1415,7 +1497,9 @@ __global__ void k_errors(int d, int k, int cond, int64_t ne, const double* __res
         for (int idx = threadIdx.x; idx < d * nR; idx += blockDim.x) {
             int c = idx / nR, m = idx % nR;
             double s = 0.0;
-            for (int a = 0; a < D.ns; ++a) s += P[m * D.ns + a] * U[vmap(D, c, a)];
+            if (cond == HHO_DGCOND) s = m < nE ? U[c * nE + m] : 0.0;  // DG: the element velocity itself
+            else
+                for (int a = 0; a < D.ns; ++a) s += P[m * D.ns + a] * U[vmap(D, c, a)];
             s_coef[c][m] = s;
         }
         __syncthreads();
@@ -1429,9 +1513,10 @@ __global__ void k_errors(int d, int k, int cond, int64_t ne, const double* __res
             s_st[c][a] = s;
             s_ut[c][a] = (a < nV) ? su : 0.0;
         }
+        const double* Up = (cond == HHO_DGCOND) ? U + d * nE : U + D.nvec;  // element pressure coefficients
         for (int a = threadIdx.x; a < nR; a += blockDim.x) {
             double s = 0.0;
-            for (int m = a; m < nE; ++m) s += U[D.nvec + m] * C[m * nR + a];
+            for (int m = a; m < nE; ++m) s += Up[m] * C[m * nR + a];
             s_pt[a] = (a < nE) ? s : 0.0;
         }
         __syncthreads();
@@ -1473,6 +1558,129 @@ __global__ void k_errors(int d, int k, int cond, int64_t ne, const double* __res
             part[t * 6 + threadIdx.x] = s;
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// DG scheme (Scheme 3, Sec. 2.4): the element-block operator.  Row block of
+// element S: slot 0 = S itself, slot 1 + i = the neighbour across S's i-th
+// interior face (local face order).  Every face coupling is formed from the
+// element data of k_elements (K, Dv, and per face the trace matrices M, DN in
+// the face basis): with M_X the traces of element X on face F,
+//   int_F phi_a^S phi_b^X = (M_S M_X^T)[a][b],
+//   int_F phi_a^S (grad phi_b^X . n_X) = (M_S DN_X^T)[a][b],
+// and the BR2 lifting of a jump is 1/2 n (x) (M_S M_X^T) on S.  One CTA per
+// element; each block entry is written by that CTA only (faces in order).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TPB) k_dg_assemble(int d, int k, int64_t ne, const double* __restrict__ xyz,
+                                                     const int32_t* __restrict__ ef_ptr, const int32_t* __restrict__ ef,
+                                                     const int32_t* __restrict__ fv_ptr, const int32_t* __restrict__ fv,
+                                                     const int8_t* __restrict__ fbc, const FaceGeo* __restrict__ fgeo,
+                                                     const int32_t* __restrict__ fe, const int32_t* __restrict__ flf,
+                                                     const int64_t* __restrict__ off_S, const double* __restrict__ dgd,
+                                                     int S_max, double* __restrict__ ff) {
+    __shared__ ElemSh E;
+    __shared__ double s_P[100], s_MDN[100], s_MQM[100], s_DP[300], s_Q[100];
+    const int nE = dimP(d, k), nF = dimP(d - 1, k), b = (d + 1) * nE;
+    for (int64_t S = blockIdx.x; S < ne; S += gridDim.x) {
+        load_element(E, d, (int)S, ef_ptr, ef, fv_ptr, fv, xyz, fgeo, fbc);
+        const double* dS = dgd + off_S[S];
+        const double* K = dS;
+        const double* Dv = dS + nE * nE;
+        const int64_t bb = (int64_t)b * b;
+        auto at = [&](int s, int r, int c) -> double& { return ff[((int64_t)s * bb + (int64_t)c * b + r) * ne + S]; };
+        for (int64_t i = threadIdx.x; i < S_max * bb; i += blockDim.x) {
+            const int s = (int)(i / bb), rc = (int)(i % bb);
+            at(s, rc % b, rc / b) = 0.0;
+        }
+        __syncthreads();
+        // volume: K per velocity component, -int p div v and its transpose
+        for (int i = threadIdx.x; i < b * b; i += blockDim.x) {
+            const int r = i / b, c = i % b;
+            const int gr = r / nE, a = r % nE, gc = c / nE, q = c % nE;
+            double v = 0.0;
+            if (gr < d && gc == gr) v = K[a * nE + q];
+            else if (gr < d && gc == d) v = -Dv[(gr * nE + q) * nE + a];
+            else if (gr == d && gc < d) v = -Dv[(gc * nE + a) * nE + q];
+            at(0, r, c) += v;
+        }
+        __syncthreads();
+        int slot = 0;
+        for (int f = 0; f < E.N; ++f) {
+            const int F = E.fid[f];
+            const bool interior = fe[2 * F] >= 0 && fe[2 * F + 1] >= 0;
+            if (!interior && E.bcf[f] == 2) continue;  // Neumann faces carry no BR2 term and no coupling
+            int Tn = -1, fn = -1;
+            if (interior) {
+                const int e0 = fe[2 * F];
+                Tn = (e0 == (int)S) ? fe[2 * F + 1] : e0;
+                fn = (e0 == (int)S) ? flf[2 * F + 1] : flf[2 * F];
+                ++slot;
+            }
+            const double* MS = dS + (d + 1) * nE * nE + (int64_t)f * 2 * nE * nF;
+            const double* MT = interior ? dgd + off_S[Tn] + (d + 1) * nE * nE + (int64_t)fn * 2 * nE * nF : nullptr;
+            const int NS = E.N, NT = interior ? ef_ptr[Tn + 1] - ef_ptr[Tn] : 0;
+            const double eta = (interior ? (double)max(NS, NT) : (double)NS) + 1.0;
+            const double hF = E.hF[f];
+            // Q = M_S^T M_S (+ M_T^T M_T on interior faces): nF x nF
+            for (int i = threadIdx.x; i < nF * nF; i += blockDim.x) {
+                const int j = i / nF, jj = i % nF;
+                double v = 0.0;
+                for (int e = 0; e < nE; ++e) v += MS[e * nF + j] * MS[e * nF + jj];
+                if (interior)
+                    for (int e = 0; e < nE; ++e) v += MT[e * nF + j] * MT[e * nF + jj];
+                s_Q[i] = v;
+            }
+            __syncthreads();
+            for (int side = 0; side < (interior ? 2 : 1); ++side) {
+                const double* MX = side == 0 ? MS : MT;
+                const double* DNX = MX + nE * nF;
+                const double sig = interior ? (side == 0 ? 1.0 : -1.0) : 2.0;
+                const int s = side == 0 ? 0 : slot;
+                for (int i = threadIdx.x; i < nE * nE; i += blockDim.x) {
+                    const int a = i / nE, q = i % nE;
+                    double p = 0.0, m = 0.0, mq = 0.0;
+                    for (int j = 0; j < nF; ++j) {
+                        p += MS[a * nF + j] * MX[q * nF + j];
+                        m += MS[a * nF + j] * DNX[q * nF + j];
+                        double t = 0.0;
+                        for (int jj = 0; jj < nF; ++jj) t += s_Q[j * nF + jj] * MX[q * nF + jj];
+                        mq += MS[a * nF + j] * t;
+                    }
+                    s_P[i] = p;
+                    s_MDN[i] = m;
+                    s_MQM[i] = mq;
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < d * nE * nE; i += blockDim.x) {
+                    const int c = i / (nE * nE), a = (i / nE) % nE, q = i % nE;
+                    double v = 0.0;
+                    for (int e = 0; e < nE; ++e) v += Dv[(c * nE + e) * nE + a] * s_P[e * nE + q];
+                    s_DP[i] = v;
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < b * b; i += blockDim.x) {
+                    const int r = i / b, c = i % b;
+                    const int gr = r / nE, a = r % nE, gc = c / nE, q = c % nE;
+                    const double P = s_P[a * nE + q];
+                    double v = 0.0;
+                    if (gr < d && gc == gr) {
+                        double dp = 0.0;
+                        for (int cc = 0; cc < d; ++cc) dp += E.nTF[f][cc] * s_DP[(cc * nE + a) * nE + q];
+                        if (interior) v = -0.5 * sig * dp - 0.5 * sig * s_MDN[a * nE + q] + 0.25 * eta * sig * s_MQM[a * nE + q];
+                        else v = -dp - s_MDN[a * nE + q] + eta * s_MQM[a * nE + q];
+                    } else if (gr < d && gc == d) {
+                        v = (interior ? 0.5 : 1.0) * E.nTF[f][gr] * P;
+                    } else if (gr == d && gc < d) {
+                        v = (interior ? 0.5 * sig : 1.0) * E.nTF[f][gc] * P;
+                    } else if (gr == d && gc == d && interior) {
+                        v = -hF * sig * P;
+                    }
+                    if (v != 0.0) at(s, r, c) += v;
+                }
+                __syncthreads();
+            }
+        }
     }
 }
 
@@ -1527,6 +1735,16 @@ static int element_grid(int64_t ne) {
     return (int)std::min<int64_t>(g, std::max<int64_t>(ne, 1));
 }
 
+// DG scheme: level-0 element-block operator from the element data of
+// k_elements (one CTA per element, grid-stride).
+hho_status dg_assemble_level0(hho_ctx* ctx, double* ff, int S_max) {
+    const Disc& D = ctx->disc;
+    k_dg_assemble<<<element_grid(D.ne), TPB, 0, ctx->stream>>>(D.d, D.k, D.ne, D.xyz, D.ef_ptr, D.ef, D.fv_ptr, D.fv,
+                                                                D.fbc, D.fgeo, D.fe, D.flf, D.off_S, D.S, S_max, ff);
+    HHO_CUDA(cudaGetLastError());
+    return HHO_OK;
+}
+
 hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond) {
     Disc& D = ctx->disc;
     const int d = m->dim;
@@ -1539,8 +1757,11 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
     D.nR = dimP(d, k + 1);
     D.nE = dimP(d, k);
     D.nF = dimP(d - 1, k);
-    D.b = local_dims(d, k, 0, cond).b;
-    D.nP = (cond == HHO_HPCOND) ? 0 : (cond == HHO_VPCOND) ? 1 : (cond == HHO_UNCOND) ? (d + 1) * D.nE : D.nE;
+    D.b = (cond == HHO_DGCOND) ? (d + 1) * D.nE : local_dims(d, k, 0, cond).b;
+    D.nP = (cond == HHO_HPCOND || cond == HHO_DGCOND) ? 0
+           : (cond == HHO_VPCOND)                      ? 1
+           : (cond == HHO_UNCOND)                      ? (d + 1) * D.nE
+                                                       : D.nE;
     // host topology (int32)
     D.h_ef_ptr.resize(D.ne + 1);
     D.h_ef.resize(m->elem_face_ptr[D.ne]);
@@ -1573,7 +1794,7 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
         const LocalDims L = local_dims(d, k, D.h_ef_ptr[t + 1] - D.h_ef_ptr[t], cond);
         const int ns = L.ns, nloc = L.nloc, nel = L.nel, nk = L.nk;
         oS[t] = tS;
-        tS += (int64_t)nk * nk;
+        tS += (cond == HHO_DGCOND) ? (int64_t)(d + 1) * D.nE * D.nE + 2LL * L.N * D.nE * D.nF : (int64_t)nk * nk;
         oX[t] = tX;
         tX += (int64_t)nel * nk;
         oK[t] = tK;
@@ -1581,9 +1802,9 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
         oP[t] = tP;
         tP += (int64_t)D.nR * ns;
         oL[t] = tL;
-        tL += nloc;
+        tL += (cond == HHO_DGCOND) ? (int64_t)(d + 1) * D.nE : nloc;  // DG: the solution block itself
         oG[t] = tG;
-        tG += nk;
+        tG += (cond == HHO_DGCOND) ? (int64_t)(d + 1) * D.nE : nk;  // DG: the element's block of the global RHS
         oY[t] = tY;
         tY += nel;
     }
@@ -1693,14 +1914,15 @@ hho_status build_discretisation(hho_ctx* ctx, const hho_mesh* m, int k, int cond
 
 hho_status build_rhs(hho_ctx* ctx, const double* f, const double* gD, const double* gN) {
     Disc& D = ctx->disc;
+    const bool dg = D.cond == HHO_DGCOND;  // the DG element data (D.S) take the place of the reconstruction
     int grid = element_grid(D.ne);
     const int64_t per = (local_dims(D.d, D.k, D.maxN, D.cond).nloc + 3) & ~3;
     double* scratch = nullptr;
     HHO_TRY(dalloc(ctx, &scratch, (size_t)grid * per));
     k_rhs<<<grid, TPB, 0, ctx->stream>>>(D.d, D.k, D.cond, D.ne, D.xyz, D.ef_ptr, D.ef, D.fv_ptr, D.fv, D.fbc, D.fgeo,
                                          D.fC, D.eC, D.emeas, D.gl, D.enode_off, D.fnode_off, f, gD, gN, D.off_X,
-                                         D.off_Kei, D.off_P, D.off_gT, D.off_yT, D.X, D.Kei, D.P, D.gT, D.yT, scratch,
-                                         per);
+                                         D.off_Kei, dg ? D.off_S : D.off_P, D.off_gT, D.off_yT, D.X, D.Kei,
+                                         dg ? D.S : D.P, D.gT, D.yT, scratch, per);
     cudaError_t le = cudaGetLastError();
     cudaError_t se = cudaStreamSynchronize(ctx->stream);
     dfree(scratch);
@@ -1715,6 +1937,7 @@ hho_status build_rhs(hho_ctx* ctx, const double* f, const double* gD, const doub
 hho_status build_rhs_scratch(hho_ctx* ctx, const double* f, const double* gD, const double* gN, double* scratch,
                              int64_t capacity) {
     Disc& D = ctx->disc;
+    const bool dg = D.cond == HHO_DGCOND;
     const int64_t per = (local_dims(D.d, D.k, D.maxN, D.cond).nloc + 3) & ~3;
     const int64_t fit = capacity / per;
     if (fit < 1) {
@@ -1724,8 +1947,8 @@ hho_status build_rhs_scratch(hho_ctx* ctx, const double* f, const double* gD, co
     const int grid = (int)std::min<int64_t>(element_grid(D.ne), fit);
     k_rhs<<<grid, TPB, 0, ctx->stream>>>(D.d, D.k, D.cond, D.ne, D.xyz, D.ef_ptr, D.ef, D.fv_ptr, D.fv, D.fbc, D.fgeo,
                                          D.fC, D.eC, D.emeas, D.gl, D.enode_off, D.fnode_off, f, gD, gN, D.off_X,
-                                         D.off_Kei, D.off_P, D.off_gT, D.off_yT, D.X, D.Kei, D.P, D.gT, D.yT, scratch,
-                                         per);
+                                         D.off_Kei, dg ? D.off_S : D.off_P, D.off_gT, D.off_yT, D.X, D.Kei,
+                                         dg ? D.S : D.P, D.gT, D.yT, scratch, per);
     HHO_CUDA(cudaGetLastError());
     return HHO_OK;
 }
@@ -1750,6 +1973,11 @@ hho_status quad_nodes(hho_ctx* ctx, int which, int64_t* n, double* xyz, double* 
 
 hho_status recover_local(hho_ctx* ctx, const double* x, double* local) {
     Disc& D = ctx->disc;
+    if (D.cond == HHO_DGCOND) {  // no eliminated unknowns: the local vectors are the solution's element blocks
+        HHO_CUDA(cudaMemcpyAsync(local, x, (size_t)D.ne * D.b * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+        return HHO_OK;
+    }
     int grid = element_grid(D.ne);
     k_recover<<<grid, 64, 0, ctx->stream>>>(D.d, D.k, D.cond, D.ne, D.nf, D.b, D.nP, D.ef_ptr, D.ef, D.off_X, D.off_yT,
                                             D.off_loc, D.X, D.yT, x, local);

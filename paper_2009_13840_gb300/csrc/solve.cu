@@ -1907,9 +1907,8 @@ hho_status vcycle(hho_ctx* ctx, const double* r, double* z) {
 template <typename T>
 hho_status null_project(hho_ctx* ctx, const LevelMat& L, T* x) {
     if (!ctx->has_null) return HHO_OK;
-    const bool hp = ctx->disc.cond == HHO_HPCOND;
     T* xp = x + null_slot(ctx, L, 0);
-    const int stride = hp ? L.b : L.nP, nch = ctx->null_nch;
+    const int stride = null_in_blocks(ctx->disc.cond) ? L.b : L.nP, nch = ctx->null_nch;
     const unsigned g = (unsigned)(ctx->probs.P * nch);
     k_null_dot<T><<<g, 512, 0, ctx->stream>>>(ctx->d_null_off, nch, ctx->null_w, xp, stride, ctx->null_part);
     k_null_sub<T><<<g, 512, 0, ctx->stream>>>(ctx->d_null_off, nch, ctx->null_w, xp, stride, ctx->null_part);

@@ -20,7 +20,7 @@ HHO_OK = 0
 STATUS = {0: "HHO_OK", 1: "HHO_ERR_ARG", 2: "HHO_ERR_MESH", 3: "HHO_ERR_CUDA", 4: "HHO_ERR_NOMEM",
           5: "HHO_ERR_SINGULAR", 6: "HHO_ERR_NOT_CONVERGED", 7: "HHO_ERR_TIMEOUT", 8: "HHO_ERR_STATE",
           9: "HHO_ERR_UNSUPPORTED"}
-COND = {"v": 0, "vp": 1, "hp": 2, "unc": 3}
+COND = {"v": 0, "vp": 1, "hp": 2, "unc": 3, "dg": 4}
 NODES = {"elem": 0, "face": 1}
 
 # every entry point declared in include/hho.h
@@ -361,11 +361,13 @@ class Context:
 
     def local_size(self):
         """Length of hho_recover's output: per element [U_T | U_F.. | P_T] (Scheme 1),
-        [U_T | U_F.. | P_T | P_F..] with U_T of degree k+1 (HHO-hp)."""
+        [U_T | U_F.. | P_T | P_F..] with U_T of degree k+1 (HHO-hp), [u_T | p_T] (DG)."""
         d, k = self.dim, self.k
         nE = _dimP(d, k)
         nF = _dimP(d - 1, k)
         N = np.diff(self.mesh.elem_face_ptr)
+        if self.cond == "dg":
+            return int(len(N) * (d + 1) * nE)
         if self.cond == "hp":
             return int(np.sum(d * _dimP(d, k + 1) + N * d * nF + nE + N * nF))
         return int(np.sum(d * nE + N * d * nF + nE))
