@@ -99,7 +99,7 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--sample-n", type=int, default=None, help="mesh size of the CPU-oracle sample")
     ap.add_argument("--oracle-faces", type=int, default=12,
-                    help="faces of the full-size solution whose residual rows the oracle recomputes")
+                    help="faces (DG: elements) of the full-size solution whose residual rows the oracle recomputes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--probe-spmv", action="store_true", help="three FP32 and one FP64 level-0 operator launches")
@@ -370,8 +370,25 @@ def oracle_check(mesh, k, cond, fld, x, b_gpu, Sx_gpu, faces, seed=0):
         sf = sample_interior_faces(mesh, faces, seed)
         rows, r, b, sc = residual_rows(mesh, k, cond, fld, x, sf, with_scale=True)
         dt = time.perf_counter() - t0
+    return dict({"faces": int(len(sf))}, **_row_check(rows, r, b, sc, b_gpu, Sx_gpu, dt))
+
+
+def oracle_check_dg(mesh, k, fld, x, b_gpu, Sx_gpu, count, seed=0):
+    """The DG scheme's counterpart of oracle_check: the oracle recomputes the
+    element rows of `count` sampled elements (oracle/sampled.py, from the
+    submesh of those elements and their neighbours)."""
+    from oracle.sampled import residual_rows_dg, sample_elements
+    with one_thread():
+        t0 = time.perf_counter()
+        se = sample_elements(mesh, count, seed)
+        rows, r, b, sc = residual_rows_dg(mesh, k, fld, x, se, with_scale=True)
+        dt = time.perf_counter() - t0
+    return dict({"elements": int(len(se))}, **_row_check(rows, r, b, sc, b_gpu, Sx_gpu, dt))
+
+
+def _row_check(rows, r, b, sc, b_gpu, Sx_gpu, dt):
     r_gpu = b_gpu[rows] - Sx_gpu[rows]
-    return {"faces": int(len(sf)), "rows": int(len(rows)),
+    return {"rows": int(len(rows)),
             "system_rows_max_diff_rel": float(np.max(np.abs(r - r_gpu) / sc)),
             "rhs_rows_max_diff_rel": float(np.abs(b - b_gpu[rows]).max() / np.abs(b_gpu[rows]).max()),
             "residual_rows_scaled": float(np.linalg.norm(r) / np.linalg.norm(b_gpu) * np.sqrt(len(b_gpu) / len(rows))),
@@ -555,9 +572,10 @@ def run_ours(args):
                "sample": f"oracle FGMRES+p-MG solve on {sample_name(args)} of the same family ({nd} DOFs against "
                          f"{ndof} in the workload, {its} its, {dt:.2f} s per solve, {ts:.1f} s setup excluded), "
                          f"one thread"}
-        # the oracle recomputes residual rows of the full-size GPU solution at sampled faces (Scheme 1 and 2; the
-        # DG operator's parity is covered at several-tile sizes by the GPU tests)
-        if args.cond != "dg":
+        # the oracle recomputes residual rows of the full-size GPU solution at sampled faces (DG: elements)
+        if args.cond == "dg":
+            check = oracle_check_dg(mesh, args.k, fld, x_host, b_host, sx_host, args.oracle_faces)
+        else:
             check = oracle_check(mesh, args.k, args.cond, fld, x_host, b_host, sx_host, args.oracle_faces)
     if rank == 0:
         last = infos[-1]

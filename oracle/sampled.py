@@ -11,13 +11,16 @@ intrinsic (its vertices in their stored order, its boundary tag), so the local
 systems are computed on the submesh made of the sampled faces' elements and
 all of their faces, with the element and face numbering of the full mesh kept
 in increasing order; HHO of Sec. 2 on that submesh gives the same S_T and g_T
-as on the full mesh.  Pinned in tests against the rows of b - S x of the full
-oracle on small meshes.
+as on the full mesh.  The DG scheme's element rows (residual_rows_dg) are
+taken the same way from the submesh of the sampled elements and their
+neighbours.  Pinned in tests against the rows of b - S x of the full oracle
+on small meshes.
 """
 from __future__ import annotations
 
 import numpy as np
 
+from .dg import DG
 from .hho import HHO
 from .hho_hp import HHOhp
 
@@ -97,6 +100,50 @@ def residual_rows(mesh, k, cond, field, x, sample_faces, with_scale=False):
         sc.extend(sc_loc[o:o + nP])
     out = (np.asarray(rows), np.asarray(r), np.asarray(b))
     return out + (np.asarray(sc),) if with_scale else out
+
+
+def residual_rows_dg(mesh, k, field, x, sample_elems, with_scale=False):
+    """DG scheme (Scheme 3, Sec. 2.4): (rows, r, b), the residual b - S x and
+    b on the element blocks of the sampled elements, x the DG vector of the
+    full mesh (one block of (d+1) n_E per element).  The block row of an
+    element S couples S with the neighbours across its interior faces only, and
+    each coupling is intrinsic to S, that neighbour and their shared face (the
+    penalty of reading 29 takes the face counts of both).  So the rows are
+    computed on the submesh of the sampled elements and their neighbours with
+    all of their faces: there the neighbours' own rows change (their outer
+    faces lose a side), the sampled rows do not.  With with_scale, also the
+    scale |b_i| + sum over the blocks (S, T) of row i of max|block| ||x_T||_1,
+    the bound on rows of S x whose blocks agree to eps of their largest
+    entry."""
+    sample = np.unique(np.asarray(sample_elems, dtype=np.int64))
+    nbrs = [int(t) for S in sample for F in mesh.faces_of(int(S)) for t in mesh.face_elem[int(F)] if t >= 0]
+    sub, elems, _ = _submesh(mesh, np.concatenate([sample, np.asarray(nbrs, dtype=np.int64)]))
+    h = DG(sub, k)
+    b_loc = h.assemble_rhs(*h.data_values(field))
+    nb = h.nb
+    xs = np.concatenate([x[int(t) * nb:(int(t) + 1) * nb] for t in elems])
+    r_loc = b_loc - h.S @ xs
+    epos = {int(t): i for i, t in enumerate(elems)}
+    rows, r, b, sc = [], [], [], []
+    for S in sample:
+        i = epos[int(S)]
+        sl = slice(i * nb, (i + 1) * nb)
+        s = np.abs(b_loc[sl])
+        for (p, q), M in h.blocks.items():
+            if p == i:
+                s = s + np.abs(M).max() * np.abs(xs[q * nb:(q + 1) * nb]).sum()
+        rows.extend(int(S) * nb + np.arange(nb))
+        r.extend(r_loc[sl])
+        b.extend(b_loc[sl])
+        sc.extend(s)
+    out = (np.asarray(rows), np.asarray(r), np.asarray(b))
+    return out + (np.asarray(sc),) if with_scale else out
+
+
+def sample_elements(mesh, count, seed):
+    """`count` elements drawn without replacement (seeded) from the elements of the mesh."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(mesh.n_elem, size=min(count, mesh.n_elem), replace=False))
 
 
 def sample_interior_faces(mesh, count, seed):

@@ -69,3 +69,23 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert out.returncode == 0, out.stderr[-2000:]
     d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
+
+
+def test_oracle_row_checks_on_cpu():
+    """bench.py's full-size row checks on an oracle-made system (no GPU): with
+    the oracle's own right-hand side and S x as the 'GPU' vectors, the rows
+    agree to rounding, for Scheme 1 (faces) and the DG scheme (elements)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from oracle.dg import DG
+    from oracle.hho import HHO
+    from synthetic import tri_mesh, fields
+    mesh = tri_mesh(6, 5, jitter=0.2, seed=3, neumann_sides=(1,))
+    fld = fields.TrigStokes2D()
+    for h, check in ((HHO(mesh, 2, "v"), lambda h, x, b, sx: bench.oracle_check(mesh, 2, "v", fld, x, b, sx, 5)),
+                     (DG(mesh, 2), lambda h, x, b, sx: bench.oracle_check_dg(mesh, 2, fld, x, b, sx, 5))):
+        b = h.assemble_rhs(*h.data_values(fld))
+        x = np.random.default_rng(4).standard_normal(h.ndof)
+        c = check(h, x, b, h.S @ x)
+        assert c["rows"] > 0 and c["system_rows_max_diff_rel"] < 1e-13 and c["rhs_rows_max_diff_rel"] < 1e-13

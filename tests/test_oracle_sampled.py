@@ -80,3 +80,28 @@ def test_row_scale_bounds_element_perturbations():
     import scipy.sparse as sp
     dS = sp.csr_matrix((np.concatenate(vv), (np.concatenate(rr), np.concatenate(cc))), shape=h.S.shape)
     assert np.all(np.abs((dS @ x)[rows]) <= eps * sc)
+
+
+@pytest.mark.parametrize("mk,k,fld", [
+    (lambda: tri_mesh(6, 5, jitter=0.2, seed=3, neumann_sides=(1,)), 2, fields.TrigStokes2D()),
+    (lambda: quad_mesh(5, 4, jitter=0.15, seed=4), 3, fields.TrigStokes2D()),
+    (lambda: hex_mesh(3, jitter=0.15, seed=2), 1, fields.CurlStokes3D()),
+])
+def test_sampled_rows_dg(mk, k, fld):
+    """The DG scheme (Scheme 3): the element rows of sampled elements, from the
+    submesh of those elements and their neighbours, equal the rows of the full
+    oracle's b - S x, and the row scale bounds |b| + |S||x| on them."""
+    from oracle.dg import DG
+    from oracle.sampled import residual_rows_dg, sample_elements
+    mesh = mk()
+    h = DG(mesh, k)
+    b = h.assemble_rhs(*h.data_values(fld))
+    x = np.random.default_rng(3).standard_normal(h.ndof)
+    full = b - h.S @ x
+    sample = sample_elements(mesh, 5, seed=7)
+    rows, r, bs, sc = residual_rows_dg(mesh, k, fld, x, sample, with_scale=True)
+    assert len(rows) == len(sample) * h.nb and len(set(rows.tolist())) == len(rows)
+    assert np.abs(r - full[rows]).max() <= 1e-12 * np.abs(full).max()
+    assert np.abs(bs - b[rows]).max() <= 1e-12 * np.abs(b).max()
+    bound = np.abs(b[rows]) + (abs(h.S) @ np.abs(x))[rows]
+    assert (sc >= bound * (1 - 1e-12)).all()
