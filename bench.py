@@ -50,7 +50,7 @@ UNIT = "DOF/s"
 SPMV_F32_TRAFFIC = {("tri", 128, 3, "v"): 144286208 + 3245056, ("hex", 32, 3, "vp"): 4119717980,
                     ("hex", 32, 3, "hp"): round((892412928 + 1694208) * 6979174400 / 874983424)}
 
-# the named workloads (BASELINE configurations); command-line values override
+# the named workloads (the paper's configurations and the comparison schemes); command-line values override
 SPECS = {
     "c3": dict(mesh="hex", n=32, k=3, cond="vp", prec="fp32", coarse_fp32=1, sample_n=4),
     "c2": dict(mesh="tri", n=128, k=3, cond="v", prec="fp32", coarse_fp32=1, sample_n=24),
