@@ -1580,6 +1580,7 @@ __global__ void __launch_bounds__(TPB) k_dg_assemble(int d, int k, int64_t ne, c
                                                      const int64_t* __restrict__ off_S, const double* __restrict__ dgd,
                                                      int S_max, double* __restrict__ ff) {
     __shared__ ElemSh E;
+    // nE, nF <= 10 and d nE^2 <= 300: hho_setup refuses DG degrees above 3 (2D) and 2 (3D)
     __shared__ double s_P[100], s_MDN[100], s_MQM[100], s_DP[300], s_Q[100];
     const int nE = dimP(d, k), nF = dimP(d - 1, k), b = (d + 1) * nE;
     for (int64_t S = blockIdx.x; S < ne; S += gridDim.x) {
