@@ -117,3 +117,80 @@ def test_closed_elements_and_outward_normals(mk):
         assert abs(vol - e.meas) < 1e-13
         total += e.meas
     assert abs(total - 1.0) < 1e-13
+
+
+def _monomials(dim, deg):
+    if dim == 2:
+        return [(a, m - a) for m in range(deg + 1) for a in range(m + 1)]
+    return [(a, b, m - a - b) for m in range(deg + 1) for a in range(m + 1) for b in range(m - a + 1)]
+
+
+def _segment_integral(P0, P1, g, deg):
+    """int over the segment P0-P1 of g (a polynomial of degree deg), Gauss-Legendre from numpy."""
+    t, w = np.polynomial.legendre.leggauss(deg // 2 + 2)
+    t, w = 0.5 * (t + 1.0), 0.5 * w
+    X = P0[None, :] + t[:, None] * (P1 - P0)[None, :]
+    return float(np.linalg.norm(P1 - P0) * (w @ g(X)))
+
+
+def _triangle_integral(P0, P1, P2, g, deg):
+    """int over a 3D triangle of g (degree deg), collapsed square (Duffy) with numpy Gauss-Legendre."""
+    t, w = np.polynomial.legendre.leggauss(deg // 2 + 3)
+    t, w = 0.5 * (t + 1.0), 0.5 * w
+    u, v = np.meshgrid(t, t, indexing="ij")
+    wu = np.outer(w, w)
+    X = P0 + u.ravel()[:, None] * (P1 - P0) + (u * v).ravel()[:, None] * (P2 - P1)
+    jac = np.linalg.norm(np.cross(P1 - P0, P2 - P1))
+    return float(jac * np.sum(wu.ravel() * u.ravel() * g(X)))
+
+
+def _polygon_face_integral(V, g, deg):
+    return sum(_triangle_integral(V[0], V[i], V[i + 1], g, deg) for i in range(1, len(V) - 1))
+
+
+@pytest.mark.parametrize("mk", [lambda: tri_mesh(3, jitter=0.3, seed=2), lambda: quad_mesh(3, jitter=0.3, seed=2),
+                                lambda: hex_mesh(2, jitter=0.3, seed=2)], ids=["tri", "quad", "hex"])
+def test_element_and_face_rules_exact_to_their_order(mk):
+    """ElemGeom.rule(p) and FaceGeom.rule(p) integrate every monomial of degree
+    <= p exactly.  Reference values from the mesh's vertices alone: element
+    integrals by the divergence theorem (int_T x^a y^b.. = int_dT x^(a+1) y^b.. /
+    (a+1) n_x, outward normals from the vertex average), boundary and face
+    integrals by numpy's Gauss-Legendre on segments and on collapsed triangles
+    of a fan of every planar face."""
+    mesh = mk()
+    d = mesh.dim
+    elems, faces = mesh_geometry(mesh)
+    for p in ((1, 4, 7) if d == 2 else (1, 3, 5)):
+        for t in range(min(mesh.n_elem, 5)):
+            e = elems[t]
+            fs = mesh.faces_of(t)
+            c = mesh.xyz[np.unique(np.concatenate([mesh.verts_of_face(int(F)) for F in fs]))].mean(axis=0)
+            h = e.hT
+            X, W = e.rule(p)
+            for mono in _monomials(d, p):
+                f = lambda Y, m=mono: np.prod(((Y - c) / h) ** np.array(m), axis=1)
+                G = lambda Y, m=mono: ((Y[:, 0] - c[0]) / h) ** (m[0] + 1) * h / (m[0] + 1) * np.prod(
+                    ((Y[:, 1:] - c[1:]) / h) ** np.array(m[1:]), axis=1)
+                exact = 0.0
+                for F in fs:
+                    V = mesh.xyz[mesh.verts_of_face(int(F))]
+                    if d == 2:
+                        tan = V[1] - V[0]
+                        n = np.array([tan[1], -tan[0]]) / np.linalg.norm(tan)
+                        n = n if n @ (V.mean(axis=0) - c) > 0 else -n
+                        exact += n[0] * _segment_integral(V[0], V[1], G, sum(mono) + 1)
+                    else:
+                        n = np.cross(V[1] - V[0], V[2] - V[0])
+                        n /= np.linalg.norm(n)
+                        n = n if n @ (V.mean(axis=0) - c) > 0 else -n
+                        exact += n[0] * _polygon_face_integral(V, G, sum(mono) + 1)
+                assert abs(W @ f(X) - exact) <= 1e-12 * e.meas, (t, p, mono)
+        for F in faces[:6]:
+            V = F.V
+            c = V.mean(axis=0)
+            X, W = F.rule(p)
+            for mono in _monomials(d, p):
+                f = lambda Y, m=mono: np.prod(((Y - c) / F.hF) ** np.array(m), axis=1)
+                exact = (_segment_integral(V[0], V[1], f, sum(mono)) if d == 2
+                         else _polygon_face_integral(V, f, sum(mono)))
+                assert abs(W @ f(X) - exact) <= 1e-12 * F.meas, (F.id, p, mono)
