@@ -6,7 +6,8 @@ dropped term (the Nitsche penalty, the BR2 penalty), a wrong sign (one of the
 two pressure-coupling blocks, the smoother's pressure pivot, the printed sign
 of the DG pressure stabilisation), a wrong orientation (an inward normal), a
 wrong index (the restriction keeping the wrong coefficients), too low a
-quadrature order."""
+quadrature order, a dropped factor in a gradient, truncation in place of
+round-to-nearest-even."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -18,6 +19,7 @@ import oracle.pmg as opmg
 import test_oracle_dg as pins_dg
 import test_oracle_hho as pins_hho
 import test_oracle_hp as pins_hp
+import test_oracle_mlp as pins_mlp
 import test_oracle_pmg as pins_pmg
 import test_oracle_quadrature_basis as pins_quad
 
@@ -153,3 +155,24 @@ def test_dg_printed_stabilisation_sign(monkeypatch):
         self.S = S.tocsr()
     monkeypatch.setattr(odg.DG, "_build", wrong)
     _fails(pins_dg.test_dg_symmetry_kernel_inertia, True)
+
+
+# --- learned-smoother oracle ---
+
+def test_mlp_gradient_without_the_factor_two(monkeypatch):
+    """d|D|^2 = 2 D dD: the gradients of the loss with the 2 dropped."""
+    real = pins_mlp.loss_and_grads
+
+    def wrong(*args):
+        loss, g = real(*args)
+        return loss, {k: 0.5 * v for k, v in g.items()}
+    monkeypatch.setattr(pins_mlp, "loss_and_grads", wrong)
+    _fails(pins_mlp.test_gradients_match_finite_differences)
+
+
+def test_bf16_truncation_instead_of_rounding(monkeypatch):
+    def truncate(a):
+        u = np.asarray(a, dtype=np.float32).copy().view(np.uint32) & np.uint32(0xFFFF0000)
+        return u.view(np.float32).astype(np.float64)
+    monkeypatch.setattr(pins_mlp, "bf16_round", truncate)
+    _fails(pins_mlp.test_bf16_rounding)
