@@ -13,11 +13,14 @@ independently of the oracle's element-by-element assembly:
   sum_T |grad u|^2 - 2 sum_F int {grad u} . n [u] + eta sum_F sum_T ||L_FT([u])||^2
   (Dirichlet faces with [u] = 2 u and -int (grad u . n) [u]) computed from the
   lifting coefficients directly;
-* h-convergence orders on smooth data (velocity k+1, pressure about k).
+* h-convergence orders on smooth data (velocity k+1, pressure about k);
+* the restriction equals the L2 projections from independently built bases
+  and the coarse operators are the Galerkin products with them.
 """
 import numpy as np
 import pytest
 
+from oracle.basis import dim_P
 from oracle.dg import DG
 from synthetic import tri_mesh, quad_mesh, hex_mesh, fields
 
@@ -135,3 +138,38 @@ def test_dg_pmg_transfers_keep_the_kernel_and_fgmres_converges():
     x, its, rr = fgmres(h.S, pmg.apply, rhs, rtol=1e-10, null=h.null_vector(), maxit=300)
     assert rr <= 1e-10
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6  # kappa(S) rtol
+
+
+def test_dg_restriction_is_the_l2_projection_and_galerkin():
+    """The DG restriction (Sec. 4.2 patched element by element: every velocity
+    component and the pressure) equals the L2 projections int phi_i^{l+1}
+    phi_j^l computed from independently built bases of each degree, and the
+    hierarchy's coarse operators are R S R^T with those projections."""
+    from oracle.basis import element_basis
+    from oracle.pmg import PMG, restriction
+    mesh = tri_mesh(2, jitter=0.2, seed=3)
+    h = DG(mesh, 3)
+    d = mesh.dim
+
+    def explicit(k_f, k_c):
+        nEf, nEc = dim_P(d, k_f), dim_P(d, k_c)
+        R = np.zeros((mesh.n_elem * (d + 1) * nEc, mesh.n_elem * (d + 1) * nEf))
+        for e in h.elems:
+            Bf, Bc = element_basis(e, k_f), element_basis(e, k_c)
+            X, W = e.rule(2 * k_f + 2)
+            I = Bc.eval(X).T @ (W[:, None] * Bf.eval(X))
+            for c in range(d + 1):
+                r0, c0 = (e.id * (d + 1) + c) * nEc, (e.id * (d + 1) + c) * nEf
+                R[r0:r0 + nEc, c0:c0 + nEf] = I
+        return R
+
+    for k_f, k_c in ((3, 2), (3, 0), (2, 1)):
+        R = restriction(mesh, d, k_f, k_c, "dg").toarray()
+        assert np.abs(R - explicit(k_f, k_c)).max() < 1e-13
+    pmg = PMG(h, [3, 2, 1, 0], coarse="lu")
+    S = h.S.toarray()
+    Sl = S
+    for l in range(1, 4):
+        Rx = explicit(pmg.degrees[l - 1], pmg.degrees[l])
+        Sl = Rx @ Sl @ Rx.T
+        assert np.abs(pmg.levels[l].S.toarray() - Sl).max() < 1e-13 * np.abs(S).max()
