@@ -16,7 +16,9 @@ the mathematics fix, independent of the oracle's own formulas:
   pressure k+1, up to the pre-asymptotic range of 4x4 -> 8x8 meshes);
 * p-multilevel transfers: the restriction maps the fine kernel onto the
   coarse one, the Galerkin coarse operators keep it, and FGMRES with the
-  V-cycle reaches the direct solution.
+  V-cycle reaches the direct solution; the restriction equals the L2
+  projections from independently built face bases (face pressure included)
+  and the coarse operators the Galerkin products with them.
 """
 import numpy as np
 import pytest
@@ -131,3 +133,36 @@ def test_pmg_transfers_keep_the_kernel_and_fgmres_converges():
     x, its, rr = fgmres(h.S, pmg.apply, rhs, rtol=1e-10, null=h.null_vector())
     assert rr <= 1e-10 and its < 40
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6
+
+
+def test_restriction_is_the_l2_projection_and_galerkin():
+    """The HHO-hp restriction (every face component, the face pressure
+    included, truncated on its own) equals the L2 projections
+    int psi_i^{l+1} psi_j^l from independently built face bases, and the
+    coarse operators are R S R^T with those projections."""
+    from oracle.basis import dim_P, face_basis
+    mesh = tri_mesh(2, jitter=0.2, seed=3)
+    h = HHOhp(mesh, 3)
+    d = mesh.dim
+
+    def explicit(k_f, k_c):
+        nFf, nFc = dim_P(d - 1, k_f), dim_P(d - 1, k_c)
+        R = np.zeros((mesh.n_face * (d + 1) * nFc, mesh.n_face * (d + 1) * nFf))
+        for F in h.faces:
+            Bf, Bc = face_basis(F, k_f), face_basis(F, k_c)
+            X, W = F.rule(2 * k_f + 2)
+            I = Bc.eval(X).T @ (W[:, None] * Bf.eval(X))
+            for c in range(d + 1):
+                r0, c0 = (F.id * (d + 1) + c) * nFc, (F.id * (d + 1) + c) * nFf
+                R[r0:r0 + nFc, c0:c0 + nFf] = I
+        return R
+
+    for k_f, k_c in ((3, 2), (3, 0), (2, 1)):
+        assert np.abs(restriction(mesh, d, k_f, k_c, "hp").toarray() - explicit(k_f, k_c)).max() < 1e-13
+    pmg = PMG(h, [3, 2, 1, 0], coarse="lu")
+    S = h.S.toarray()
+    Sl = S
+    for l in range(1, 4):
+        Rx = explicit(pmg.degrees[l - 1], pmg.degrees[l])
+        Sl = Rx @ Sl @ Rx.T
+        assert np.abs(pmg.levels[l].S.toarray() - Sl).max() < 1e-13 * np.abs(S).max()
