@@ -11,7 +11,7 @@ orthonormal element basis; the global vector is these blocks in element
 order.  The global operator couples an element with itself and with its face
 neighbours.
 
-Readings (listed with the others in the design notes):
+Readings of the paper:
 * The BR2 terms act on every velocity component separately (the vector
   Laplacian), with the lifting L_FT(phi) in P^k(T)^d defined by
   int_T L_FT(phi) . tau = 1/2 int_F phi (tau . n_TF); the jump is

@@ -16,7 +16,7 @@ then one block of n_P per element (n_P = 1 for v&p-cond, n_E for v-cond).
 Uncondensed ("unc", Sec. 5.4's reference formulation): the same face blocks,
 then one block of n_P = (d+1) n_E per element, [U_T (d components) | P_T].
 
-Readings of the paper (each listed in the design notes):
+Readings of the paper:
 * Penalty (Eq. HHOdiscrMNT, "eta large enough"): eta_F = 4 (k+1)(k+d)/d |F| h_F / |T|.
 * Neumann datum: the residual subtracts int g_N . v_F, which is consistent with
   g_N = (grad u - p I) n (the problem statement prints the opposite sign).

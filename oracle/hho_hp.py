@@ -20,7 +20,7 @@ face pressure, so the global condensed system has one block of
 b = (d+1) n_F per face (velocity component-major, then pressure) and no
 element rows.
 
-Readings (listed with the others in the design notes):
+Readings of the paper:
 * The local residuals are those of Scheme 1 with k' = k+1 except for the boxed
   terms of Sec. 2.3.2, and the reconstruction, face residual (Sec. 2.2 with
   k' = k+1: the element part of r_TF is the whole trace of v_T - p v, which

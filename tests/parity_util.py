@@ -24,6 +24,6 @@ def rel(a, b):
 
 
 def report(tag, **vals):
-    """One PARITY line per result (collected into the design notes from `pytest -s`)."""
+    """One PARITY line per result (printed with `pytest -s`)."""
     print("PARITY " + tag + " " + " ".join(f"{k}={v:.3e}" if isinstance(v, float) else f"{k}={v}"
                                           for k, v in vals.items()), flush=True)
