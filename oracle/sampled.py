@@ -108,7 +108,7 @@ def residual_rows_dg(mesh, k, field, x, sample_elems, with_scale=False):
     full mesh (one block of (d+1) n_E per element).  The block row of an
     element S couples S with the neighbours across its interior faces only, and
     each coupling is intrinsic to S, that neighbour and their shared face (the
-    penalty of reading 29 takes the face counts of both).  So the rows are
+    BR2 penalty takes the face counts of both).  So the rows are
     computed on the submesh of the sampled elements and their neighbours with
     all of their faces: there the neighbours' own rows change (their outer
     faces lose a side), the sampled rows do not.  With with_scale, also the
