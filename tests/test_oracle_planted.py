@@ -6,8 +6,8 @@ dropped term (the Nitsche penalty, the BR2 penalty), a wrong sign (one of the
 two pressure-coupling blocks, the smoother's pressure pivot, the printed sign
 of the DG pressure stabilisation), a wrong orientation (an inward normal), a
 wrong index (the restriction keeping the wrong coefficients), too low a
-quadrature order, a dropped factor in a gradient, truncation in place of
-round-to-nearest-even."""
+quadrature order, a dropped sweep (the ILU forward solve), a dropped factor in
+a gradient, truncation in place of round-to-nearest-even."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -15,10 +15,12 @@ import scipy.sparse as sp
 import oracle.dg as odg
 import oracle.geometry as ogeo
 import oracle.hho as ohho
+import oracle.ilu as oilu
 import oracle.pmg as opmg
 import test_oracle_dg as pins_dg
 import test_oracle_hho as pins_hho
 import test_oracle_hp as pins_hp
+import test_oracle_ilu as pins_ilu
 import test_oracle_mlp as pins_mlp
 import test_oracle_pmg as pins_pmg
 import test_oracle_quadrature_basis as pins_quad
@@ -116,6 +118,22 @@ def test_pressure_pivot_sign_slip(monkeypatch):
     monkeypatch.setattr(opmg.Level, "_jacobi", wrong)
     _fails(pins_pmg.test_jacobi_pivot_blocks_equal_ilu_pivots_without_face_coupling, "v",
            lambda: pins_pmg.quad_mesh(3, 3, jitter=0.15, seed=2))
+
+
+def test_ilu_apply_without_the_forward_sweep(monkeypatch):
+    """z = U^-1 v instead of U^-1 L^-1 v."""
+    def wrong(self, v):
+        z = np.array(v, dtype=float)
+        sl, pat, rank, B = self.sl, self.pat, self.rank, self.blocks
+        for i in reversed(self.order):
+            s = z[sl(i)].copy()
+            for j in pat[i]:
+                if rank[j] > rank[i]:
+                    s -= B[(i, j)] @ z[sl(j)]
+            z[sl(i)] = np.linalg.solve(B[(i, i)], s)
+        return z
+    monkeypatch.setattr(oilu.BlockILU, "apply", wrong)
+    _fails(pins_ilu.test_single_element_is_exact, "vp")
 
 
 # --- DG scheme (Scheme 3) ---
